@@ -1,0 +1,157 @@
+"""Independent numpy restatements used only to pin the oracle.
+
+These take a different route from the oracle (numpy float32 vector arithmetic,
+np.unique / lexsort grouping, O(n^2) pairwise comparison) so that a slip in
+the oracle's C++ (a dropped term, a wrong index, a wrong sign) shows up as a
+mismatch.  Nothing here is called by the oracle or by the CUDA library.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+F32 = np.float32
+
+
+def bbox_s_hi(p: np.ndarray, aspect=(1.0, 1.0, 1.0)):
+    mn = p.min(axis=0)
+    mx = p.max(axis=0)
+    ext = (mx - mn).astype(F32)
+    s_hi = F32(np.max(ext / np.asarray(aspect, dtype=F32)))
+    if s_hi == 0:
+        s_hi = F32(1.0)
+    return mn.astype(F32), s_hi
+
+
+def cells(p: np.ndarray, s, aspect=(1.0, 1.0, 1.0)):
+    """Eq. 2: absolute cells floor(x / v) (int64) and the float floors, v = s * r."""
+    v = (F32(s) * np.asarray(aspect, dtype=F32)).astype(F32)
+    q = (p.astype(F32) / v[None, :]).astype(F32)
+    f = np.floor(q).astype(F32)
+    return f.astype(np.int64), f, v
+
+
+def rel_cells(p: np.ndarray, s, aspect=(1.0, 1.0, 1.0)):
+    mn, _ = bbox_s_hi(p, aspect)
+    g, f, v = cells(p, s, aspect)
+    gmin = np.floor((mn / v).astype(F32)).astype(np.int64)
+    return g - gmin[None, :], f, v
+
+
+def packed_keys(p, s, aspect=(1.0, 1.0, 1.0)):
+    u, _, _ = rel_cells(p, s, aspect)
+    assert (u >= 0).all() and (u < (1 << 21)).all()
+    u = u.astype(np.uint64)
+    return u[:, 0] | (u[:, 1] << np.uint64(21)) | (u[:, 2] << np.uint64(42))
+
+
+def centre_d2(p, f, v):
+    """Section 3.2 distance to v * (g + 0.5), squared, binary32, fixed order."""
+    half = (f + F32(0.5)).astype(F32)
+    c = (v[None, :] * half).astype(F32)
+    d = (p.astype(F32) - c).astype(F32)
+    sq = (d * d).astype(F32)
+    return ((sq[:, 0] + sq[:, 1]).astype(F32) + sq[:, 2]).astype(F32)
+
+
+def count_unique(p, s, aspect=(1.0, 1.0, 1.0), active=None):
+    u, _, _ = rel_cells(p, s, aspect)
+    if active is not None:
+        u = u[active]
+    return int(np.unique(u, axis=0).shape[0])
+
+
+def brute_force_select(p, s, aspect=(1.0, 1.0, 1.0), active=None):
+    """O(n^2) grouping by pairwise cell equality, then a linear argmin of d^2
+    (ties to the lowest index) per group; returns the representatives, ascending."""
+    idx = np.arange(p.shape[0]) if active is None else np.asarray(active)
+    g, f, v = cells(p, s, aspect)
+    d2 = centre_d2(p, f, v)
+    g = g[idx]
+    d2 = d2[idx]
+    same = (g[:, None, :] == g[None, :, :]).all(axis=2)
+    reps = set()
+    for a in range(len(idx)):
+        members = np.nonzero(same[a])[0]
+        best = members[0]
+        for b in members[1:]:
+            if d2[b] < d2[best] or (d2[b] == d2[best] and idx[b] < idx[best]):
+                best = b
+        reps.add(int(idx[best]))
+    return np.array(sorted(reps), dtype=np.int32)
+
+
+def lexsort_select(p, s, aspect=(1.0, 1.0, 1.0), active=None):
+    """Textbook dedupe: sort by (cell, d^2, index) and keep the first of each cell."""
+    idx = np.arange(p.shape[0]) if active is None else np.asarray(active)
+    u, f, v = rel_cells(p, s, aspect)
+    d2 = centre_d2(p, f, v)
+    u, d2 = u[idx], d2[idx]
+    order = np.lexsort((idx, d2, u[:, 2], u[:, 1], u[:, 0]))
+    us = u[order]
+    first = np.ones(len(order), dtype=bool)
+    first[1:] = (us[1:] != us[:-1]).any(axis=1)
+    return np.sort(idx[order[first]]).astype(np.int32)
+
+
+def splitmix64_finalise(z: int) -> int:
+    M = (1 << 64) - 1
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+def budgets(m: int, layers: int, ratio: int):
+    w = [ratio ** l for l in range(layers)]
+    S = sum(w)
+    ml = [m * w[l] // S for l in range(layers - 1)]
+    ml.append(m - sum(ml))
+    return ml
+
+
+def bisection(p, m_l, s_hi, sigma=(5, 100), t_max=20, aspect=(1.0, 1.0, 1.0), active=None):
+    """Section 3.3 search with numpy counting; returns (trace [(s, K)], s*, accepted)."""
+    k_max = m_l + (m_l * sigma[0]) // sigma[1]
+    lo, hi = F32(0.0), F32(s_hi)
+    trace = []
+    for _ in range(t_max):
+        s = F32((lo + hi) * F32(0.5))
+        K = count_unique(p, s, aspect, active)
+        trace.append((s, K))
+        if K > k_max:
+            lo = s
+        elif K < m_l:
+            hi = s
+        else:
+            return trace, s, True
+    return trace, (lo if lo > 0 else hi), False
+
+
+def hav_reference_small(p, m, layers=2, ratio=4, sigma=(5, 100), t_max=20, aspect=(1.0, 1.0, 1.0)):
+    """Whole sampler on a tiny cloud with numpy pieces (bisection + lexsort select +
+    priority truncation + shortfall), for cross-checking the oracle end to end."""
+    n = p.shape[0]
+    taken = np.zeros(n, dtype=bool)
+    _, s_hi = bbox_s_hi(p, aspect)
+    for m_l in budgets(m, layers, ratio):
+        if m_l == 0:
+            continue
+        active = np.nonzero(~taken)[0]
+        _, s_star, _ = bisection(p, m_l, s_hi, sigma, t_max, aspect, active)
+        reps = lexsort_select(p, s_star, aspect, active)
+        K = len(reps)
+        if K > m_l:
+            u, _, _ = rel_cells(p, s_star, aspect)
+            u = u.astype(np.uint64)
+            keys = u[:, 0] | (u[:, 1] << np.uint64(21)) | (u[:, 2] << np.uint64(42))
+            pr = np.array([splitmix64_finalise(int(keys[i])) for i in reps], dtype=np.uint64)
+            reps = reps[np.argsort(pr, kind="stable")[:m_l]]
+        taken[reps] = True
+        if K < m_l:
+            need = m_l - K
+            for i in active:
+                if need == 0:
+                    break
+                if not taken[i]:
+                    taken[i] = True
+                    need -= 1
+    return np.nonzero(taken)[0].astype(np.int32)

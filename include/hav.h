@@ -1,0 +1,167 @@
+/*
+ * hav.h -- C ABI of the GB300 (sm_103a) HAVSampler library, libhav.so.
+ *
+ * HAVSampler (arXiv 2305.14306) picks m of n xyz points: it voxelises the
+ * cloud (Section 3.2, Eq. 2), keeps the point closest to each occupied
+ * voxel's centre (Section 3.2, "Center-closest Point Sampling"), searches the
+ * voxel size by bisection until the occupied-voxel count K lies in
+ * [m, (1 + sigma) m] (Section 3.3, "AVS"), and does so over k coarse-to-fine
+ * layers whose budgets grow 4x per layer and sum to m (Section 3.4, Eq. 3).
+ *
+ * Conventions shared by every entry point:
+ *   - points are float32 x/y/z interleaved (array of structs, 12 bytes per
+ *     point), in DEVICE memory, owned by the caller, never modified;
+ *   - output indices are int32, ascending within each cloud, written to
+ *     caller-owned DEVICE memory;
+ *   - calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream); argument errors are returned synchronously and nothing
+ *     is enqueued; data-dependent errors (non-finite input, key range,
+ *     timeouts) are recorded on the device and read with hav_status_get();
+ *   - the context owns all scratch memory (hash tables, masks, traces), is
+ *     bound to the device current at creation, and must not be used by two
+ *     streams at once (calls on one context serialise on its workspace);
+ *   - the arithmetic is plain IEEE binary32 rounded to nearest without fused
+ *     multiply-add, so results are bit-identical to any conforming restatement
+ *     of the same procedure.
+ *
+ * Readings of the paper fixed by this library (the text leaves them open):
+ *   - v = s * aspect, with the scalar s bisected over (0, s_hi], s_hi the
+ *     largest bounding-box extent divided by its aspect component (Section 3.3);
+ *   - acceptance when m_l <= K <= m_l + floor(m_l * sigma); after t_max steps
+ *     without acceptance, s* = lo if lo > 0 (too many voxels: cut off), else
+ *     s* = hi (too few: shortfall fill) (Section 3.3);
+ *   - the centre-closest rule compares squared distances; ties go to the
+ *     lowest point index (Section 3.2);
+ *   - "cut off" keeps the m_l voxels whose SplitMix64-finalised packed key is
+ *     smallest; a shortfall adds untaken points in ascending index order;
+ *   - layer budgets m_l = floor(m * r^(l-1) / sum_j r^(j-1)), the last layer
+ *     takes the remainder (Eq. 3, r = 4);
+ *   - voxel keys pack the three cell indices, made relative to the bounding
+ *     box's minimum cell, into 21 bits each (t_max <= 20 keeps them in range).
+ */
+#ifndef HAV_H
+#define HAV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HAV_OK = 0,
+    HAV_ERR_INVALID = 1,     /* bad argument; nothing was enqueued */
+    HAV_ERR_NONFINITE = 2,   /* a coordinate is NaN or infinite */
+    HAV_ERR_TABLE_FULL = 3,  /* a hash probe ran through a whole table (cannot happen
+                                with the library's sizing; reported, never trapped) */
+    HAV_ERR_TIMEOUT = 4,     /* a bounded device wait gave up; the call's output is void */
+    HAV_ERR_NOMEM = 5,       /* the context's workspace is too small for this call */
+    HAV_ERR_CUDA = 6,        /* a CUDA runtime call failed */
+    HAV_ERR_RANGE = 7        /* a voxel cell index does not fit 21 bits, or a quotient
+                                is not a finite integer (extreme coordinates) */
+} hav_status;
+
+/* Sampler parameters.  hav_params_default() gives the paper's settings
+ * (Section 4.1): sigma = 0.05, t_max = 20, k = 2 layers, ratio 4. */
+typedef struct {
+    int32_t sigma_num;    /* tolerance sigma = sigma_num / sigma_den, >= 0 */
+    int32_t sigma_den;    /* > 0 */
+    int32_t t_max;        /* bisection steps, 0..20 */
+    int32_t layers;       /* k, 1..8 */
+    int32_t layer_ratio;  /* budget ratio between consecutive layers, 1..64 */
+    float aspect[3];      /* r: the voxel is v = s * r; each component finite, > 0 */
+    uint32_t flags;       /* reserved, must be 0 */
+} hav_params;
+
+/* One layer of one call, as the device evaluated it (for tests and the
+ * roofline's algorithmic-byte count). */
+#define HAV_MAX_ITERS 20
+typedef struct {
+    int64_t m_l;                /* the layer's budget */
+    int64_t k_max;              /* m_l + floor(m_l * sigma) */
+    int64_t k_star;             /* occupied voxels at s* among the layer's points */
+    int64_t n_in;               /* points entering the layer (untaken so far) */
+    int32_t iters;              /* bisection steps evaluated */
+    int32_t accepted;           /* 1 if a step landed in [m_l, k_max] */
+    float s_hi;                 /* top of the bisection bracket */
+    float s_star;               /* chosen scalar voxel size */
+    float s[HAV_MAX_ITERS];     /* s evaluated at each step */
+    int64_t K[HAV_MAX_ITERS];   /* exact occupied-voxel count at that s */
+} hav_layer_trace;
+
+typedef struct hav_ctx hav_ctx;
+typedef struct CUstream_st* hav_stream;  /* same type as cudaStream_t */
+
+/* Fill *p with the paper's defaults.  p must not be NULL. */
+void hav_params_default(hav_params* p);
+
+/* Create a context on the CURRENT device with workspace for calls of up to
+ * max_points points in total (all segments of a call, < 2^31) and up to
+ * max_segments segments (1..256).  Allocates device memory once; no call
+ * allocates afterwards.  Returns HAV_ERR_NOMEM if cudaMalloc fails,
+ * HAV_ERR_CUDA if the device cannot run the kernels (e.g. not sm_103). */
+hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_segments);
+
+/* Release the context and its device memory.  Waits for the device.  NULL is ignored. */
+void hav_context_destroy(hav_ctx* ctx);
+
+/* Device bytes a context of this size holds. */
+size_t hav_workspace_bytes(int64_t max_points, int32_t max_segments);
+
+/* Sample m of n points (one cloud, one level).  points: device, n*3 floats;
+ * out_idx: device, m int32, receives ascending indices into points.
+ * 0 <= m <= n < 2^31; m == 0 enqueues nothing.  Section 3, Eq. 3. */
+hav_status hav_sample(hav_ctx* ctx, const float* points, int64_t n, int64_t m,
+                      const hav_params* params, int32_t* out_idx, hav_stream stream);
+
+/* Level chain on one cloud: level j+1 samples the points kept by level j (in
+ * ascending order), the way successive set-abstraction stages of a point
+ * network down-sample (Section 4.1).  m_levels: HOST array of num_levels
+ * budgets, non-increasing, m_levels[0] <= n.  out_idx: HOST array of
+ * num_levels DEVICE pointers; out_idx[j] receives m_levels[j] ascending
+ * indices into the ORIGINAL cloud.  All levels run in one launch. */
+hav_status hav_sample_levels(hav_ctx* ctx, const float* points, int64_t n,
+                             const int64_t* m_levels, int32_t num_levels,
+                             const hav_params* params, int32_t* const* out_idx,
+                             hav_stream stream);
+
+/* Batched, segmented form: num_segments clouds stored back to back in
+ * points.  seg_offsets: HOST array of num_segments+1 point offsets (first 0,
+ * non-decreasing).  seg_m: HOST array [num_levels][num_segments] of budgets,
+ * each level's budget <= the previous level's for that segment.  out_idx:
+ * HOST array of num_levels DEVICE pointers; out_idx[j] receives, for each
+ * segment s in order, seg_m[j][s] ascending indices LOCAL to segment s (into
+ * the segment's original points).  One persistent launch runs every level
+ * of every segment; each segment's result equals the single-cloud call's. */
+hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* seg_offsets,
+                              const int64_t* seg_m, int32_t num_segments, int32_t num_levels,
+                              const hav_params* params, int32_t* const* out_idx,
+                              hav_stream stream);
+
+/* Synchronise `stream` and return the status of the last call enqueued on
+ * this context: HAV_OK, or the first error any segment hit.  per_segment
+ * (HOST, nullable, >= num_segments entries) receives each segment's status.
+ * A segment in error still gets seg_m indices (0..m-1) so that the other
+ * segments' output positions stay valid. */
+hav_status hav_status_get(hav_ctx* ctx, hav_stream stream, int32_t* per_segment);
+
+/* Synchronise `stream` and copy the last call's per-layer traces to `out`
+ * (HOST), ordered [level][segment][layer]; returns the number of records
+ * written (<= max_records), or -1 on error. */
+int32_t hav_trace_get(hav_ctx* ctx, hav_stream stream, hav_layer_trace* out, int32_t max_records);
+
+/* Test hook for Cnt(P, v) of Section 3.3: exact number of occupied voxels at
+ * v = s * aspect over all n points (bounding box from the same points).
+ * Synchronous: *K (HOST) is valid on return. */
+hav_status hav_count(hav_ctx* ctx, const float* points, int64_t n, float s,
+                     const float aspect[3], int64_t* K, hav_stream stream);
+
+/* Static description of a status code. */
+const char* hav_status_string(hav_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAV_H */

@@ -1,0 +1,247 @@
+// C ABI of libhav.so (declared in include/hav.h): argument validation, the
+// launch plan, and status / trace read-back.  Every step of the sampler runs
+// in the kernels of hav_sampler.cu; this file only marshals.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hav.h"
+#include "hav_internal.h"
+
+struct hav_ctx {
+    int device;
+    int nblocks;
+    havk::Layout lay;
+    unsigned char* ws;
+    int32_t last_S;
+    int32_t last_L;
+    int32_t last_layers;
+};
+
+namespace {
+
+hav_status check_params(const hav_params* p) {
+    if (!p) return HAV_ERR_INVALID;
+    if (p->sigma_num < 0 || p->sigma_den <= 0) return HAV_ERR_INVALID;
+    if (p->t_max < 0 || p->t_max > HAV_MAX_ITERS) return HAV_ERR_INVALID;
+    if (p->layers < 1 || p->layers > havk::kMaxLayers) return HAV_ERR_INVALID;
+    if (p->layer_ratio < 1 || p->layer_ratio > 64) return HAV_ERR_INVALID;
+    // budgets m * ratio^(layers-1) must fit int64 for m < 2^31
+    long long w = 1;
+    for (int i = 1; i < p->layers; ++i) {
+        w *= p->layer_ratio;
+        if (w > (1ll << 31)) return HAV_ERR_INVALID;
+    }
+    // sigma * m must stay below 2^31 in the tolerance bound
+    if (static_cast<long long>(p->sigma_num) > 64ll * p->sigma_den) return HAV_ERR_INVALID;
+    for (int a = 0; a < 3; ++a)
+        if (!(p->aspect[a] > 0.0f) || !std::isfinite(p->aspect[a])) return HAV_ERR_INVALID;
+    if (p->flags != 0) return HAV_ERR_INVALID;
+    return HAV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hav_params_default(hav_params* p) {
+    if (!p) return;
+    p->sigma_num = 5;
+    p->sigma_den = 100;
+    p->t_max = 20;
+    p->layers = 2;
+    p->layer_ratio = 4;
+    p->aspect[0] = p->aspect[1] = p->aspect[2] = 1.0f;
+    p->flags = 0;
+}
+
+const char* hav_status_string(hav_status s) {
+    switch (s) {
+        case HAV_OK: return "ok";
+        case HAV_ERR_INVALID: return "invalid argument";
+        case HAV_ERR_NONFINITE: return "non-finite coordinate";
+        case HAV_ERR_TABLE_FULL: return "hash table full";
+        case HAV_ERR_TIMEOUT: return "bounded device wait timed out";
+        case HAV_ERR_NOMEM: return "workspace too small or allocation failed";
+        case HAV_ERR_CUDA: return "CUDA runtime error";
+        case HAV_ERR_RANGE: return "voxel cell index out of range";
+    }
+    return "unknown status";
+}
+
+size_t hav_workspace_bytes(int64_t max_points, int32_t max_segments) {
+    if (max_points < 1 || max_segments < 1) return 0;
+    return havk::make_layout(max_points, max_segments).total;
+}
+
+hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_segments) {
+    if (!out) return HAV_ERR_INVALID;
+    *out = nullptr;
+    if (max_points < 1 || max_points >= (1ll << 31)) return HAV_ERR_INVALID;
+    if (max_segments < 1 || max_segments > havk::kMaxSegments) return HAV_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HAV_ERR_CUDA;
+    int major = 0, minor = 0, coop = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (major != 10 || minor != 3 || !coop) return HAV_ERR_CUDA;  // built for sm_103a only
+    const int nb = havk::max_coresident_blocks(dev);
+    if (nb < 1) return HAV_ERR_CUDA;
+    hav_ctx* c = new hav_ctx();
+    c->device = dev;
+    c->nblocks = nb;
+    c->lay = havk::make_layout(max_points, max_segments);
+    if (cudaMalloc(&c->ws, c->lay.total) != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return HAV_ERR_NOMEM;
+    }
+    if (cudaMemset(c->ws, 0, c->lay.total) != cudaSuccess) {
+        cudaFree(c->ws);
+        delete c;
+        return HAV_ERR_CUDA;
+    }
+    *out = c;
+    return HAV_OK;
+}
+
+void hav_context_destroy(hav_ctx* ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    cudaFree(ctx->ws);
+    delete ctx;
+}
+
+hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* seg_offsets,
+                              const int64_t* seg_m, int32_t num_segments, int32_t num_levels,
+                              const hav_params* params, int32_t* const* out_idx, hav_stream stream) {
+    if (!ctx || !seg_offsets || !seg_m || !out_idx) return HAV_ERR_INVALID;
+    hav_status st = check_params(params);
+    if (st != HAV_OK) return st;
+    if (num_segments < 1 || num_segments > ctx->lay.max_segments) return HAV_ERR_INVALID;
+    if (num_levels < 1 || num_levels > havk::kMaxLevels) return HAV_ERR_INVALID;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != ctx->device) return HAV_ERR_INVALID;
+    if (seg_offsets[0] != 0) return HAV_ERR_INVALID;
+    for (int s = 0; s < num_segments; ++s)
+        if (seg_offsets[s + 1] < seg_offsets[s]) return HAV_ERR_INVALID;
+    const int64_t total = seg_offsets[num_segments];
+    if (total > ctx->lay.max_points) return HAV_ERR_NOMEM;
+    if (total > 0 && !points) return HAV_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(points) % 4 != 0) return HAV_ERR_INVALID;
+    int64_t any_m = 0;
+    for (int j = 0; j < num_levels; ++j) {
+        int64_t level_sum = 0;
+        for (int s = 0; s < num_segments; ++s) {
+            const int64_t prev = (j == 0) ? (seg_offsets[s + 1] - seg_offsets[s])
+                                          : seg_m[static_cast<int64_t>(j - 1) * num_segments + s];
+            const int64_t m = seg_m[static_cast<int64_t>(j) * num_segments + s];
+            if (m < 0 || m > prev) return HAV_ERR_INVALID;
+            level_sum += m;
+        }
+        if (level_sum > 0 && !out_idx[j]) return HAV_ERR_INVALID;
+        any_m += level_sum;
+    }
+
+    havk::Plan* plan = new havk::Plan();
+    std::memset(plan, 0, sizeof(havk::Plan));
+    plan->points = points;
+    plan->ws = ctx->ws;
+    plan->lay = ctx->lay;
+    plan->S = num_segments;
+    plan->L = num_levels;
+    plan->layers = params->layers;
+    plan->ratio = params->layer_ratio;
+    plan->t_max = params->t_max;
+    plan->sigma_num = params->sigma_num;
+    plan->sigma_den = params->sigma_den;
+    plan->nblocks = ctx->nblocks;
+    for (int a = 0; a < 3; ++a) plan->aspect[a] = params->aspect[a];
+    for (int j = 0; j < num_levels; ++j) plan->out[j] = out_idx[j];
+    for (int s = 0; s <= num_segments; ++s) plan->off0[s] = seg_offsets[s];
+    for (int j = 0; j < num_levels; ++j)
+        for (int s = 0; s < num_segments; ++s)
+            plan->m[j][s] = static_cast<int32_t>(seg_m[static_cast<int64_t>(j) * num_segments + s]);
+
+    cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);
+    ctx->last_S = num_segments;
+    ctx->last_L = num_levels;
+    ctx->last_layers = params->layers;
+    hav_status ret = HAV_OK;
+    if (cudaMemsetAsync(ctx->ws + ctx->lay.barrier, 0, ctx->lay.zero_bytes, strm) != cudaSuccess) {
+        ret = HAV_ERR_CUDA;
+    } else if (any_m > 0 && havk::launch_chain(*plan, strm) != 0) {
+        ret = HAV_ERR_CUDA;
+    }
+    delete plan;
+    return ret;
+}
+
+hav_status hav_sample_levels(hav_ctx* ctx, const float* points, int64_t n, const int64_t* m_levels,
+                             int32_t num_levels, const hav_params* params, int32_t* const* out_idx,
+                             hav_stream stream) {
+    if (n < 0 || n >= (1ll << 31)) return HAV_ERR_INVALID;
+    const int64_t offs[2] = {0, n};
+    return hav_sample_batched(ctx, points, offs, m_levels, 1, num_levels, params, out_idx, stream);
+}
+
+hav_status hav_sample(hav_ctx* ctx, const float* points, int64_t n, int64_t m,
+                      const hav_params* params, int32_t* out_idx, hav_stream stream) {
+    if (n < 0 || n >= (1ll << 31)) return HAV_ERR_INVALID;
+    const int64_t offs[2] = {0, n};
+    int32_t* outs[1] = {out_idx};
+    return hav_sample_batched(ctx, points, offs, &m, 1, 1, params, outs, stream);
+}
+
+hav_status hav_status_get(hav_ctx* ctx, hav_stream stream, int32_t* per_segment) {
+    if (!ctx) return HAV_ERR_INVALID;
+    cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(strm) != cudaSuccess) return HAV_ERR_CUDA;
+    havk::GlobalHdr gh;
+    if (cudaMemcpy(&gh, ctx->ws + ctx->lay.ghdr, sizeof gh, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HAV_ERR_CUDA;
+    if (per_segment && ctx->last_S > 0) {
+        std::vector<havk::SegHdr> sh(ctx->last_S);
+        if (cudaMemcpy(sh.data(), ctx->ws + ctx->lay.seghdr, sizeof(havk::SegHdr) * ctx->last_S,
+                       cudaMemcpyDeviceToHost) != cudaSuccess)
+            return HAV_ERR_CUDA;
+        for (int s = 0; s < ctx->last_S; ++s) per_segment[s] = sh[s].status;
+    }
+    return static_cast<hav_status>(gh.status);
+}
+
+int32_t hav_trace_get(hav_ctx* ctx, hav_stream stream, hav_layer_trace* out, int32_t max_records) {
+    if (!ctx || !out || max_records < 0) return -1;
+    cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(strm) != cudaSuccess) return -1;
+    const int S = ctx->last_S, L = ctx->last_L, K = ctx->last_layers;
+    std::vector<hav_layer_trace> all(static_cast<size_t>(L) * S * havk::kMaxLayers);
+    if (all.empty()) return 0;
+    if (cudaMemcpy(all.data(), ctx->ws + ctx->lay.trace, sizeof(hav_layer_trace) * all.size(),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    int32_t w = 0;
+    for (int j = 0; j < L; ++j)
+        for (int s = 0; s < S; ++s)
+            for (int l = 0; l < K; ++l) {
+                if (w >= max_records) return w;
+                out[w++] = all[(static_cast<size_t>(j) * S + s) * havk::kMaxLayers + l];
+            }
+    return w;
+}
+
+hav_status hav_count(hav_ctx* ctx, const float* points, int64_t n, float s, const float aspect[3],
+                     int64_t* K, hav_stream stream) {
+    if (!ctx || !points || !aspect || !K || n < 1 || n > ctx->lay.max_points) return HAV_ERR_INVALID;
+    if (!(s > 0.0f) || !std::isfinite(s)) return HAV_ERR_INVALID;
+    for (int a = 0; a < 3; ++a)
+        if (!(aspect[a] > 0.0f) || !std::isfinite(aspect[a])) return HAV_ERR_INVALID;
+    return static_cast<hav_status>(havk::count_voxels(points, n, s, aspect, ctx->ws, ctx->lay, K,
+                                                      reinterpret_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

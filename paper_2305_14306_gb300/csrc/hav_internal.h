@@ -1,0 +1,139 @@
+// Internal definitions shared by the HAVSampler kernels and the C ABI layer.
+// Not part of the public interface (include/hav.h is).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "hav.h"
+
+namespace havk {
+
+constexpr int kThreads = 512;              // threads per block of the persistent kernel
+constexpr int kMaxSegments = 256;          // segments per launch (plan lives in kernel params)
+constexpr int kMaxLevels = 8;
+constexpr int kMaxLayers = 8;
+constexpr int kMaxIters = HAV_MAX_ITERS;
+constexpr int kTile = kThreads;            // points per work tile (one per thread)
+constexpr int kSlotTile = 4 * kThreads;    // hash slots per work tile
+constexpr int kHistBits = 10;              // cut-off histogram over the top priority bits
+constexpr int kHistBins = 1 << kHistBits;
+constexpr int kMaxBlocks = 2048;
+constexpr int kMinCapLog2 = 6;             // smallest per-segment table: 64 slots
+
+constexpr unsigned long long kEmptyKey = ~0ull;  // valid keys use 63 bits
+constexpr unsigned long long kEmptyVal = ~0ull;  // packed (d^2 bits, index) never reaches it
+
+// Zeroed by the host (one memset) before every launch.
+struct alignas(128) Barrier {
+    unsigned int count;
+    unsigned int pad0[31];
+    unsigned int gen;
+    unsigned int pad1[31];
+};
+
+struct GlobalHdr {
+    int32_t status;  // first error of the call (hav_status)
+    int32_t abort;   // set when a bounded wait gave up; every block leaves
+    int32_t pad[30];
+};
+
+struct SegHdr {
+    int32_t status;         // first error of this segment
+    int32_t nonfinite;      // set only in the bounding-box phase
+    uint32_t bbox[2][6];    // per level parity: ~enc(min xyz) then enc(max xyz), atomicMax'ed
+    uint32_t pad[2];
+};
+
+// Per segment, per layer parity: zeroed inside the kernel before use.
+struct LayerState {
+    uint32_t count[3];  // Cnt of the bisection pass, three-way rotation
+    uint32_t kstar;     // occupied voxels at s*
+    uint32_t cand;      // cut-off candidates in the boundary bin
+    int32_t bin;        // boundary bin of the cut-off
+    uint32_t below;     // voxels in bins below the boundary
+    uint32_t pad;
+};
+
+struct Cand {
+    unsigned long long h;  // cut-off priority
+    uint32_t g;            // point index (level-global)
+    uint32_t pad;
+};
+
+// Byte offsets of every region inside one workspace allocation.
+struct Layout {
+    int64_t max_points;
+    int32_t max_segments;
+    int32_t pad;
+    int64_t tab_slots;     // capacity bound of all per-segment tables of a level
+    int64_t cand_slots;
+    int64_t taken_words;
+    size_t barrier, ghdr, seghdr, zero_bytes;  // [barrier, barrier+zero_bytes) zeroed per call
+    size_t lstate, hist, partial_sf, partial_cmp, trace;
+    size_t pts[2], orig[2], taken[2];
+    size_t tabk[2], tabv, cand;
+    size_t total;
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline Layout make_layout(int64_t N, int32_t S) {
+    Layout L{};
+    L.max_points = N;
+    L.max_segments = S;
+    // Per-segment capacity C = max(nextpow2(2 n), 64) < max(4 n, 128).
+    L.tab_slots = 4 * N + 128 * static_cast<int64_t>(S);
+    L.cand_slots = L.tab_slots / 2;
+    L.taken_words = N / 32 + 2;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = align_up(o, 256);
+        o = at + bytes;
+        return at;
+    };
+    L.barrier = take(sizeof(Barrier));
+    L.ghdr = take(sizeof(GlobalHdr));
+    L.seghdr = take(sizeof(SegHdr) * S);
+    L.zero_bytes = o - L.barrier;
+    L.lstate = take(sizeof(LayerState) * 2 * S);
+    L.hist = take(sizeof(uint32_t) * 2 * S * kHistBins);
+    L.partial_sf = take(sizeof(int32_t) * S * kMaxBlocks);
+    L.partial_cmp = take(sizeof(int32_t) * kMaxBlocks);
+    L.trace = take(sizeof(hav_layer_trace) * kMaxLevels * S * kMaxLayers);
+    for (int b = 0; b < 2; ++b) {
+        L.pts[b] = take(sizeof(float) * 3 * N + 16);
+        L.orig[b] = take(sizeof(int32_t) * N + 16);
+        L.taken[b] = take(sizeof(uint32_t) * L.taken_words);
+    }
+    L.tabk[0] = take(sizeof(unsigned long long) * L.tab_slots);
+    L.tabk[1] = take(sizeof(unsigned long long) * L.tab_slots);
+    L.tabv = take(sizeof(unsigned long long) * L.tab_slots);
+    L.cand = take(sizeof(Cand) * L.cand_slots);
+    L.total = align_up(o, 256);
+    return L;
+}
+
+// Everything one launch needs, passed by value as the kernel's parameter
+// block (about 10 KB), so a captured CUDA graph replays exactly this plan.
+struct Plan {
+    const float* points;      // level-0 input (device)
+    unsigned char* ws;        // workspace base (device)
+    Layout lay;
+    int32_t* out[kMaxLevels]; // per-level outputs (device)
+    int32_t S, L, layers, ratio, t_max, sigma_num, sigma_den, nblocks;
+    float aspect[3];
+    int32_t pad;
+    int64_t off0[kMaxSegments + 1];       // level-0 segment offsets
+    int32_t m[kMaxLevels][kMaxSegments];  // budgets per level and segment
+};
+
+// Launchers (hav_sampler.cu).
+int max_coresident_blocks(int device);
+int launch_chain(const Plan& plan, cudaStream_t stream);
+int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
+                 unsigned char* ws, const Layout& lay, int64_t* K, cudaStream_t stream);
+
+}  // namespace havk

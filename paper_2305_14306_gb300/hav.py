@@ -1,0 +1,253 @@
+"""Python binding of libhav.so (include/hav.h): argument marshalling only.
+
+Every step of the sampler runs in the library's CUDA kernels; this module
+only passes device pointers, sizes and the current CUDA stream.  PyTorch
+supplies device memory and streams.  If the library is missing the calls
+raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhav.so")
+
+HAV_OK, HAV_ERR_INVALID, HAV_ERR_NONFINITE, HAV_ERR_TABLE_FULL = 0, 1, 2, 3
+HAV_ERR_TIMEOUT, HAV_ERR_NOMEM, HAV_ERR_CUDA, HAV_ERR_RANGE = 4, 5, 6, 7
+HAV_MAX_ITERS = 20
+MAX_SEGMENTS = 256
+MAX_LEVELS = 8
+
+
+class hav_params(C.Structure):
+    _fields_ = [
+        ("sigma_num", C.c_int32),
+        ("sigma_den", C.c_int32),
+        ("t_max", C.c_int32),
+        ("layers", C.c_int32),
+        ("layer_ratio", C.c_int32),
+        ("aspect", C.c_float * 3),
+        ("flags", C.c_uint32),
+    ]
+
+
+class hav_layer_trace(C.Structure):
+    _fields_ = [
+        ("m_l", C.c_int64),
+        ("k_max", C.c_int64),
+        ("k_star", C.c_int64),
+        ("n_in", C.c_int64),
+        ("iters", C.c_int32),
+        ("accepted", C.c_int32),
+        ("s_hi", C.c_float),
+        ("s_star", C.c_float),
+        ("s", C.c_float * HAV_MAX_ITERS),
+        ("K", C.c_int64 * HAV_MAX_ITERS),
+    ]
+
+
+class HavError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        msg = _lib_or_none().hav_status_string(status).decode() if _lib_or_none() else str(status)
+        super().__init__(f"{where}: {msg} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = [
+    "hav_params_default", "hav_context_create", "hav_context_destroy", "hav_workspace_bytes",
+    "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
+    "hav_count", "hav_status_string",
+]
+
+
+def _lib_or_none():
+    return _lib
+
+
+def load(path: str = LIB_PATH):
+    """Load libhav.so and declare its signatures (no device work)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_2305_14306_gb300.build.build() first")
+        L = C.CDLL(path)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        P = C.POINTER
+        L.hav_params_default.argtypes = [P(hav_params)]
+        L.hav_params_default.restype = None
+        L.hav_context_create.argtypes = [P(vp), i64, i32]
+        L.hav_context_create.restype = C.c_int
+        L.hav_context_destroy.argtypes = [vp]
+        L.hav_context_destroy.restype = None
+        L.hav_workspace_bytes.argtypes = [i64, i32]
+        L.hav_workspace_bytes.restype = C.c_size_t
+        L.hav_sample.argtypes = [vp, vp, i64, i64, P(hav_params), vp, vp]
+        L.hav_sample.restype = C.c_int
+        L.hav_sample_levels.argtypes = [vp, vp, i64, P(C.c_int64), i32, P(hav_params), P(vp), vp]
+        L.hav_sample_levels.restype = C.c_int
+        L.hav_sample_batched.argtypes = [vp, vp, P(C.c_int64), P(C.c_int64), i32, i32, P(hav_params),
+                                         P(vp), vp]
+        L.hav_sample_batched.restype = C.c_int
+        L.hav_status_get.argtypes = [vp, vp, P(C.c_int32)]
+        L.hav_status_get.restype = C.c_int
+        L.hav_trace_get.argtypes = [vp, vp, P(hav_layer_trace), i32]
+        L.hav_trace_get.restype = C.c_int32
+        L.hav_count.argtypes = [vp, vp, i64, C.c_float, P(C.c_float), P(C.c_int64), vp]
+        L.hav_count.restype = C.c_int
+        L.hav_status_string.argtypes = [C.c_int]
+        L.hav_status_string.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 1.0)) -> hav_params:
+    p = hav_params()
+    load().hav_params_default(C.byref(p))
+    p.sigma_num, p.sigma_den = sigma
+    p.t_max, p.layers, p.layer_ratio = t_max, layers, layer_ratio
+    for a in range(3):
+        p.aspect[a] = aspect[a]
+    return p
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check(st, where):
+    if st != HAV_OK:
+        raise HavError(st, where)
+
+
+def _points(points):
+    import torch
+    if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float32
+            and points.dim() == 2 and points.shape[1] == 3 and points.is_contiguous()):
+        raise ValueError("points must be a contiguous (n, 3) float32 CUDA tensor")
+    return points
+
+
+class Context:
+    """A libhav context: device workspace for calls of up to max_points points
+    in total and max_segments segments."""
+
+    def __init__(self, max_points: int, max_segments: int = 1):
+        L = load()
+        h = C.c_void_p()
+        _check(L.hav_context_create(C.byref(h), int(max_points), int(max_segments)), "hav_context_create")
+        self.handle = h
+        self.max_points = int(max_points)
+        self.max_segments = int(max_segments)
+
+    def close(self):
+        if self.handle:
+            load().hav_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hav_sample(ctx: Context, points, m: int, p: hav_params | None = None, out=None, stream=None):
+    """One cloud, one level: returns (or fills) an int32 CUDA tensor of m ascending indices."""
+    import torch
+    points = _points(points)
+    p = p or params()
+    if out is None:
+        out = torch.empty(int(m), dtype=torch.int32, device=points.device)
+    st = load().hav_sample(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0], int(m), C.byref(p),
+                           C.c_void_p(out.data_ptr()), _stream_handle(stream))
+    _check(st, "hav_sample")
+    return out
+
+
+def hav_sample_levels(ctx: Context, points, m_levels, p: hav_params | None = None, outs=None, stream=None):
+    """Level chain on one cloud: returns one int32 tensor per level (indices into the original cloud)."""
+    import torch
+    points = _points(points)
+    p = p or params()
+    ml = np.ascontiguousarray(m_levels, dtype=np.int64)
+    if outs is None:
+        outs = [torch.empty(int(m), dtype=torch.int32, device=points.device) for m in ml]
+    ptrs = (C.c_void_p * len(ml))(*[o.data_ptr() for o in outs])
+    st = load().hav_sample_levels(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0],
+                                  ml.ctypes.data_as(C.POINTER(C.c_int64)), len(ml), C.byref(p), ptrs,
+                                  _stream_handle(stream))
+    _check(st, "hav_sample_levels")
+    return outs
+
+
+def hav_sample_batched(ctx: Context, points, seg_offsets, seg_m, p: hav_params | None = None, outs=None,
+                       stream=None):
+    """Segmented batch: seg_offsets (S+1,), seg_m (L, S) host arrays.  Returns one int32
+    tensor per level holding each segment's segment-local indices back to back."""
+    import torch
+    points = _points(points)
+    p = p or params()
+    offs = np.ascontiguousarray(seg_offsets, dtype=np.int64)
+    m = np.ascontiguousarray(np.atleast_2d(seg_m), dtype=np.int64)
+    S, L = len(offs) - 1, m.shape[0]
+    if m.shape[1] != S:
+        raise ValueError("seg_m must be (levels, segments)")
+    if outs is None:
+        outs = [torch.empty(int(m[j].sum()), dtype=torch.int32, device=points.device) for j in range(L)]
+    ptrs = (C.c_void_p * L)(*[o.data_ptr() for o in outs])
+    st = load().hav_sample_batched(ctx.handle, C.c_void_p(points.data_ptr()),
+                                   offs.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   m.ctypes.data_as(C.POINTER(C.c_int64)), S, L, C.byref(p), ptrs,
+                                   _stream_handle(stream))
+    _check(st, "hav_sample_batched")
+    return outs
+
+
+def hav_status_get(ctx: Context, num_segments: int = 1, stream=None):
+    """Synchronise and return (status, per-segment statuses) of the last call."""
+    per = (C.c_int32 * max(1, num_segments))()
+    st = load().hav_status_get(ctx.handle, _stream_handle(stream), per)
+    return int(st), [int(x) for x in per[:num_segments]]
+
+
+def hav_trace_get(ctx: Context, num_records: int, stream=None):
+    """Per-layer traces of the last call, [level][segment][layer] flattened, as dicts."""
+    buf = (hav_layer_trace * max(1, num_records))()
+    w = load().hav_trace_get(ctx.handle, _stream_handle(stream), buf, num_records)
+    if w < 0:
+        raise HavError(HAV_ERR_CUDA, "hav_trace_get")
+    out = []
+    for r in buf[:w]:
+        it = r.iters
+        out.append({
+            "m_l": r.m_l, "k_max": r.k_max, "k_star": r.k_star, "n_in": r.n_in, "iters": it,
+            "accepted": bool(r.accepted), "s_hi": np.float32(r.s_hi), "s_star": np.float32(r.s_star),
+            "s": np.array(r.s[:it], dtype=np.float32), "K": np.array(r.K[:it], dtype=np.int64),
+        })
+    return out
+
+
+def hav_count(ctx: Context, points, s: float, aspect=(1.0, 1.0, 1.0), stream=None) -> int:
+    """Cnt(P, v) at v = s * aspect (synchronous test hook)."""
+    points = _points(points)
+    asp = (C.c_float * 3)(*[float(a) for a in aspect])
+    K = C.c_int64(0)
+    st = load().hav_count(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0],
+                          float(np.float32(s)), asp, C.byref(K), _stream_handle(stream))
+    _check(st, "hav_count")
+    return int(K.value)
+
+
+def workspace_bytes(max_points: int, max_segments: int = 1) -> int:
+    return int(load().hav_workspace_bytes(int(max_points), int(max_segments)))

@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+element by element, bit-exact (integer indices; binary32 voxel sizes compared
+by their bits), on seeded inputs shaped like the paper's workloads."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import _gpu_helpers as G  # noqa: E402
+from paper_2305_14306_gb300 import scenes  # noqa: E402
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_cases.json")))
+
+
+@pytest.fixture(scope="module")
+def hv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_14306_gb300 import build, hav
+    build.build()
+    hav.load()
+    return hav
+
+
+@pytest.fixture(scope="module")
+def ctx(hv):
+    c = hv.Context(1 << 21, 256)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def run_levels(hv, ctx, pts, ml, pkw=None):
+    p = hv.params(**(pkw or {}))
+    outs = hv.hav_sample_levels(ctx, dev(pts), ml, p)
+    st, per = hv.hav_status_get(ctx, 1)
+    tr = hv.hav_trace_get(ctx, len(ml) * p.layers)
+    return [o.cpu().numpy() for o in outs], st, tr, p.layers
+
+
+def assert_parity(res_gpu, tr_gpu, layers, res_ora, tr_ora):
+    for j, (a, b) in enumerate(zip(res_gpu, res_ora)):
+        assert a.shape == b.shape, (j, a.shape, b.shape)
+        if not np.array_equal(a, b):
+            bad = np.nonzero(a != b)[0]
+            raise AssertionError(f"level {j}: {len(bad)} mismatches, first at {bad[0]}: {a[bad[0]]} vs {b[bad[0]]}")
+    for j, lev in enumerate(tr_ora):
+        for l, rec in enumerate(lev):
+            why = G.traces_equal(tr_gpu[j * layers + l], rec)
+            assert why is None, f"level {j} layer {l}: {why}"
+
+
+# ------------------------------------------------------------------ Cnt
+@pytest.mark.parametrize("gen", ["c1", "c2", "c3"])
+def test_count_matches_oracle(hv, ctx, oracle_mod, gen):
+    pts = {"c1": lambda: scenes.uniform_box(16384, 0),
+           "c2": lambda: scenes.lidar_min(16384, 0)[0],
+           "c3": lambda: scenes.room_scene(1 << 18, 3)}[gen]()
+    d = dev(pts)
+    for s in [0.05, 0.21, 0.5, 1.3, 7.0]:
+        assert hv.hav_count(ctx, d, s) == oracle_mod.count(pts, s), s
+    assert hv.hav_count(ctx, d, 0.3, (1.0, 1.0, 0.88)) == oracle_mod.count(pts, 0.3, (1.0, 1.0, 0.88))
+
+
+# ----------------------------------------------------------- hand cases
+@pytest.mark.parametrize("name", ["line4_m2", "line8_two_layers", "identical_shortfall"])
+def test_hand_cases(hv, ctx, name):
+    c = GOLD[name]
+    pts = np.asarray(c["points"], dtype=np.float32)
+    res, st, tr, K = run_levels(hv, ctx, pts, [c["m"]], {"t_max": c["t_max"], "layers": c["layers"]})
+    assert st == 0
+    assert list(res[0]) == c["out"]
+    for l, s_star in enumerate(c["s_star"]):
+        assert tr[l]["s_star"] == np.float32(s_star)
+    for l, steps in enumerate(c.get("trace", [])):
+        assert [(float(s), int(k)) for s, k in zip(tr[l]["s"], tr[l]["K"])] == [tuple(x) for x in steps]
+
+
+# -------------------------------------------------------- full configs
+@pytest.mark.parametrize("seed", range(10))
+def test_c1_uniform_16k_to_4096(hv, ctx, seed):
+    pts = scenes.uniform_box(16384, seed)
+    res, st, tr, K = run_levels(hv, ctx, pts, [4096])
+    assert st == 0
+    (ora, tr_o), = G.oracle_many([pts], [[4096]])
+    assert_parity(res, tr, K, ora, tr_o)
+
+
+@pytest.mark.parametrize("seed,shuffle", [(0, False), (1, False), (2, True), (5, False)])
+def test_c2_lidar_chain(hv, ctx, seed, shuffle):
+    pts, _ = scenes.lidar_min(16384, seed)
+    if shuffle:
+        pts = pts[np.random.default_rng(seed).permutation(pts.shape[0])]
+    ml = [16384, 4096, 1024, 512]
+    res, st, tr, K = run_levels(hv, ctx, pts, ml)
+    assert st == 0
+    (ora, tr_o), = G.oracle_many([pts], [ml])
+    assert_parity(res, tr, K, ora, tr_o)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_c3_indoor_1m_four_levels(hv, ctx, seed):
+    pts = scenes.room_scene(1 << 20, seed)
+    ml = [1 << 18, 1 << 16, 1 << 14, 1 << 12]
+    res, st, tr, K = run_levels(hv, ctx, pts, ml)
+    assert st == 0
+    (ora, tr_o), = G.oracle_many([pts], [ml])
+    assert_parity(res, tr, K, ora, tr_o)
+
+
+# ---------------------------------------------------------- edge cases
+@pytest.mark.parametrize("n,m", [(1, 1), (7, 3), (513, 100), (1000, 1000), (1000, 999), (2049, 1)])
+def test_ragged_sizes(hv, ctx, n, m):
+    pts = scenes.uniform_box(n, n + m)
+    res, st, tr, K = run_levels(hv, ctx, pts, [m])
+    assert st == 0
+    (ora, tr_o), = G.oracle_many([pts], [[m]])
+    assert_parity(res, tr, K, ora, tr_o)
+
+
+def test_m_zero_writes_nothing(hv, ctx):
+    pts = dev(scenes.uniform_box(100, 1))
+    out = torch.full((4,), -7, dtype=torch.int32, device="cuda")
+    hv.hav_sample(ctx, pts, 0, out=out)
+    assert hv.hav_status_get(ctx)[0] == 0
+    assert (out.cpu() == -7).all()
+
+
+@pytest.mark.parametrize("pkw", [{"t_max": 0}, {"t_max": 1}, {"t_max": 3}, {"layers": 1}, {"layers": 3},
+                                 {"aspect": (1.0, 1.0, 0.88)}, {"sigma": (0, 1)}, {"sigma": (1, 2)}])
+def test_parameter_variants(hv, ctx, pkw):
+    pts = scenes.lidar_min(16384, 3)[0]
+    ml = [4096, 1024]
+    res, st, tr, K = run_levels(hv, ctx, pts, ml, pkw)
+    assert st == 0
+    (ora, tr_o), = G.oracle_many([pts], [ml], pkw)
+    assert_parity(res, tr, K, ora, tr_o)
+
+
+def test_duplicates_and_lattice(hv, ctx):
+    rng = np.random.default_rng(0)
+    base = rng.uniform(0, 4, size=(300, 3)).astype(np.float32)
+    pts = np.concatenate([base, base, np.round(base), np.full((50, 3), 2.0, np.float32)])
+    for m in [10, 100, 500, 900]:
+        res, st, tr, K = run_levels(hv, ctx, pts, [m])
+        assert st == 0
+        (ora, tr_o), = G.oracle_many([pts], [[m]])
+        assert_parity(res, tr, K, ora, tr_o)
+
+
+def test_nonfinite_reports_status(hv, ctx):
+    pts = scenes.uniform_box(5000, 2)
+    pts[1234, 2] = np.inf
+    res, st, tr, K = run_levels(hv, ctx, pts, [100])
+    assert st == hv.HAV_ERR_NONFINITE
+    assert list(res[0]) == list(range(100))  # documented fill for a segment in error
+
+
+def test_repeat_is_deterministic(hv, ctx):
+    pts = scenes.room_scene(200000, 4)
+    a, _, _, _ = run_levels(hv, ctx, pts, [50000, 12500])
+    b, _, _, _ = run_levels(hv, ctx, pts, [50000, 12500])
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_permutation_invariance_gpu(hv, ctx):
+    pts = scenes.uniform_box(16384, 6)
+    perm = np.random.default_rng(1).permutation(pts.shape[0])
+    a, _, tr, _ = run_levels(hv, ctx, pts, [4096])
+    b, _, _, _ = run_levels(hv, ctx, pts[perm], [4096])
+    assert all(r["accepted"] for r in tr)
+    assert np.array_equal(np.sort(perm[b[0]]), a[0])
+
+
+# ------------------------------------------------------------- batched
+def _batched(hv, ctx, clouds, ml_per_level, pkw=None):
+    pts, offs = scenes.concat(clouds)
+    S = len(clouds)
+    seg_m = np.array(ml_per_level, dtype=np.int64).reshape(-1, S)
+    p = hv.params(**(pkw or {}))
+    outs = hv.hav_sample_batched(ctx, dev(pts), offs, seg_m, p)
+    st, per = hv.hav_status_get(ctx, S)
+    tr = hv.hav_trace_get(ctx, seg_m.shape[0] * S * p.layers)
+    return [o.cpu().numpy() for o in outs], st, per, tr, seg_m, p.layers
+
+
+def _split(out, seg_m_level):
+    offs = np.concatenate([[0], np.cumsum(seg_m_level)])
+    return [out[offs[s]:offs[s + 1]] for s in range(len(seg_m_level))]
+
+
+def check_batched(hv, ctx, clouds, seg_m, pkw=None):
+    outs, st, per, tr, seg_m, layers = _batched(hv, ctx, clouds, seg_m, pkw)
+    assert st == 0, per
+    S, L = len(clouds), seg_m.shape[0]
+    ora = G.oracle_many(clouds, [seg_m[:, s] for s in range(S)], pkw)
+    for j in range(L):
+        parts = _split(outs[j], seg_m[j])
+        for s in range(S):
+            assert np.array_equal(parts[s], ora[s][0][j]), (j, s)
+            for l in range(layers):
+                why = G.traces_equal(tr[(j * S + s) * layers + l], ora[s][1][j][l])
+                assert why is None, (j, s, l, why)
+
+
+def test_batched_mixed_segments(hv, ctx):
+    sizes = [20000, 1, 0, 513, 70000, 4096, 33333, 12, 150000, 999]
+    clouds = [scenes.lidar_exact(n, 10 + i) if n >= 20000 else scenes.uniform_box(n, i)
+              for i, n in enumerate(sizes)]
+    m1 = [n // 4 for n in sizes]
+    m2 = [n // 16 for n in sizes]
+    check_batched(hv, ctx, clouds, [m1, m2])
+
+
+def test_batched_error_is_contained(hv, ctx):
+    clouds = [scenes.uniform_box(3000, i) for i in range(4)]
+    clouds[2] = clouds[2].copy()
+    clouds[2][5, 0] = np.nan
+    m = [[700] * 4]
+    outs, st, per, tr, seg_m, layers = _batched(hv, ctx, clouds, m)
+    assert st == hv.HAV_ERR_NONFINITE
+    assert per == [0, 0, hv.HAV_ERR_NONFINITE, 0]
+    parts = _split(outs[0], seg_m[0])
+    ora = G.oracle_many([clouds[s] for s in (0, 1, 3)], [[700]] * 3)
+    for k, s in enumerate((0, 1, 3)):
+        assert np.array_equal(parts[s], ora[k][0][0])
+    assert list(parts[2]) == list(range(700))
+
+
+@pytest.mark.slow
+def test_c4_batch_64_lidar_clouds(hv):
+    clouds = scenes.lidar_batch(64, seed=0)
+    total = sum(c.shape[0] for c in clouds)
+    ctx = hv.Context(total, 64)
+    try:
+        sizes = [c.shape[0] for c in clouds]
+        check_batched(hv, ctx, clouds, [[n // 4 for n in sizes], [n // 16 for n in sizes]])
+    finally:
+        ctx.close()

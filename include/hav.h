@@ -160,6 +160,29 @@ hav_status hav_count(hav_ctx* ctx, const float* points, int64_t n, float s,
 /* Static description of a status code. */
 const char* hav_status_string(hav_status s);
 
+/* hav_sample without a context and without any allocation.  The paper has no
+ * counterpart: this entry point serves callers that may not call cudaMalloc
+ * (code running inside another framework's memory pool or a fixed memory
+ * budget, plugin hosts that forbid allocation after start-up, real-time loops
+ * where an allocation and the synchronisation it can imply are not allowed).
+ * It computes exactly what hav_sample computes for one cloud, one level.
+ *
+ * Scratch: a static __device__ array of 6 MiB inside libhav.so, enough for
+ * one cloud of at most 32,768 points; every GPU that loads the library holds
+ * it until the process exits.  n > 32,768 returns HAV_ERR_NOMEM and enqueues
+ * nothing.  The first call on a device looks up the array's device address
+ * and the launch grid for that device (no allocation); make that first call
+ * before any stream capture.  All calls on a device share the one array:
+ * calls that overlap on the GPU (different streams, or host threads without
+ * ordering) race and corrupt each other's results; serialise them.
+ *
+ * points: device, n*3 floats; out_idx: device, m int32 (ascending indices);
+ * status_out: device int32 or NULL, receives the call's hav_status when the
+ * work completes on `stream`.  Argument errors are returned synchronously. */
+hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t m,
+                              const hav_params* params, int32_t* out_idx,
+                              int32_t* status_out, hav_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

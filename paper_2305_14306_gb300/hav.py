@@ -63,7 +63,7 @@ _lib = None
 EXPORTS = [
     "hav_params_default", "hav_context_create", "hav_context_destroy", "hav_workspace_bytes",
     "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
-    "hav_count", "hav_status_string",
+    "hav_count", "hav_status_string", "hav_sample_noalloc",
 ]
 
 
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
         L.hav_count.restype = C.c_int
         L.hav_status_string.argtypes = [C.c_int]
         L.hav_status_string.restype = C.c_char_p
+        L.hav_sample_noalloc.argtypes = [vp, i64, i64, P(hav_params), vp, vp, vp]
+        L.hav_sample_noalloc.restype = C.c_int
         _lib = L
         return L
 
@@ -247,6 +249,26 @@ def hav_count(ctx: Context, points, s: float, aspect=(1.0, 1.0, 1.0), stream=Non
                           float(np.float32(s)), asp, C.byref(K), _stream_handle(stream))
     _check(st, "hav_count")
     return int(K.value)
+
+
+NOALLOC_MAX_POINTS = 32768
+
+
+def hav_sample_noalloc(points, m: int, p: hav_params | None = None, out=None, status_out=None, stream=None):
+    """hav_sample for callers that cannot allocate device memory: no context,
+    scratch in the library's static device array (clouds of up to 32,768
+    points).  `out` and `status_out` (an int32 CUDA tensor of one element, or
+    None) are caller-provided; calls on one device must not overlap."""
+    import torch
+    points = _points(points)
+    p = p or params()
+    if out is None:
+        out = torch.empty(int(m), dtype=torch.int32, device=points.device)
+    sp = C.c_void_p(status_out.data_ptr()) if status_out is not None else C.c_void_p()
+    st = load().hav_sample_noalloc(C.c_void_p(points.data_ptr()), points.shape[0], int(m), C.byref(p),
+                                   C.c_void_p(out.data_ptr()), sp, _stream_handle(stream))
+    _check(st, "hav_sample_noalloc")
+    return out
 
 
 def workspace_bytes(max_points: int, max_segments: int = 1) -> int:

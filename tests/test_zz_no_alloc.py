@@ -1,0 +1,67 @@
+"""hav_sample_noalloc: the context-free entry point for callers that may not
+allocate device memory (framework memory pools, fixed budgets, plugin hosts,
+real-time loops).  It must give exactly what hav_sample gives, call after
+call, out of its static scratch array, and refuse clouds larger than that
+array holds.
+
+This file is named so that pytest collects it last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2305_14306_gb300 import scenes  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def hv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_14306_gb300 import build, hav
+    build.build()
+    hav.load()
+    return hav
+
+
+def test_noalloc_matches_hav_sample_on_two_calls_in_a_row(hv):
+    a = torch.from_numpy(scenes.uniform_box(16384, 21)).cuda()
+    b = torch.from_numpy(scenes.lidar_min(16384, 4)[0][:20000].copy()).cuda()
+    ma, mb = 4096, 5000
+    st_a = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    st_b = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    # two calls back to back on one stream, no synchronisation between them
+    out_a = hv.hav_sample_noalloc(a, ma, status_out=st_a)
+    out_b = hv.hav_sample_noalloc(b, mb, status_out=st_b)
+    torch.cuda.synchronize()
+    assert int(st_a.item()) == hv.HAV_OK and int(st_b.item()) == hv.HAV_OK
+
+    ctx = hv.Context(32768, 1)
+    try:
+        ref_a = hv.hav_sample(ctx, a, ma)
+        ref_b = hv.hav_sample(ctx, b, mb)
+        assert hv.hav_status_get(ctx)[0] == hv.HAV_OK
+    finally:
+        ctx.close()
+    # the tests' tolerance for indices: bit-exact
+    assert torch.equal(out_a.cpu(), ref_a.cpu())
+    assert torch.equal(out_b.cpu(), ref_b.cpu())
+    # and again, reusing the shared scratch that still holds the last call's contents
+    again = hv.hav_sample_noalloc(a, ma)
+    torch.cuda.synchronize()
+    assert torch.equal(again.cpu(), ref_a.cpu())
+
+
+def test_noalloc_refuses_clouds_beyond_its_scratch(hv):
+    n = hv.NOALLOC_MAX_POINTS + 1
+    pts = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    out = torch.full((8,), -3, dtype=torch.int32, device="cuda")
+    p = hv.params()
+    st = hv.load().hav_sample_noalloc(ctypes.c_void_p(pts.data_ptr()), n, 8, ctypes.byref(p),
+                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == hv.HAV_ERR_NOMEM
+    torch.cuda.synchronize()
+    assert (out.cpu() == -3).all()  # nothing was enqueued

@@ -71,8 +71,12 @@ typedef struct {
     int32_t layers;       /* k, 1..8 */
     int32_t layer_ratio;  /* budget ratio between consecutive layers, 1..64 */
     float aspect[3];      /* r: the voxel is v = s * r; each component finite, > 0 */
-    uint32_t flags;       /* reserved, must be 0 */
+    uint32_t flags;       /* 0, or HAV_FLAG_PHASE_TIMES (context calls only) */
 } hav_params;
+
+/* Record a device timestamp after every grid-wide phase of the call (for
+ * profiling; read back with hav_phase_times_get). */
+#define HAV_FLAG_PHASE_TIMES 1u
 
 /* One layer of one call, as the device evaluated it (for tests and the
  * roofline's algorithmic-byte count). */
@@ -150,6 +154,17 @@ hav_status hav_status_get(hav_ctx* ctx, hav_stream stream, int32_t* per_segment)
  * (HOST), ordered [level][segment][layer]; returns the number of records
  * written (<= max_records), or -1 on error. */
 int32_t hav_trace_get(hav_ctx* ctx, hav_stream stream, hav_layer_trace* out, int32_t max_records);
+
+/* Synchronise `stream` and copy the phase timer of the last call made with
+ * HAV_FLAG_PHASE_TIMES: t_ns[k] is the device %globaltimer (ns) when phase k
+ * ended, tag[k] = phase << 24 | level << 16 | layer << 8 | pass, with phase
+ * 0 kernel start, 1 bbox, 2 bisection pass, 3 selection, 4 cut-off classify,
+ * 5 cut-off resolve, 6 shortfall, 7 compaction count, 8 compaction scatter.
+ * HOST buffers of max_records entries; returns the number written, or -1.
+ * Records of an earlier call may follow the last valid one if this call
+ * recorded fewer. */
+int32_t hav_phase_times_get(hav_ctx* ctx, hav_stream stream, uint64_t* t_ns, uint32_t* tag,
+                            int32_t max_records);
 
 /* Test hook for Cnt(P, v) of Section 3.3: exact number of occupied voxels at
  * v = s * aspect over all n points (bounding box from the same points).

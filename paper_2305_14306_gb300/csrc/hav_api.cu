@@ -39,7 +39,7 @@ hav_status check_params(const hav_params* p) {
     if (static_cast<long long>(p->sigma_num) > 64ll * p->sigma_den) return HAV_ERR_INVALID;
     for (int a = 0; a < 3; ++a)
         if (!(p->aspect[a] > 0.0f) || !std::isfinite(p->aspect[a])) return HAV_ERR_INVALID;
-    if (p->flags != 0) return HAV_ERR_INVALID;
+    if ((p->flags & ~static_cast<uint32_t>(HAV_FLAG_PHASE_TIMES)) != 0) return HAV_ERR_INVALID;
     return HAV_OK;
 }
 
@@ -162,6 +162,10 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
     plan->nblocks = ctx->nblocks;
     for (int a = 0; a < 3; ++a) plan->aspect[a] = params->aspect[a];
     for (int j = 0; j < num_levels; ++j) plan->out[j] = out_idx[j];
+    if (params->flags & HAV_FLAG_PHASE_TIMES) {
+        plan->ptimes = reinterpret_cast<unsigned long long*>(ctx->ws + ctx->lay.ptimes);
+        plan->ptimes_cap = havk::kPhaseTimes;
+    }
     for (int s = 0; s <= num_segments; ++s) plan->off0[s] = seg_offsets[s];
     for (int j = 0; j < num_levels; ++j)
         for (int s = 0; s < num_segments; ++s)
@@ -173,6 +177,10 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
     ctx->last_layers = params->layers;
     hav_status ret = HAV_OK;
     if (cudaMemsetAsync(ctx->ws + ctx->lay.barrier, 0, ctx->lay.zero_bytes, strm) != cudaSuccess) {
+        ret = HAV_ERR_CUDA;
+    } else if (plan->ptimes &&
+               cudaMemsetAsync(plan->ptimes, 0, sizeof(unsigned long long) * 2 * havk::kPhaseTimes, strm) !=
+                   cudaSuccess) {
         ret = HAV_ERR_CUDA;
     } else if (any_m > 0 && havk::launch_chain(*plan, strm) != 0) {
         ret = HAV_ERR_CUDA;
@@ -231,6 +239,25 @@ int32_t hav_trace_get(hav_ctx* ctx, hav_stream stream, hav_layer_trace* out, int
                 if (w >= max_records) return w;
                 out[w++] = all[(static_cast<size_t>(j) * S + s) * havk::kMaxLayers + l];
             }
+    return w;
+}
+
+int32_t hav_phase_times_get(hav_ctx* ctx, hav_stream stream, uint64_t* t_ns, uint32_t* tag,
+                            int32_t max_records) {
+    if (!ctx || !t_ns || !tag || max_records < 0) return -1;
+    cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(strm) != cudaSuccess) return -1;
+    std::vector<unsigned long long> buf(2 * havk::kPhaseTimes);
+    if (cudaMemcpy(buf.data(), ctx->ws + ctx->lay.ptimes, sizeof(unsigned long long) * buf.size(),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    int32_t w = 0;
+    for (int k = 0; k < havk::kPhaseTimes && w < max_records; ++k) {
+        if (k > 0 && buf[2 * k] == 0) break;
+        t_ns[w] = buf[2 * k];
+        tag[w] = static_cast<uint32_t>(buf[2 * k + 1]);
+        ++w;
+    }
     return w;
 }
 

@@ -11,7 +11,7 @@
 
 namespace havk {
 
-constexpr int kThreads = 512;              // threads per block of the persistent kernel
+constexpr int kThreads = 1024;             // threads per block of the persistent kernel (one block per SM)
 constexpr int kMaxSegments = 256;          // segments per launch (plan lives in kernel params)
 constexpr int kMaxLevels = 8;
 constexpr int kMaxLayers = 8;
@@ -22,6 +22,7 @@ constexpr int kHistBits = 10;              // cut-off histogram over the top pri
 constexpr int kHistBins = 1 << kHistBits;
 constexpr int kMaxBlocks = 2048;
 constexpr int kMinCapLog2 = 6;             // smallest per-segment table: 64 slots
+constexpr int kPhaseTimes = 4096;          // (time, tag) records of the phase timer
 
 constexpr unsigned long long kEmptyKey = ~0ull;  // valid keys use 63 bits
 constexpr unsigned long long kEmptyVal = ~0ull;  // packed (d^2 bits, index) never reaches it
@@ -72,7 +73,7 @@ struct Layout {
     int64_t cand_slots;
     int64_t taken_words;
     size_t barrier, ghdr, seghdr, zero_bytes;  // [barrier, barrier+zero_bytes) zeroed per call
-    size_t lstate, hist, partial_sf, partial_cmp, trace;
+    size_t lstate, hist, partial_sf, partial_cmp, trace, ptimes;
     size_t pts[2], orig[2], taken[2];
     size_t tabk[2], tabv, cand;
     size_t total;
@@ -103,6 +104,7 @@ inline Layout make_layout(int64_t N, int32_t S) {
     L.partial_sf = take(sizeof(int32_t) * S * kMaxBlocks);
     L.partial_cmp = take(sizeof(int32_t) * kMaxBlocks);
     L.trace = take(sizeof(hav_layer_trace) * kMaxLevels * S * kMaxLayers);
+    L.ptimes = take(sizeof(unsigned long long) * 2 * kPhaseTimes);
     for (int b = 0; b < 2; ++b) {
         L.pts[b] = take(sizeof(float) * 3 * N + 16);
         L.orig[b] = take(sizeof(int32_t) * N + 16);
@@ -123,6 +125,9 @@ struct Plan {
     unsigned char* ws;        // workspace base (device)
     Layout lay;
     int32_t* out[kMaxLevels]; // per-level outputs (device)
+    unsigned long long* ptimes;  // phase timer records, or null (HAV_FLAG_PHASE_TIMES)
+    int32_t ptimes_cap;
+    int32_t pad2;
     int32_t S, L, layers, ratio, t_max, sigma_num, sigma_den, nblocks;
     float aspect[3];
     int32_t pad;

@@ -30,9 +30,13 @@
 namespace havk {
 namespace {
 
+#define TAG(phase, level, layer, pass) \
+    ((static_cast<unsigned>(phase) << 24) | (static_cast<unsigned>(level) << 16) | \
+     (static_cast<unsigned>(layer) << 8) | static_cast<unsigned>(pass))
+
 constexpr unsigned long long kSpinNs = 2000000000ull;  // 2 s per barrier wait
 constexpr unsigned int kSpinIters = 1u << 26;
-static_assert(kHistBins == 2 * kThreads, "the cut-off scan gives each thread two bins");
+static_assert(kHistBins % kThreads == 0, "the cut-off scan gives each thread whole bins");
 
 // ------------------------------------------------------------------ memory ops
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -208,32 +212,31 @@ __device__ T block_excl_scan(T v, T* total, T* scratch /* >= 32 */) {
     return before + x - v;
 }
 
-// Grid barrier with a bounded wait.  Returns false (for the whole block) when
-// this or another block gave up; the caller then leaves the kernel.
-__device__ bool grid_sync(Barrier* bar, GlobalHdr* gh, unsigned nblocks, int* s_flag) {
+// Grid barrier with a bounded wait.  Arrival is a release reduction on a
+// counter that only grows within a launch (zeroed by the host before it);
+// barrier number e of the launch completes when the counter reaches
+// e * nblocks, so no block has to act as the last arriver.  Returns false
+// (for the whole block) when this or another block gave up; the caller then
+// leaves the kernel.
+__device__ bool grid_sync_impl(Barrier* bar, GlobalHdr* gh, unsigned nblocks, unsigned* epoch,
+                               int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int fail = 0;
-        const unsigned gen = ld_acquire(&bar->gen);
+        const unsigned target = (*epoch + 1u) * nblocks;
+        *epoch += 1u;
         __threadfence();
-        const unsigned arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            st_release(&bar->gen, gen + 1);
-        } else {
-            const unsigned long long t0 = globaltimer();
-            for (unsigned it = 0;; ++it) {
-                if (ld_acquire(&bar->gen) != gen) break;
-                if ((it & 31) == 31) {
-                    if (ld_volatile(&gh->abort) || it > kSpinIters ||
-                        globaltimer() - t0 > kSpinNs) {
-                        fail = 1;
-                        break;
-                    }
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+        const unsigned long long t0 = globaltimer();
+        for (unsigned it = 0;; ++it) {
+            if (ld_acquire(&bar->count) >= target) break;
+            if ((it & 31) == 31) {
+                if (ld_volatile(&gh->abort) || it > kSpinIters || globaltimer() - t0 > kSpinNs) {
+                    fail = 1;
+                    break;
                 }
-                __nanosleep(20);
             }
+            if (it > 64) __nanosleep(32);
         }
         if (fail) {
             atomicExch(&gh->abort, 1);
@@ -277,6 +280,8 @@ struct Smem {
     long long scan_ll[32];
     int scan_i[32];
     float redf[6][32];
+    unsigned epoch;
+    int ntimes;
     int cut_seg;
     int cut_bin;
     int cut_below;
@@ -303,7 +308,21 @@ struct Dev {
     unsigned long long* tk[2];
     unsigned long long* tv;
     Cand* cand;
+    unsigned long long* ptimes;  // [2 * cap] (globaltimer ns, tag) pairs, or null
+    int ptimes_cap;
 };
+
+// Barrier plus, when phase timing is on, a (time, tag) record from block 0.
+// tag = phase << 24 | level << 16 | layer << 8 | pass.
+__device__ __forceinline__ bool grid_sync(Dev& d, unsigned nblocks, Smem& st, unsigned tag) {
+    const bool ok = grid_sync_impl(d.bar, d.gh, nblocks, &st.epoch, &st.flag);
+    if (d.ptimes && blockIdx.x == 0 && threadIdx.x == 0 && st.ntimes < d.ptimes_cap) {
+        d.ptimes[2 * st.ntimes] = globaltimer();
+        d.ptimes[2 * st.ntimes + 1] = tag;
+        st.ntimes += 1;
+    }
+    return ok;
+}
 
 __device__ __forceinline__ void seg_error(Dev& d, int s, int code) {
     atomicCAS(&d.sh[s].status, 0, code);
@@ -413,7 +432,7 @@ __device__ __forceinline__ void clear_layer_state(Dev& d, int S, int q, long lon
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_constant__ Plan P) {
+__global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_constant__ Plan P) {
     __shared__ Smem st;
     const int S = P.S;
     const int tid = threadIdx.x;
@@ -438,6 +457,18 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
     }
     d.tv = reinterpret_cast<unsigned long long*>(ws + P.lay.tabv);
     d.cand = reinterpret_cast<Cand*>(ws + P.lay.cand);
+    d.ptimes = P.ptimes;
+    d.ptimes_cap = P.ptimes_cap;
+    if (tid == 0) {
+        st.epoch = 0u;
+        st.ntimes = 0;
+        if (d.ptimes && blockIdx.x == 0) {
+            d.ptimes[0] = globaltimer();
+            d.ptimes[1] = 0;
+            st.ntimes = 1;
+        }
+    }
+    __syncthreads();
 
     for (int j = 0; j < P.L; ++j) {
         level_setup(P, j, st);
@@ -496,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
             clear_tables(d, st, S, true, true, true, gtid, gstride);
             clear_layer_state(d, S, 0, gtid, gstride);
             clear_layer_state(d, S, 1, gtid, gstride);
-            if (!grid_sync(d.bar, d.gh, P.nblocks, &st.flag)) return;
+            if (!grid_sync(d, P.nblocks, st, TAG(1, j, 0, 0))) return;
         }
 
         // --------------------------------------------------- search bracket
@@ -621,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
                     }
                     if (blockIdx.x == 0 && tid < S) ls[tid].count[(p + 1) % 3] = 0;
                 }
-                if (!grid_sync(d.bar, d.gh, P.nblocks, &st.flag)) return;
+                if (!grid_sync(d, P.nblocks, st, TAG(2, j, l, p))) return;
 
                 // decide (identically in every block)
                 if (tid < S && (st.flags[tid] & F_SEARCH)) {
@@ -698,7 +729,7 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
                 const int cnt = __syncthreads_count(first);
                 if (tid == 0 && cnt) atomicAdd(&ls[s].kstar, static_cast<uint32_t>(cnt));
             }
-            if (!grid_sync(d.bar, d.gh, P.nblocks, &st.flag)) return;
+            if (!grid_sync(d, P.nblocks, st, TAG(3, j, l, 0))) return;
 
             // ------------------------------------------- cut-off: classify
             if (tid < S) {
@@ -719,18 +750,24 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
                 if (cut && st.cut_seg != s) {
                     // boundary bin: smallest b with (voxels in bins <= b) >= m_l
                     const uint32_t* h = hist + static_cast<long long>(s) * kHistBins;
-                    // kHistBins == 2 * kThreads: each thread owns bins [2 tid, 2 tid + 1]
-                    const int b0 = static_cast<int>(h[2 * tid]);
-                    const int b1 = static_cast<int>(h[2 * tid + 1]);
+                    constexpr int kPer = kHistBins / kThreads;  // bins owned by each thread
+                    int mine[kPer];
+                    int sum = 0;
+#pragma unroll
+                    for (int k = 0; k < kPer; ++k) {
+                        mine[k] = static_cast<int>(h[kPer * tid + k]);
+                        sum += mine[k];
+                    }
                     int tot;
-                    const int before = block_excl_scan<int>(b0 + b1, &tot, st.scan_i);
+                    int before = block_excl_scan<int>(sum, &tot, st.scan_i);
                     const int need = st.ml[s];
-                    if (before < need && before + b0 >= need) {
-                        st.cut_bin = 2 * tid;
-                        st.cut_below = before;
-                    } else if (before + b0 < need && before + b0 + b1 >= need) {
-                        st.cut_bin = 2 * tid + 1;
-                        st.cut_below = before + b0;
+#pragma unroll
+                    for (int k = 0; k < kPer; ++k) {
+                        if (before < need && before + mine[k] >= need) {
+                            st.cut_bin = kPer * tid + k;
+                            st.cut_below = before;
+                        }
+                        before += mine[k];
                     }
                     __syncthreads();
                     if (tid == 0) {
@@ -770,7 +807,7 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
                 }
                 __syncthreads();
             }
-            if (!grid_sync(d.bar, d.gh, P.nblocks, &st.flag)) return;
+            if (!grid_sync(d, P.nblocks, st, TAG(4, j, l, 0))) return;
 
             // ------------------------------- cut-off: resolve; shortfall count
             {
@@ -817,7 +854,7 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
                     clear_tables(d, st, S, true, true, true, gtid, gstride);
                     clear_layer_state(d, S, q ^ 1, gtid, gstride);
                 }
-                if (!grid_sync(d.bar, d.gh, P.nblocks, &st.flag)) return;
+                if (!grid_sync(d, P.nblocks, st, TAG(5, j, l, 0))) return;
             }
             // ------------------------------------------------ shortfall fill
             if (st.any) {
@@ -842,7 +879,7 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
                         __syncthreads();
                     }
                 }
-                if (!grid_sync(d.bar, d.gh, P.nblocks, &st.flag)) return;
+                if (!grid_sync(d, P.nblocks, st, TAG(6, j, l, 0))) return;
             }
         }
 
@@ -882,7 +919,7 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
             int tot;
             block_excl_scan<int>(cnt, &tot, st.scan_i);
             if (tid == 0) d.pcmp[blockIdx.x] = tot;
-            if (!grid_sync(d.bar, d.gh, P.nblocks, &st.flag)) return;
+            if (!grid_sync(d, P.nblocks, st, TAG(7, j, 0, 0))) return;
         }
         {
             int pre = 0;
@@ -922,7 +959,7 @@ __global__ void __launch_bounds__(kThreads, 2) hav_chain_kernel(const __grid_con
                 base += chunk;
             }
             if (!last_level) {
-                if (!grid_sync(d.bar, d.gh, P.nblocks, &st.flag)) return;
+                if (!grid_sync(d, P.nblocks, st, TAG(8, j, 0, 0))) return;
             }
         }
     }

@@ -63,8 +63,9 @@ _lib = None
 EXPORTS = [
     "hav_params_default", "hav_context_create", "hav_context_destroy", "hav_workspace_bytes",
     "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
-    "hav_count", "hav_status_string", "hav_sample_noalloc",
+    "hav_count", "hav_status_string", "hav_sample_noalloc", "hav_phase_times_get",
 ]
+HAV_FLAG_PHASE_TIMES = 1
 
 
 def _lib_or_none():
@@ -105,19 +106,23 @@ def load(path: str = LIB_PATH):
         L.hav_count.restype = C.c_int
         L.hav_status_string.argtypes = [C.c_int]
         L.hav_status_string.restype = C.c_char_p
+        L.hav_phase_times_get.argtypes = [vp, vp, P(C.c_uint64), P(C.c_uint32), i32]
+        L.hav_phase_times_get.restype = C.c_int32
         L.hav_sample_noalloc.argtypes = [vp, i64, i64, P(hav_params), vp, vp, vp]
         L.hav_sample_noalloc.restype = C.c_int
         _lib = L
         return L
 
 
-def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 1.0)) -> hav_params:
+def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 1.0),
+           flags=0) -> hav_params:
     p = hav_params()
     load().hav_params_default(C.byref(p))
     p.sigma_num, p.sigma_den = sigma
     p.t_max, p.layers, p.layer_ratio = t_max, layers, layer_ratio
     for a in range(3):
         p.aspect[a] = aspect[a]
+    p.flags = flags
     return p
 
 
@@ -238,6 +243,16 @@ def hav_trace_get(ctx: Context, num_records: int, stream=None):
             "s": np.array(r.s[:it], dtype=np.float32), "K": np.array(r.K[:it], dtype=np.int64),
         })
     return out
+
+
+def hav_phase_times_get(ctx: Context, max_records: int = 4096, stream=None):
+    """Phase timer of the last call made with flags=HAV_FLAG_PHASE_TIMES: list of (ns, tag)."""
+    t = (C.c_uint64 * max_records)()
+    g = (C.c_uint32 * max_records)()
+    w = load().hav_phase_times_get(ctx.handle, _stream_handle(stream), t, g, max_records)
+    if w < 0:
+        raise HavError(HAV_ERR_CUDA, "hav_phase_times_get")
+    return [(int(t[k]), int(g[k])) for k in range(w)]
 
 
 def hav_count(ctx: Context, points, s: float, aspect=(1.0, 1.0, 1.0), stream=None) -> int:

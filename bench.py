@@ -42,6 +42,9 @@ WORKLOADS = {
                     "n": None, "levels": [16384, 4096, 1024, 512]},
     "uniform-16k": {"desc": "16,384 uniform points in the KITTI range, one level to 4,096",
                     "n": 16384, "levels": [4096]},
+    "batch64": {"desc": "64 LiDAR clouds, N log-uniform in [20k, 200k], per cloud M = N/4 then N/16, "
+                        "one persistent segmented launch (also replayed from a CUDA graph) vs 64 per-cloud calls",
+                "n": None, "levels": None},
 }
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
@@ -217,6 +220,114 @@ def run_reference(args, world, rank):
     return 0
 
 
+# ----------------------------------------------------------------- batched arm
+def run_batched(args, world, rank, local):
+    """64 clouds per step: one hav_sample_batched launch, the same launch from a
+    CUDA graph, and 64 plain per-cloud hav_sample_levels calls, at identical outputs."""
+    import torch
+    import torch.distributed as dist
+    from paper_2305_14306_gb300 import hav
+
+    clouds = scenes.lidar_batch(64, seed=rank)
+    pts, offs = scenes.concat(clouds)
+    sizes = np.diff(offs)
+    seg_m = np.stack([sizes // 4, sizes // 16]).astype(np.int64)
+    total = int(offs[-1])
+    p = hav.params()
+    ctx = hav.Context(total, 64)
+    ctx1 = hav.Context(int(sizes.max()), 1)
+    stream = torch.cuda.current_stream()
+    d_pts = torch.from_numpy(pts).cuda()
+    outs = [torch.empty(int(seg_m[j].sum()), dtype=torch.int32, device="cuda") for j in range(2)]
+    per_outs = [[torch.empty(int(seg_m[j, s]), dtype=torch.int32, device="cuda") for j in range(2)]
+                for s in range(64)]
+    views = [d_pts[int(offs[s]):int(offs[s + 1])] for s in range(64)]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step_batched(strm=stream):
+        hav.hav_sample_batched(ctx, d_pts, offs, seg_m, p, outs=outs, stream=strm)
+
+    def step_per_cloud():
+        for s in range(64):
+            hav.hav_sample_levels(ctx1, views[s], seg_m[:, s], p, outs=per_outs[s], stream=stream)
+
+    for _ in range(args.warmup):
+        step_batched()
+        step_per_cloud()
+    st, per = hav.hav_status_get(ctx, 64)
+    if st != hav.HAV_OK:
+        raise SystemExit(f"batched status {st}")
+    # identical outputs, cloud by cloud
+    cut = [np.concatenate([[0], np.cumsum(seg_m[j])]) for j in range(2)]
+    for j in range(2):
+        got = outs[j].cpu().numpy()
+        for s in range(64):
+            if not np.array_equal(got[cut[j][s]:cut[j][s + 1]], per_outs[s][j].cpu().numpy()):
+                raise SystemExit(f"batched and per-cloud outputs differ at level {j}, cloud {s}")
+
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_batched(torch.cuda.current_stream())  # the capturing stream
+    graph.replay()
+    torch.cuda.synchronize()
+    st, _ = hav.hav_status_get(ctx, 64)
+    for j in range(2):
+        if st != hav.HAV_OK or not torch.equal(outs[j][:8], outs[j][:8]):
+            raise SystemExit("graph replay failed")
+
+    def time_it(fn, steps):
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ms.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ms]
+
+    gpu_index = local
+    steps = max(10, min(args.steps, 200))
+    clk = Clocks(gpu_index)
+    time.sleep(0.3)
+    ms_b = time_it(step_batched, steps)
+    ms_g = time_it(graph.replay, steps)
+    ms_p = time_it(step_per_cloud, max(5, steps // 4))
+    clocks = clk.stop()
+    tb = sum(ms_b) / 1e3
+    if world > 1:
+        t = torch.tensor([tb], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tb = float(t.item())
+    value = total * len(ms_b) * world / tb / 1e6
+    v_graph = total * len(ms_g) / (sum(ms_g) / 1e3) / 1e6
+    v_per = total * len(ms_p) / (sum(ms_p) / 1e3) / 1e6
+    if rank == 0:
+        srt = sorted(ms_b)
+        line = {
+            "metric": "input Mpoints/s", "value": value, "unit": "Mpoints/s", "n_gpus": world,
+            "steps": len(ms_b), "warmup": args.warmup, "ms_per_step": statistics.fmean(ms_b),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch64", "desc": WORKLOADS["batch64"]["desc"], "points": total,
+                       "segments": 64, "levels": 2, "l2": "flushed before every step (256 MB write)"},
+            "scenes_per_s": 64 * len(ms_b) / (sum(ms_b) / 1e3),
+            "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+            "graph": {"value": v_graph, "ms_per_step": statistics.fmean(ms_g)},
+            "per_cloud": {"value": v_per, "ms_per_step": statistics.fmean(ms_p),
+                          "launches_per_step": 64},
+            "speedup_vs_per_cloud": value / v_per,
+            "identical_outputs": True,
+            "gpu_launches": len(ms_b),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    ctx1.close()
+    return 0
+
+
 # ----------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -248,6 +359,11 @@ def main():
     if world > 1:
         dist.barrier()
     hav.load()
+    if args.workload == "batch64":
+        rc = run_batched(args, world, rank, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return rc
 
     w = WORKLOADS[args.workload]
     pts = make_scene(args.workload, seed=rank)

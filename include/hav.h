@@ -101,7 +101,7 @@ typedef struct CUstream_st* hav_stream;  /* same type as cudaStream_t */
 void hav_params_default(hav_params* p);
 
 /* Create a context on the CURRENT device with workspace for calls of up to
- * max_points points in total (all segments of a call, < 2^31) and up to
+ * max_points points in total (all segments of a call, < 2^30) and up to
  * max_segments segments (1..256).  Allocates device memory once; no call
  * allocates afterwards.  Returns HAV_ERR_NOMEM if cudaMalloc fails,
  * HAV_ERR_CUDA if the device cannot run the kernels (e.g. not sm_103). */

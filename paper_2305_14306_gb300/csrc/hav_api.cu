@@ -80,7 +80,7 @@ size_t hav_workspace_bytes(int64_t max_points, int32_t max_segments) {
 hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_segments) {
     if (!out) return HAV_ERR_INVALID;
     *out = nullptr;
-    if (max_points < 1 || max_points >= (1ll << 31)) return HAV_ERR_INVALID;
+    if (max_points < 1 || max_points >= (1ll << 30)) return HAV_ERR_INVALID;  // table slots index in 32 bits
     if (max_segments < 1 || max_segments > havk::kMaxSegments) return HAV_ERR_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HAV_ERR_CUDA;

@@ -1,0 +1,329 @@
+// Device helpers of the HAVSampler kernels: memory-order primitives, the
+// Eq. 2 voxel key, the Section 3.2 centre distance, hashing, block scans and
+// the bounded grid barrier.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hav_internal.h"
+
+namespace havk {
+
+constexpr unsigned long long kSpinNs = 2000000000ull;  // 2 s per barrier wait
+constexpr unsigned int kSpinIters = 1u << 26;
+
+// ------------------------------------------------------------------ memory ops
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_strong64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ unsigned ld_volatile_u(const unsigned* p) { return *(const volatile unsigned*)p; }
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Monotone map of binary32 onto uint32 (larger float -> larger code).
+__device__ __forceinline__ uint32_t enc_f(float x) {
+    uint32_t b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float dec_f(uint32_t e) {
+    return __uint_as_float((e & 0x80000000u) ? (e & 0x7fffffffu) : ~e);
+}
+
+// -------------------------------------------------------------------- hashing
+// Slot hash: a 64-bit mixer (xor-shift / multiply rounds).  The global table
+// indexes by its top bits, the block-local sets by its low bits.
+__device__ __forceinline__ unsigned long long slot_mix(unsigned long long k) {
+    k ^= k >> 32;
+    k *= 0xd6e8feb86659fd93ull;
+    k ^= k >> 32;
+    k *= 0xd6e8feb86659fd93ull;
+    k ^= k >> 32;
+    return k;
+}
+// Cut-off priority: the SplitMix64 output finaliser (Steele, Lea, Flood 2014).
+__device__ __forceinline__ unsigned long long priority(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------ Eq. 2 voxel keys
+// The cell indices are kept as integral binary32 values: floor(x / v) and
+// floor(min / v) are exact floats, and their difference u is exact whenever
+// the true u is below 2^21 (Sterbenz's lemma when both exceed 2^21 in size,
+// small exact integers otherwise); a true u >= 2^21 rounds to a value >= 2^21,
+// so the range test below is exact as well.
+struct Grid {
+    float v[3];
+    float fmin[3];
+};
+
+__device__ __forceinline__ bool floor_div(float x, float v, float* f) {
+    const float q = __fdiv_rn(x, v);
+    const float fl = floorf(q);
+    if (!(fabsf(fl) < 4.6e18f)) return false;  // |floor| < 2^62 and finite, as the key range requires
+    *f = fl;
+    return true;
+}
+
+__device__ inline bool make_grid(float s, const float r[3], const float mn[3], Grid* g) {
+    for (int a = 0; a < 3; ++a) {
+        const float v = __fmul_rn(s, r[a]);
+        if (!(v > 0.0f) || !isfinite(v)) return false;
+        g->v[a] = v;
+        if (!floor_div(mn[a], v, &g->fmin[a])) return false;
+    }
+    return true;
+}
+
+// key = u_x | u_y << 21 | u_z << 42 with u = floor(x / v) - floor(min / v).
+__device__ __forceinline__ bool cell_key(const float p[3], const Grid& g, unsigned long long* key,
+                                         float f[3]) {
+    unsigned long long k = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!floor_div(p[a], g.v[a], &f[a])) return false;
+        const float u = __fsub_rn(f[a], g.fmin[a]);
+        if (!(u >= 0.0f && u < 2097152.0f)) return false;
+        k |= static_cast<unsigned long long>(static_cast<unsigned>(u)) << (21 * a);
+    }
+    *key = k;
+    return true;
+}
+
+// Section 3.2: squared distance to the voxel centre v * (g + 0.5).
+__device__ __forceinline__ float centre_d2(const float p[3], const Grid& g, const float f[3]) {
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float c = __fmul_rn(g.v[a], __fadd_rn(f[a], 0.5f));
+        d[a] = __fsub_rn(p[a], c);
+    }
+    const float xy = __fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1]));
+    return __fadd_rn(xy, __fmul_rn(d[2], d[2]));
+}
+
+// Find or insert `key` in a global open-addressed table by linear probing;
+// *fresh tells whether this call inserted it.  Returns the slot, or -1 after
+// a full sweep (table full).
+__device__ __forceinline__ long long find_or_insert(unsigned long long* T, int cap_log2,
+                                                    unsigned long long key, bool* fresh) {
+    const unsigned long long mask = (1ull << cap_log2) - 1;
+    unsigned long long slot = slot_mix(key) >> (64 - cap_log2);
+    *fresh = false;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+        const unsigned long long cur = ld_strong64(T + slot);
+        if (cur == key) return static_cast<long long>(slot);
+        if (cur == kEmptyKey) {
+            const unsigned long long prev = atomicCAS(T + slot, kEmptyKey, key);
+            if (prev == kEmptyKey) {
+                *fresh = true;
+                return static_cast<long long>(slot);
+            }
+            if (prev == key) return static_cast<long long>(slot);
+        }
+        slot = (slot + 1) & mask;
+    }
+    return -1;
+}
+
+// find_or_insert for U keys at once: the first probe of every key is issued
+// before any result is used (memory-level parallelism); keys equal to
+// kEmptyKey are skipped.  slot[u] = -1 after a full sweep (table full).
+template <int U>
+__device__ __forceinline__ void find_or_insert_batch(unsigned long long* T, int cap_log2,
+                                                     const unsigned long long (&key)[U],
+                                                     long long (&slot)[U], bool (&fresh)[U]) {
+    const unsigned mask = static_cast<unsigned>((1ull << cap_log2) - 1);
+    unsigned sl[U];
+    unsigned long long cur[U];
+    // the home slot of every key is claimed with a compare-and-swap straight
+    // away (one round trip for a fresh key), all U of them before any result
+    // is used
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        sl[u] = static_cast<unsigned>(slot_mix(key[u]) >> (64 - cap_log2));
+        cur[u] = (key[u] != kEmptyKey) ? atomicCAS(T + sl[u], kEmptyKey, key[u]) : kEmptyKey;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        fresh[u] = false;
+        slot[u] = -1;
+        if (key[u] == kEmptyKey) continue;
+        if (cur[u] == kEmptyKey || cur[u] == key[u]) {
+            slot[u] = sl[u];
+            fresh[u] = (cur[u] == kEmptyKey);
+            continue;
+        }
+        // collision: linear probing from the next slot
+        unsigned s2 = (sl[u] + 1) & mask;
+        for (unsigned probe = 1; probe <= mask; ++probe) {
+            const unsigned long long c = ld_strong64(T + s2);
+            if (c == key[u]) {
+                slot[u] = s2;
+                break;
+            }
+            if (c == kEmptyKey) {
+                const unsigned long long prev = atomicCAS(T + s2, kEmptyKey, key[u]);
+                if (prev == kEmptyKey || prev == key[u]) {
+                    slot[u] = s2;
+                    fresh[u] = (prev == kEmptyKey);
+                    break;
+                }
+            }
+            s2 = (s2 + 1) & mask;
+        }
+    }
+}
+
+// Warp-aggregated append to a shared-memory list: every lane of the warp
+// calls it (flag false for lanes with nothing to add); returns the lane's
+// position, or -1.
+__device__ __forceinline__ int warp_append(bool flag, unsigned* counter) {
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (!m) return -1;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(counter, static_cast<unsigned>(__popc(m)));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return flag ? static_cast<int>(base + __popc(m & ((1u << lane) - 1u))) : -1;
+}
+
+// Block-local set in shared memory (a filter in front of the global table):
+// returns the slot holding `key` and whether this call inserted it, or -1
+// when the probe limit is reached (the caller then goes to the global table).
+template <int kSlots>
+__device__ __forceinline__ int smem_insert(unsigned long long* set, unsigned long long key, bool* fresh) {
+    unsigned slot = static_cast<unsigned>(slot_mix(key)) & (kSlots - 1);
+    *fresh = false;
+#pragma unroll 1
+    for (int probe = 0; probe < 32; ++probe) {
+        const unsigned long long cur = set[slot];
+        if (cur == key) return static_cast<int>(slot);
+        if (cur == kEmptyKey) {
+            const unsigned long long prev = atomicCAS(set + slot, kEmptyKey, key);
+            if (prev == kEmptyKey) {
+                *fresh = true;
+                return static_cast<int>(slot);
+            }
+            if (prev == key) return static_cast<int>(slot);
+        }
+        slot = (slot + 1) & (kSlots - 1);
+    }
+    return -1;
+}
+
+// Eq. 3 budget of layer l (0-based).
+__device__ __forceinline__ long long layer_budget(long long m, int layers, int ratio, int l) {
+    long long S = 0, pw = 1;
+    for (int i = 0; i < layers; ++i) {
+        S += pw;
+        pw *= ratio;
+    }
+    long long used = 0;
+    pw = 1;
+    for (int i = 0; i < layers - 1; ++i) {
+        const long long mi = m * pw / S;
+        if (i == l) return mi;
+        used += mi;
+        pw *= ratio;
+    }
+    return m - used;
+}
+
+// ------------------------------------------------------------ block helpers
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan over the block; *total receives the sum.  All threads call it.
+template <typename T>
+__device__ T block_excl_scan(T v, T* total, T* scratch /* >= 32 */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int kWarps = kThreads / 32;
+    T x = warp_incl_scan(v);
+    if (lane == 31) scratch[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        T w = (lane < kWarps) ? scratch[lane] : T(0);
+        w = warp_incl_scan(w);
+        scratch[lane] = w;
+    }
+    __syncthreads();
+    const T before = wid ? scratch[wid - 1] : T(0);
+    *total = scratch[kWarps - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// Sum over the block (every thread receives it).
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* scratch /* >= 32 */) {
+    const unsigned w = __reduce_add_sync(0xffffffffu, v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) scratch[wid] = w;
+    __syncthreads();
+    unsigned t = 0;
+#pragma unroll
+    for (int k = 0; k < kThreads / 32; ++k) t += scratch[k];
+    __syncthreads();
+    return t;
+}
+
+// Grid barrier with a bounded wait.  Arrival is a release reduction on a
+// counter that only grows within a launch (zeroed by the host before it);
+// barrier number e of the launch completes when the counter reaches
+// e * nblocks, so no block has to act as the last arriver.  Returns false
+// (for the whole block) when this or another block gave up; the caller then
+// leaves the kernel.
+__device__ inline bool grid_sync_impl(Barrier* bar, GlobalHdr* gh, unsigned nblocks, unsigned* epoch,
+                                      int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        const unsigned target = (*epoch + 1u) * nblocks;
+        *epoch += 1u;
+        // The block barrier above orders every thread's writes before this
+        // release; the acquire load below orders them before every thread's
+        // reads after the closing block barrier.  No further fence is needed.
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+        const unsigned long long t0 = globaltimer();
+        for (unsigned it = 0;; ++it) {
+            if (ld_acquire(&bar->count) >= target) break;
+            if ((it & 31) == 31) {
+                if (ld_volatile(&gh->abort) || it > kSpinIters || globaltimer() - t0 > kSpinNs) {
+                    fail = 1;
+                    break;
+                }
+            }
+            if (it > 64) __nanosleep(32);
+        }
+        if (fail) {
+            atomicExch(&gh->abort, 1);
+            atomicCAS(&gh->status, 0, static_cast<int>(HAV_ERR_TIMEOUT));
+        }
+        *s_flag = fail | ld_volatile(&gh->abort);
+    }
+    __syncthreads();
+    return *s_flag == 0;
+}
+
+}  // namespace havk

@@ -73,13 +73,16 @@ struct Layout {
     int64_t cand_slots;
     int64_t taken_words;
     size_t barrier, ghdr, seghdr, zero_bytes;  // [barrier, barrier+zero_bytes) zeroed per call
-    size_t lstate, hist, partial_sf, partial_cmp, trace, ptimes;
-    size_t pts[2], orig[2], taken[2];
+    size_t clean;          // 1 when every hash-table slot is empty (kept across calls)
+    size_t lstate, hist, partial_sf, partial_cmp, pitem, trace, ptimes;
+    size_t ord[2], orig[2], taken[2], wpre, dirty[2], bkt;
     size_t tabk[2], tabv, cand;
     size_t total;
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+constexpr int kMaxItems = kMaxBlocks + kMaxSegments;  // work items of one level
 
 inline Layout make_layout(int64_t N, int32_t S) {
     Layout L{};
@@ -99,17 +102,22 @@ inline Layout make_layout(int64_t N, int32_t S) {
     L.ghdr = take(sizeof(GlobalHdr));
     L.seghdr = take(sizeof(SegHdr) * S);
     L.zero_bytes = o - L.barrier;
+    L.clean = take(sizeof(uint32_t));
     L.lstate = take(sizeof(LayerState) * 2 * S);
     L.hist = take(sizeof(uint32_t) * 2 * S * kHistBins);
     L.partial_sf = take(sizeof(int32_t) * S * kMaxBlocks);
     L.partial_cmp = take(sizeof(int32_t) * kMaxBlocks);
+    L.pitem = take(sizeof(int32_t) * kMaxItems);
     L.trace = take(sizeof(hav_layer_trace) * kMaxLevels * S * kMaxLayers);
     L.ptimes = take(sizeof(unsigned long long) * 2 * kPhaseTimes);
     for (int b = 0; b < 2; ++b) {
-        L.pts[b] = take(sizeof(float) * 3 * N + 16);
+        L.ord[b] = take(16 * static_cast<size_t>(N) + 16);
         L.orig[b] = take(sizeof(int32_t) * N + 16);
         L.taken[b] = take(sizeof(uint32_t) * L.taken_words);
+        L.dirty[b] = take(sizeof(uint32_t) * N + 16);
     }
+    L.wpre = take(sizeof(uint32_t) * L.taken_words);
+    L.bkt = take(sizeof(uint32_t) * 2 * 4096);
     L.tabk[0] = take(sizeof(unsigned long long) * L.tab_slots);
     L.tabk[1] = take(sizeof(unsigned long long) * L.tab_slots);
     L.tabv = take(sizeof(unsigned long long) * L.tab_slots);

@@ -2,22 +2,33 @@
 // whole batched level chain.
 //
 // Per level j, for every segment (cloud) of the batch at once:
-//   bbox   : per-axis min/max and finiteness (bracket of the Section 3.3 search)
+//   bbox    per-axis min/max and finiteness (the bracket of the Section 3.3
+//           search); the level's points are laid out as float4 (x, y, z, g)
+//           with g the point's level index
+//   bucket  (one large cloud, first level) a counting sort by a 16^3 Morton
+//           cell of the bounding box, so that each block's share of the points
+//           is a compact region; later levels inherit the order
 //   layer l = 1..k (Section 3.4, Eq. 3):
-//     pass p : Cnt(P_l, s_p) by open-addressed insertion of Eq. 2 voxel keys
-//              (atomicCAS), counted per work tile; the bisection of Section 3.3
-//              is decided redundantly and identically by every block from the
-//              pass counts, so no block waits for a leader
-//     select : centre-closest representative per voxel at s* by a packed 64-bit
-//              atomicMin of (squared distance bits, point index) (Section 3.2);
+//     pass p   Cnt(P_l, s_p): Eq. 2 voxel keys are first deduplicated in a
+//              block-local shared-memory set, and only keys new to the block
+//              probe the global open-addressed table (atomicCAS); every fresh
+//              global insert is logged so the table can be cleaned slot by slot;
+//              the bisection of Section 3.3 is decided identically by every
+//              block from the pass counts (no leader, no host round trip)
+//     select   centre-closest representative per voxel at s*: a block-local
+//              shared-memory argmin of packed (d^2 bits, index), then one global
+//              64-bit atomicMin per block-distinct voxel (Section 3.2); the
 //              first touch of a slot feeds the cut-off histogram
-//     cut    : voxels below the boundary priority bin are taken, the boundary
-//              bin's voxels are ranked exactly (or the shortfall is filled)
-//   compact: taken bitmask -> ascending indices, composed to the segment's
-//            original cloud, plus the gather that feeds level j+1
+//     cut      voxels below the boundary priority bin are taken, the boundary
+//              bin's voxels are ranked exactly, or the shortfall is filled
+//   compact taken bitmask -> ascending indices composed to the segment's
+//           original cloud; the kept points are also gathered, in the current
+//           processing order, as the next level's input
 // Phases are separated by a grid barrier whose wait is bounded in time; a
-// timeout sets an abort flag that every block honours, and the host reads
-// HAV_ERR_TIMEOUT.  Every loop in this file has a fixed bound.
+// timeout sets an abort flag every block honours and the host reads
+// HAV_ERR_TIMEOUT.  Every loop has a fixed bound.  Control flow depends only
+// on values that no block can change while others read them, so every block
+// executes the same sequence of barriers.
 //
 // Arithmetic: voxel keys and distances use explicitly rounded binary32
 // intrinsics (__fdiv_rn, __fmul_rn, __fadd_rn, __fsub_rn), so the compiler
@@ -25,231 +36,27 @@
 
 #include <cuda_runtime.h>
 
+#include "hav_device.cuh"
 #include "hav_internal.h"
 
 namespace havk {
 namespace {
 
-#define TAG(phase, level, layer, pass) \
+#define TAG(phase, level, layer, pass)                                            \
     ((static_cast<unsigned>(phase) << 24) | (static_cast<unsigned>(level) << 16) | \
      (static_cast<unsigned>(layer) << 8) | static_cast<unsigned>(pass))
 
-constexpr unsigned long long kSpinNs = 2000000000ull;  // 2 s per barrier wait
-constexpr unsigned int kSpinIters = 1u << 26;
 static_assert(kHistBins % kThreads == 0, "the cut-off scan gives each thread whole bins");
+constexpr int kSetSlots = 16384;   // block-local dedupe set of a bisection pass (128 KB + 32 KB list)
+constexpr int kSelSlots = 8192;    // block-local argmin table of the selection (128 KB + 16 KB list)
+constexpr int kLocalItems = 8;     // work items one block can own in a level
+constexpr int kBucketMin = 1 << 17;
+constexpr size_t kDynSmem = 163840;
+constexpr int kInFlight = 4;       // points loaded ahead per thread in a pass
+constexpr int kProbes = 2;         // global first probes issued together per thread
+static_assert(kSetSlots % (kProbes * kThreads) == 0 && kSelSlots % (kProbes * kThreads) == 0,
+              "flush loops take kProbes slots per thread per step");
 
-// ------------------------------------------------------------------ memory ops
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_strong64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Monotone map of binary32 onto uint32 (larger float -> larger code).
-__device__ __forceinline__ uint32_t enc_f(float x) {
-    uint32_t b = __float_as_uint(x);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float dec_f(uint32_t e) {
-    return __uint_as_float((e & 0x80000000u) ? (e & 0x7fffffffu) : ~e);
-}
-
-// -------------------------------------------------------------------- hashing
-// Slot hash: a 64-bit mixer (xor-shift / multiply rounds), top bits index the table.
-__device__ __forceinline__ unsigned long long slot_mix(unsigned long long k) {
-    k ^= k >> 32;
-    k *= 0xd6e8feb86659fd93ull;
-    k ^= k >> 32;
-    k *= 0xd6e8feb86659fd93ull;
-    k ^= k >> 32;
-    return k;
-}
-// Cut-off priority: the SplitMix64 output finaliser (Steele, Lea, Flood 2014).
-__device__ __forceinline__ unsigned long long priority(unsigned long long z) {
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return z ^ (z >> 31);
-}
-
-// ------------------------------------------------------------ Eq. 2 voxel keys
-struct Grid {
-    float v[3];
-    long long fmin[3];
-};
-
-__device__ __forceinline__ bool floor_div(float x, float v, long long* F, float* f) {
-    float q = __fdiv_rn(x, v);
-    float fl = floorf(q);
-    if (!(fabsf(fl) < 4.6e18f)) return false;
-    *F = static_cast<long long>(fl);
-    *f = fl;
-    return true;
-}
-
-__device__ bool make_grid(float s, const float r[3], const float mn[3], Grid* g) {
-    for (int a = 0; a < 3; ++a) {
-        float v = __fmul_rn(s, r[a]);
-        if (!(v > 0.0f) || !isfinite(v)) return false;
-        g->v[a] = v;
-        float f;
-        if (!floor_div(mn[a], v, &g->fmin[a], &f)) return false;
-    }
-    return true;
-}
-
-// key = u_x | u_y << 21 | u_z << 42 with u = floor(x / v) - floor(min / v).
-__device__ __forceinline__ bool cell_key(const float p[3], const Grid& g,
-                                         unsigned long long* key, float f[3]) {
-    unsigned long long k = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        long long F;
-        if (!floor_div(p[a], g.v[a], &F, &f[a])) return false;
-        long long u = F - g.fmin[a];
-        if (u < 0 || u >= (1ll << 21)) return false;
-        k |= static_cast<unsigned long long>(u) << (21 * a);
-    }
-    *key = k;
-    return true;
-}
-
-// Section 3.2: squared distance to the voxel centre v * (g + 0.5).
-__device__ __forceinline__ float centre_d2(const float p[3], const Grid& g, const float f[3]) {
-    float d[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float c = __fmul_rn(g.v[a], __fadd_rn(f[a], 0.5f));
-        d[a] = __fsub_rn(p[a], c);
-    }
-    float xy = __fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1]));
-    return __fadd_rn(xy, __fmul_rn(d[2], d[2]));
-}
-
-// Find or insert `key` by linear probing; *fresh tells whether this call
-// inserted it.  Returns the slot, or -1 after a full sweep (table full).
-__device__ __forceinline__ long long find_or_insert(unsigned long long* T, int cap_log2,
-                                                    unsigned long long key, bool* fresh) {
-    const unsigned long long mask = (1ull << cap_log2) - 1;
-    unsigned long long slot = slot_mix(key) >> (64 - cap_log2);
-    *fresh = false;
-    for (unsigned long long probe = 0; probe <= mask; ++probe) {
-        unsigned long long cur = ld_strong64(T + slot);
-        if (cur == key) return static_cast<long long>(slot);
-        if (cur == kEmptyKey) {
-            unsigned long long prev = atomicCAS(T + slot, kEmptyKey, key);
-            if (prev == kEmptyKey) {
-                *fresh = true;
-                return static_cast<long long>(slot);
-            }
-            if (prev == key) return static_cast<long long>(slot);
-        }
-        slot = (slot + 1) & mask;
-    }
-    return -1;
-}
-
-// Eq. 3 budget of layer l (0-based).
-__device__ __forceinline__ long long layer_budget(long long m, int layers, int ratio, int l) {
-    long long S = 0, pw = 1;
-    for (int i = 0; i < layers; ++i) {
-        S += pw;
-        pw *= ratio;
-    }
-    long long used = 0;
-    pw = 1;
-    for (int i = 0; i < layers - 1; ++i) {
-        long long mi = m * pw / S;
-        if (i == l) return mi;
-        used += mi;
-        pw *= ratio;
-    }
-    return m - used;
-}
-
-// ------------------------------------------------------------ block helpers
-template <typename T>
-__device__ __forceinline__ T warp_incl_scan(T x) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
-// Exclusive scan over the block; *total receives the sum.  All threads call it.
-template <typename T>
-__device__ T block_excl_scan(T v, T* total, T* scratch /* >= 32 */) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int kWarps = kThreads / 32;
-    T x = warp_incl_scan(v);
-    if (lane == 31) scratch[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        T w = (lane < kWarps) ? scratch[lane] : T(0);
-        w = warp_incl_scan(w);
-        scratch[lane] = w;
-    }
-    __syncthreads();
-    T before = wid ? scratch[wid - 1] : T(0);
-    *total = scratch[kWarps - 1];
-    __syncthreads();
-    return before + x - v;
-}
-
-// Grid barrier with a bounded wait.  Arrival is a release reduction on a
-// counter that only grows within a launch (zeroed by the host before it);
-// barrier number e of the launch completes when the counter reaches
-// e * nblocks, so no block has to act as the last arriver.  Returns false
-// (for the whole block) when this or another block gave up; the caller then
-// leaves the kernel.
-__device__ bool grid_sync_impl(Barrier* bar, GlobalHdr* gh, unsigned nblocks, unsigned* epoch,
-                               int* s_flag) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int fail = 0;
-        const unsigned target = (*epoch + 1u) * nblocks;
-        *epoch += 1u;
-        __threadfence();
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
-        const unsigned long long t0 = globaltimer();
-        for (unsigned it = 0;; ++it) {
-            if (ld_acquire(&bar->count) >= target) break;
-            if ((it & 31) == 31) {
-                if (ld_volatile(&gh->abort) || it > kSpinIters || globaltimer() - t0 > kSpinNs) {
-                    fail = 1;
-                    break;
-                }
-            }
-            if (it > 64) __nanosleep(32);
-        }
-        if (fail) {
-            atomicExch(&gh->abort, 1);
-            atomicCAS(&gh->status, 0, static_cast<int>(HAV_ERR_TIMEOUT));
-        }
-        __threadfence();
-        *s_flag = fail | ld_volatile(&gh->abort);
-    }
-    __syncthreads();
-    return *s_flag == 0;
-}
-
-// ------------------------------------------------------------------ state
 enum : int { F_ACTIVE = 1, F_SEARCH = 2, F_ACCEPT = 4 };
 
 struct Smem {
@@ -260,35 +67,40 @@ struct Smem {
     int n[kMaxSegments];
     int m[kMaxSegments];
     int cap_log2[kMaxSegments];
-    int tile0[kMaxSegments + 1];
-    int stile0[kMaxSegments + 1];
+    int item0[kMaxSegments + 1];
     int err[kMaxSegments];
     // bracket
     float mn[kMaxSegments][3];
+    float mx[kMaxSegments][3];
     float s_hi[kMaxSegments];
     // controller of the current layer
     float lo[kMaxSegments], hi[kMaxSegments], s_cur[kMaxSegments], s_star[kMaxSegments];
     Grid grid[kMaxSegments];
     int ml[kMaxSegments];
     int kmax[kMaxSegments];
-    int iters[kMaxSegments];
     int flags[kMaxSegments];
     int sel[kMaxSegments];
     int kstar[kMaxSegments];
     int cprefix[kMaxSegments + 1];
+    // per-block logs of fresh global inserts, one per (table parity, owned item)
+    int dcnt[2][kLocalItems];
     // scratch
     long long scan_ll[32];
     int scan_i[32];
+    unsigned scan_u[32];
     float redf[6][32];
     unsigned epoch;
+    unsigned list_n;
+    int set_clean;  // 1 when every slot of the block set is empty
     int ntimes;
+    int was_clean;
     int cut_seg;
     int cut_bin;
     int cut_below;
     int flag;
     int any;
-    int tiles_total;
-    int stiles_total;
+    int items_total;
+    int chunk;
     long long n_level;
     long long m_total;
 };
@@ -297,23 +109,27 @@ struct Dev {
     Barrier* bar;
     GlobalHdr* gh;
     SegHdr* sh;
-    LayerState* ls;       // [2][S]
-    uint32_t* hist;       // [2][S][kHistBins]
-    int32_t* psf;         // [S][kMaxBlocks]
-    int32_t* pcmp;        // [kMaxBlocks]
-    hav_layer_trace* tr;  // [L][S][kMaxLayers]
-    float* pts[2];
-    int32_t* orig[2];
-    uint32_t* taken[2];
+    unsigned* clean;
+    LayerState* ls;        // [2][S]
+    uint32_t* hist;        // [2][S][kHistBins]
+    int32_t* psf;          // [S][kMaxBlocks]
+    int32_t* pcmp;         // [kMaxBlocks]
+    int32_t* pitem;        // [kMaxItems]
+    hav_layer_trace* tr;   // [L][S][kMaxLayers]
+    float4* ord[2];        // level input in processing order: x, y, z, level index
+    int32_t* orig[2];      // original (segment-local) index by level index
+    uint32_t* taken[2];    // by level index
+    uint32_t* wpre;        // block-local prefix of taken bits per mask word
+    uint32_t* dirty[2];    // fresh-insert logs, item-owned ranges of the level index space
+    uint32_t* bkt;         // [2][4096] bucket counts, bucket cursors
     unsigned long long* tk[2];
     unsigned long long* tv;
     Cand* cand;
-    unsigned long long* ptimes;  // [2 * cap] (globaltimer ns, tag) pairs, or null
+    unsigned long long* ptimes;
     int ptimes_cap;
 };
 
 // Barrier plus, when phase timing is on, a (time, tag) record from block 0.
-// tag = phase << 24 | level << 16 | layer << 8 | pass.
 __device__ __forceinline__ bool grid_sync(Dev& d, unsigned nblocks, Smem& st, unsigned tag) {
     const bool ok = grid_sync_impl(d.bar, d.gh, nblocks, &st.epoch, &st.flag);
     if (d.ptimes && blockIdx.x == 0 && threadIdx.x == 0 && st.ntimes < d.ptimes_cap) {
@@ -329,53 +145,79 @@ __device__ __forceinline__ void seg_error(Dev& d, int s, int code) {
     atomicCAS(&d.gh->status, 0, code);
 }
 
-__device__ __forceinline__ int find_seg(const int* prefix, int S, int t) {
-    // largest s with prefix[s] <= t (prefix has S+1 entries, prefix[0] = 0)
+// largest s with prefix[s] <= t (prefix has S+1 entries, prefix[0] = 0)
+template <typename T>
+__device__ __forceinline__ int find_seg(const T* prefix, int S, long long t) {
     int lo = 0, hi = S;
     while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
+        const int mid = (lo + hi) >> 1;
         if (prefix[mid] <= t) lo = mid; else hi = mid;
     }
     return lo;
 }
 
-__device__ __forceinline__ int find_seg_ll(const long long* prefix, int S, long long g) {
-    int lo = 0, hi = S;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= g) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ bool is_taken(const uint32_t* tk, long long g) {
+__device__ __forceinline__ bool is_taken(const uint32_t* tk, int g) {
     return (tk[g >> 5] >> (g & 31)) & 1u;
 }
-__device__ __forceinline__ void set_taken(uint32_t* tk, long long g) {
+__device__ __forceinline__ void set_taken(uint32_t* tk, int g) {
     atomicOr(&tk[g >> 5], 1u << (g & 31));
 }
 
-__device__ __forceinline__ void load_point(const float* pts, long long g, float p[3]) {
-    const float* q = pts + 3 * g;
-    p[0] = q[0];
-    p[1] = q[1];
-    p[2] = q[2];
+template <typename T>
+__device__ __forceinline__ void fill(T* p, long long count, T v, long long gtid, long long gstride) {
+    for (long long i = gtid; i < count; i += gstride) p[i] = v;
+}
+
+__device__ __forceinline__ void clear_layer_state(Dev& d, int S, int q, long long gtid, long long gstride) {
+    fill<uint32_t>(reinterpret_cast<uint32_t*>(d.ls + q * S), static_cast<long long>(S) * (sizeof(LayerState) / 4),
+                   0u, gtid, gstride);
+    fill<uint32_t>(d.hist + static_cast<long long>(q) * S * kHistBins, static_cast<long long>(S) * kHistBins, 0u,
+                   gtid, gstride);
+}
+
+// Item `it` of the level: segment and point range [a, b).
+// (A level holds fewer than 2^30 points, so point indices fit 32 bits.)
+__device__ __forceinline__ int item_range(const Smem& st, int S, int it, int* a, int* b) {
+    const int s = find_seg(st.item0, S, it);
+    const int k = it - st.item0[s];
+    *a = static_cast<int>(st.off[s]) + k * st.chunk;
+    const int e = *a + st.chunk;
+    const int end = static_cast<int>(st.off[s]) + st.n[s];
+    *b = e < end ? e : end;
+    return s;
+}
+
+// 16^3 Morton cell of a point inside its segment's bounding box (layout only).
+__device__ __forceinline__ unsigned bucket_of(const float p[3], const float mn[3], const float mx[3]) {
+    unsigned c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float e = mx[a] - mn[a];
+        int q = (e > 0.0f) ? static_cast<int>((p[a] - mn[a]) / e * 16.0f) : 0;
+        q = q < 0 ? 0 : (q > 15 ? 15 : q);
+        c[a] = static_cast<unsigned>(q);
+    }
+    unsigned id = 0;
+#pragma unroll
+    for (int bit = 0; bit < 4; ++bit)
+        id |= (((c[0] >> bit) & 1u) << (3 * bit)) | (((c[1] >> bit) & 1u) << (3 * bit + 1)) |
+              (((c[2] >> bit) & 1u) << (3 * bit + 2));
+    return id;
 }
 
 // Level layout of every segment, computed identically by every block.
 __device__ void level_setup(const Plan& P, int j, Smem& st) {
     const int S = P.S;
     const int s = threadIdx.x;
-    long long n = 0, C = 0, tiles = 0, stiles = 0;
+    long long n = 0, C = 0, mm = 0;
     int lg = kMinCapLog2;
     if (s < S) {
         n = (j == 0) ? (P.off0[s + 1] - P.off0[s]) : P.m[j - 1][s];
+        mm = P.m[j][s];
         while ((1ll << lg) < 2 * n) ++lg;
         C = 1ll << lg;
-        tiles = (n + kTile - 1) / kTile;
-        stiles = (C + kSlotTile - 1) / kSlotTile;
         st.n[s] = static_cast<int>(n);
-        st.m[s] = P.m[j][s];
+        st.m[s] = static_cast<int>(mm);
         st.cap_log2[s] = lg;
     }
     long long tot;
@@ -385,57 +227,39 @@ __device__ void level_setup(const Plan& P, int j, Smem& st) {
         st.off[S] = tot;
         st.n_level = tot;
     }
-    o = block_excl_scan<long long>(s < S ? static_cast<long long>(P.m[j][s]) : 0ll, &tot, st.scan_ll);
-    if (s == 0) st.m_total = tot;
+    __syncthreads();
+    const long long nl = st.n_level;
+    long long chunk = (nl + P.nblocks - 1) / P.nblocks;
+    if (chunk < kThreads) chunk = kThreads;
+    o = block_excl_scan<long long>(mm, &tot, st.scan_ll);
+    if (s == 0) {
+        st.m_total = tot;
+        st.chunk = static_cast<int>(chunk);
+    }
     o = block_excl_scan<long long>(C, &tot, st.scan_ll);
     if (s < S) {
         st.tab_off[s] = o;
         st.cand_off[s] = o / 2;
     }
-    o = block_excl_scan<long long>(tiles, &tot, st.scan_ll);
-    if (s < S) st.tile0[s] = static_cast<int>(o);
+    const long long items = (s < S) ? (n + chunk - 1) / chunk : 0;
+    o = block_excl_scan<long long>(items, &tot, st.scan_ll);
+    if (s < S) st.item0[s] = static_cast<int>(o);
     if (s == 0) {
-        st.tile0[S] = static_cast<int>(tot);
-        st.tiles_total = static_cast<int>(tot);
+        st.item0[S] = static_cast<int>(tot);
+        st.items_total = static_cast<int>(tot);
     }
-    o = block_excl_scan<long long>(stiles, &tot, st.scan_ll);
-    if (s < S) st.stile0[s] = static_cast<int>(o);
-    if (s == 0) {
-        st.stile0[S] = static_cast<int>(tot);
-        st.stiles_total = static_cast<int>(tot);
-    }
+    if (s < 2 * kLocalItems) st.dcnt[s / kLocalItems][s % kLocalItems] = 0;
     __syncthreads();
-}
-
-// Grid-strided fill of [0, count) with a value.
-template <typename T>
-__device__ __forceinline__ void fill(T* p, long long count, T v, long long gtid, long long gstride) {
-    for (long long i = gtid; i < count; i += gstride) p[i] = v;
-}
-
-// Table region of one segment (slots [tab_off, tab_off + C)).
-__device__ __forceinline__ void clear_tables(Dev& d, const Smem& st, int S, bool k0, bool k1, bool v,
-                                             long long gtid, long long gstride) {
-    const long long total = st.tab_off[S - 1] + (1ll << st.cap_log2[S - 1]);
-    if (k0) fill<unsigned long long>(d.tk[0], total, kEmptyKey, gtid, gstride);
-    if (k1) fill<unsigned long long>(d.tk[1], total, kEmptyKey, gtid, gstride);
-    if (v) fill<unsigned long long>(d.tv, total, kEmptyVal, gtid, gstride);
-}
-
-__device__ __forceinline__ void clear_layer_state(Dev& d, int S, int q, long long gtid, long long gstride) {
-    LayerState* ls = d.ls + q * S;
-    fill<uint32_t>(reinterpret_cast<uint32_t*>(ls), static_cast<long long>(S) * (sizeof(LayerState) / 4),
-                   0u, gtid, gstride);
-    fill<uint32_t>(d.hist + static_cast<long long>(q) * S * kHistBins,
-                   static_cast<long long>(S) * kHistBins, 0u, gtid, gstride);
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_constant__ Plan P) {
     __shared__ Smem st;
+    extern __shared__ __align__(16) unsigned char dyn[];
     const int S = P.S;
     const int tid = threadIdx.x;
+    const unsigned nb = static_cast<unsigned>(P.nblocks);
     const long long gtid = static_cast<long long>(blockIdx.x) * kThreads + tid;
     const long long gstride = static_cast<long long>(P.nblocks) * kThreads;
 
@@ -444,24 +268,32 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
     d.bar = reinterpret_cast<Barrier*>(ws + P.lay.barrier);
     d.gh = reinterpret_cast<GlobalHdr*>(ws + P.lay.ghdr);
     d.sh = reinterpret_cast<SegHdr*>(ws + P.lay.seghdr);
+    d.clean = reinterpret_cast<unsigned*>(ws + P.lay.clean);
     d.ls = reinterpret_cast<LayerState*>(ws + P.lay.lstate);
     d.hist = reinterpret_cast<uint32_t*>(ws + P.lay.hist);
     d.psf = reinterpret_cast<int32_t*>(ws + P.lay.partial_sf);
     d.pcmp = reinterpret_cast<int32_t*>(ws + P.lay.partial_cmp);
+    d.pitem = reinterpret_cast<int32_t*>(ws + P.lay.pitem);
     d.tr = reinterpret_cast<hav_layer_trace*>(ws + P.lay.trace);
     for (int b = 0; b < 2; ++b) {
-        d.pts[b] = reinterpret_cast<float*>(ws + P.lay.pts[b]);
+        d.ord[b] = reinterpret_cast<float4*>(ws + P.lay.ord[b]);
         d.orig[b] = reinterpret_cast<int32_t*>(ws + P.lay.orig[b]);
         d.taken[b] = reinterpret_cast<uint32_t*>(ws + P.lay.taken[b]);
+        d.dirty[b] = reinterpret_cast<uint32_t*>(ws + P.lay.dirty[b]);
         d.tk[b] = reinterpret_cast<unsigned long long*>(ws + P.lay.tabk[b]);
     }
+    d.wpre = reinterpret_cast<uint32_t*>(ws + P.lay.wpre);
+    d.bkt = reinterpret_cast<uint32_t*>(ws + P.lay.bkt);
     d.tv = reinterpret_cast<unsigned long long*>(ws + P.lay.tabv);
     d.cand = reinterpret_cast<Cand*>(ws + P.lay.cand);
     d.ptimes = P.ptimes;
     d.ptimes_cap = P.ptimes_cap;
     if (tid == 0) {
         st.epoch = 0u;
+        st.set_clean = 0;
         st.ntimes = 0;
+        // every block reads this before block 0 may change it (after the first barrier)
+        st.was_clean = static_cast<int>(ld_volatile_u(d.clean));
         if (d.ptimes && blockIdx.x == 0) {
             d.ptimes[0] = globaltimer();
             d.ptimes[1] = 0;
@@ -472,39 +304,52 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
 
     for (int j = 0; j < P.L; ++j) {
         level_setup(P, j, st);
-        const float* pts = (j == 0) ? P.points : d.pts[(j - 1) & 1];
+        float4* ord = d.ord[j & 1];
         const int32_t* orig_in = (j == 0) ? nullptr : d.orig[(j - 1) & 1];
         uint32_t* taken = d.taken[j & 1];
         const long long NL = st.n_level;
+        const bool bucketing = (j == 0 && S == 1 && NL >= kBucketMin);
 
-        // ---------------------------------------------------- bbox + clears
+        // ------------------------------------------------ bbox, layout, clears
         {
             const int par = j & 1;
-            for (int t = blockIdx.x; t < st.tiles_total; t += P.nblocks) {
-                const int s = find_seg(st.tile0, S, t);
-                const long long g = st.off[s] + static_cast<long long>(t - st.tile0[s]) * kTile + tid;
-                const bool in = g < st.off[s] + st.n[s];
+            for (int it = blockIdx.x; it < st.items_total; it += nb) {
+                int a, b;
+                const int s = item_range(st, S, it, &a, &b);
                 float mnv[3] = {INFINITY, INFINITY, INFINITY}, mxv[3] = {-INFINITY, -INFINITY, -INFINITY};
                 int bad = 0;
-                if (in) {
+                for (int i = a + tid; i < b; i += kThreads) {
                     float p[3];
-                    load_point(pts, g, p);
-                    for (int a = 0; a < 3; ++a) {
-                        if (!isfinite(p[a])) bad = 1;
-                        mnv[a] = p[a];
-                        mxv[a] = p[a];
+                    if (j == 0) {
+                        const float* q = P.points + 3 * i;
+                        p[0] = q[0];
+                        p[1] = q[1];
+                        p[2] = q[2];
+                        if (!bucketing) ord[i] = make_float4(p[0], p[1], p[2], __int_as_float(static_cast<int>(i)));
+                    } else {
+                        const float4 q = ord[i];
+                        p[0] = q.x;
+                        p[1] = q.y;
+                        p[2] = q.z;
+                    }
+#pragma unroll
+                    for (int a3 = 0; a3 < 3; ++a3) {
+                        if (!isfinite(p[a3])) bad = 1;
+                        mnv[a3] = fminf(mnv[a3], p[a3]);
+                        mxv[a3] = fmaxf(mxv[a3], p[a3]);
                     }
                 }
-                for (int a = 0; a < 3; ++a) {
+#pragma unroll
+                for (int a3 = 0; a3 < 3; ++a3) {
                     for (int o = 16; o > 0; o >>= 1) {
-                        mnv[a] = fminf(mnv[a], __shfl_xor_sync(0xffffffffu, mnv[a], o));
-                        mxv[a] = fmaxf(mxv[a], __shfl_xor_sync(0xffffffffu, mxv[a], o));
+                        mnv[a3] = fminf(mnv[a3], __shfl_xor_sync(0xffffffffu, mnv[a3], o));
+                        mxv[a3] = fmaxf(mxv[a3], __shfl_xor_sync(0xffffffffu, mxv[a3], o));
                     }
                 }
                 if ((tid & 31) == 0) {
-                    for (int a = 0; a < 3; ++a) {
-                        st.redf[a][tid >> 5] = mnv[a];
-                        st.redf[3 + a][tid >> 5] = mxv[a];
+                    for (int a3 = 0; a3 < 3; ++a3) {
+                        st.redf[a3][tid >> 5] = mnv[a3];
+                        st.redf[3 + a3][tid >> 5] = mxv[a3];
                     }
                 }
                 bad = __syncthreads_or(bad);
@@ -524,10 +369,17 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 __syncthreads();
             }
             fill<uint32_t>(taken, NL / 32 + 1, 0u, gtid, gstride);
-            clear_tables(d, st, S, true, true, true, gtid, gstride);
             clear_layer_state(d, S, 0, gtid, gstride);
             clear_layer_state(d, S, 1, gtid, gstride);
-            if (!grid_sync(d, P.nblocks, st, TAG(1, j, 0, 0))) return;
+            if (j == 0 && !st.was_clean) {
+                // first call on this workspace, or the previous call was cut short
+                fill<unsigned long long>(d.tk[0], P.lay.tab_slots, kEmptyKey, gtid, gstride);
+                fill<unsigned long long>(d.tk[1], P.lay.tab_slots, kEmptyKey, gtid, gstride);
+                fill<unsigned long long>(d.tv, P.lay.tab_slots, kEmptyVal, gtid, gstride);
+            }
+            if (bucketing) fill<uint32_t>(d.bkt, 2 * 4096, 0u, gtid, gstride);
+            if (!grid_sync(d, nb, st, TAG(1, j, 0, 0))) return;
+            if (j == 0 && blockIdx.x == 0 && tid == 0) *(volatile unsigned*)d.clean = 0u;
         }
 
         // --------------------------------------------------- search bracket
@@ -542,9 +394,10 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             for (int a = 0; a < 3; ++a) {
                 float mn = dec_f(~d.sh[tid].bbox[par][a]);
                 float mx = dec_f(d.sh[tid].bbox[par][3 + a]);
-                if (st.n[tid] == 0) mn = mx = 0.0f;
+                if (st.n[tid] == 0 || err) mn = mx = 0.0f;
                 st.mn[tid][a] = mn;
-                float e = __fsub_rn(mx, mn);
+                st.mx[tid][a] = mx;
+                const float e = __fsub_rn(mx, mn);
                 s_hi = fmaxf(s_hi, __fdiv_rn(e, P.aspect[a]));
             }
             if (s_hi == 0.0f) s_hi = 1.0f;
@@ -557,8 +410,62 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
         }
         __syncthreads();
 
+        // ---------------------------------------- bucketing (one large cloud)
+        if (bucketing) {
+            if (tid == 0) st.set_clean = 0;
+            uint32_t* h = reinterpret_cast<uint32_t*>(dyn);          // this block's counts
+            uint32_t* hb = reinterpret_cast<uint32_t*>(dyn) + 4096;  // global bucket bases
+            for (int b = tid; b < 4096; b += kThreads) h[b] = 0u;
+            __syncthreads();
+            for (int it = blockIdx.x; it < st.items_total; it += nb) {
+                int a, b;
+                item_range(st, S, it, &a, &b);
+                for (int i = a + tid; i < b; i += kThreads) {
+                    const float* q = P.points + 3 * i;
+                    const float p[3] = {q[0], q[1], q[2]};
+                    atomicAdd(&h[bucket_of(p, st.mn[0], st.mx[0])], 1u);
+                }
+            }
+            __syncthreads();
+            for (int b = tid; b < 4096; b += kThreads)
+                if (h[b]) atomicAdd(&d.bkt[b], h[b]);
+            if (!grid_sync(d, nb, st, TAG(9, j, 0, 0))) return;
+            {
+                // exclusive prefix over the 4096 global counts (4 bins per thread)
+                uint32_t c4[4], sum = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    c4[k] = d.bkt[4 * tid + k];
+                    sum += c4[k];
+                }
+                unsigned tot;
+                unsigned before = block_excl_scan<unsigned>(sum, &tot, st.scan_u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    hb[4 * tid + k] = before;
+                    before += c4[k];
+                }
+                __syncthreads();
+                for (int b = tid; b < 4096; b += kThreads)
+                    if (h[b]) h[b] = hb[b] + atomicAdd(&d.bkt[4096 + b], h[b]);
+                __syncthreads();
+                for (int it = blockIdx.x; it < st.items_total; it += nb) {
+                    int a, b;
+                    item_range(st, S, it, &a, &b);
+                    for (int i = a + tid; i < b; i += kThreads) {
+                        const float* q = P.points + 3 * i;
+                        const float p[3] = {q[0], q[1], q[2]};
+                        const unsigned r = atomicAdd(&h[bucket_of(p, st.mn[0], st.mx[0])], 1u);
+                        if (r < static_cast<unsigned>(NL))
+                            ord[r] = make_float4(p[0], p[1], p[2], __int_as_float(static_cast<int>(i)));
+                    }
+                }
+            }
+            if (!grid_sync(d, nb, st, TAG(10, j, 0, 0))) return;
+        }
+
         // ------------------------------------------------------------ layers
-        long long taken_before = 0;  // per-thread copy for thread s (budget sum of earlier layers)
+        long long taken_before = 0;  // thread s: budgets of earlier layers of segment s
         for (int l = 0; l < P.layers; ++l) {
             const int q = l & 1;
             LayerState* ls = d.ls + q * S;
@@ -573,7 +480,6 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 st.kmax[tid] = static_cast<int>(kmax);
                 st.lo[tid] = 0.0f;
                 st.hi[tid] = st.s_hi[tid];
-                st.iters[tid] = 0;
                 st.sel[tid] = 0;
                 st.kstar[tid] = 0;
                 int fl = active ? F_ACTIVE : 0;
@@ -582,6 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     st.s_star[tid] = st.s_hi[tid];
                     if (!make_grid(st.s_star[tid], P.aspect, st.mn[tid], &st.grid[tid])) {
                         seg_error(d, tid, HAV_ERR_RANGE);
+                        st.err[tid] = HAV_ERR_RANGE;
                         fl = 0;
                     }
                 }
@@ -616,43 +523,115 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     }
                 }
                 if (!__syncthreads_or(searching)) break;
+                const int X = p & 1, Y = X ^ 1;
+                unsigned long long* TX = d.tk[X];
+                unsigned long long* TY = d.tk[Y];
 
-                unsigned long long* T = d.tk[p & 1];
-                for (int t = blockIdx.x; t < st.tiles_total; t += P.nblocks) {
-                    const int s = find_seg(st.tile0, S, t);
-                    if (!(st.flags[s] & F_SEARCH)) continue;  // uniform across the block
-                    const long long g = st.off[s] + static_cast<long long>(t - st.tile0[s]) * kTile + tid;
-                    int fresh = 0;
-                    if (g < st.off[s] + st.n[s] && !(use_mask && is_taken(taken, g))) {
-                        float p3[3], f[3];
-                        unsigned long long key;
-                        load_point(pts, g, p3);
-                        if (cell_key(p3, st.grid[s], &key, f)) {
-                            bool fr;
-                            long long slot = find_or_insert(T + st.tab_off[s], st.cap_log2[s], key, &fr);
-                            if (slot < 0) seg_error(d, s, HAV_ERR_TABLE_FULL);
-                            fresh = fr;
-                        } else {
-                            seg_error(d, s, HAV_ERR_RANGE);
+                // clean the other table, slot by slot, from this block's logs
+                if (p >= 1) {
+                    int li = 0;
+                    for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
+                        int a, b;
+                        const int s = item_range(st, S, it, &a, &b);
+                        if (!(st.flags[s] & F_SEARCH)) continue;
+                        const int c = st.dcnt[Y][li];
+                        for (int k = tid; k < c; k += kThreads) TY[d.dirty[Y][a + k]] = kEmptyKey;
+                    }
+                    __syncthreads();
+                    li = 0;
+                    for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
+                        const int s = find_seg(st.item0, S, it);
+                        if (tid == 0 && (st.flags[s] & F_SEARCH)) st.dcnt[Y][li] = 0;
+                    }
+                }
+
+                // Cnt(P_l, s_p): (a) every point's key into the block set, the keys new
+                // to the block listed densely; (b) the listed keys into the global
+                // table, kProbes compare-and-swaps in flight per thread
+                unsigned long long* set = reinterpret_cast<unsigned long long*>(dyn);
+                unsigned short* list = reinterpret_cast<unsigned short*>(dyn + kSetSlots * sizeof(unsigned long long));
+                int li = 0;
+                for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
+                    int a, b;
+                    const int s = item_range(st, S, it, &a, &b);
+                    if (!(st.flags[s] & F_SEARCH)) continue;
+                    if (!st.set_clean)  // otherwise every slot is already empty
+                        for (int k = tid; k < kSetSlots; k += kThreads) set[k] = kEmptyKey;
+                    if (tid == 0) st.list_n = 0u;
+                    __syncthreads();
+                    const Grid& G = st.grid[s];
+                    unsigned long long* T = TX + st.tab_off[s];
+                    const int cap = st.cap_log2[s];
+                    unsigned fresh = 0;
+                    int bad = 0;
+                    auto log_fresh = [&](long long slot) {
+                        ++fresh;
+                        const int k = atomicAdd(&st.dcnt[X][li], 1);
+                        d.dirty[X][a + k] = static_cast<uint32_t>(st.tab_off[s] + slot);
+                    };
+                    const int lane = tid & 31;
+                    for (int base = a + (tid - lane); base < b; base += kInFlight * kThreads) {  // warp-uniform
+                        float4 q4[kInFlight];
+#pragma unroll
+                        for (int u = 0; u < kInFlight; ++u) {
+                            const int i = base + lane + u * kThreads;
+                            q4[u] = (i < b) ? ord[i] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                        }
+#pragma unroll
+                        for (int u = 0; u < kInFlight; ++u) {
+                            const int g = __float_as_int(q4[u].w);
+                            bool ok = g >= 0 && !(use_mask && is_taken(taken, g));
+                            unsigned long long key = kEmptyKey;
+                            if (ok) {
+                                const float p3[3] = {q4[u].x, q4[u].y, q4[u].z};
+                                float f[3];
+                                if (!cell_key(p3, G, &key, f)) {
+                                    bad = HAV_ERR_RANGE;
+                                    ok = false;
+                                }
+                            }
+                            int r = -2;
+                            bool nw = false;
+                            if (ok) r = smem_insert<kSetSlots>(set, key, &nw);
+                            const int pos = warp_append(r >= 0 && nw, &st.list_n);
+                            if (pos >= 0) list[pos] = static_cast<unsigned short>(r);
+                            if (r == -1) {  // block set saturated: straight to the global table
+                                bool fr;
+                                const long long slot = find_or_insert(T, cap, key, &fr);
+                                if (slot < 0) bad = HAV_ERR_TABLE_FULL;
+                                else if (fr) log_fresh(slot);
+                            }
                         }
                     }
-                    const int cnt = __syncthreads_count(fresh);
-                    if (tid == 0 && cnt) atomicAdd(&ls[s].count[p % 3], static_cast<uint32_t>(cnt));
-                }
-                // the other table is the next pass's: clear it (it is clean before pass 1)
-                if (p >= 1) {
-                    unsigned long long* T2 = d.tk[(p + 1) & 1];
-                    for (int t = blockIdx.x; t < st.stiles_total; t += P.nblocks) {
-                        const int s = find_seg(st.stile0, S, t);
-                        if (!(st.flags[s] & F_SEARCH)) continue;
-                        const long long a0 = static_cast<long long>(t - st.stile0[s]) * kSlotTile;
-                        const long long C = 1ll << st.cap_log2[s];
-                        for (long long i = a0 + tid; i < a0 + kSlotTile && i < C; i += kThreads)
-                            T2[st.tab_off[s] + i] = kEmptyKey;
+                    __syncthreads();
+                    const int nl = static_cast<int>(st.list_n);
+                    for (int k0 = tid; k0 < nl; k0 += kProbes * kThreads) {
+                        unsigned long long key[kProbes];
+                        long long slot[kProbes];
+                        bool fr[kProbes];
+#pragma unroll
+                        for (int u = 0; u < kProbes; ++u) {
+                            const int k = k0 + u * kThreads;
+                            key[u] = (k < nl) ? set[list[k]] : kEmptyKey;
+                        }
+                        find_or_insert_batch<kProbes>(T, cap, key, slot, fr);
+#pragma unroll
+                        for (int u = 0; u < kProbes; ++u) {
+                            if (key[u] == kEmptyKey) continue;
+                            if (slot[u] < 0) bad = HAV_ERR_TABLE_FULL;
+                            else if (fr[u]) log_fresh(slot[u]);
+                        }
                     }
-                    if (blockIdx.x == 0 && tid < S) ls[tid].count[(p + 1) % 3] = 0;
+                    // empty the set again: exactly the listed slots are occupied
+                    __syncthreads();
+                    for (int k = tid; k < nl; k += kThreads) set[list[k]] = kEmptyKey;
+                    if (tid == 0) st.set_clean = 1;
+                    if (bad) seg_error(d, s, bad);
+                    const unsigned total = block_sum(fresh, st.scan_u);
+                    if (tid == 0 && total) atomicAdd(&ls[s].count[p % 3], total);
                 }
-                if (!grid_sync(d, P.nblocks, st, TAG(2, j, l, p))) return;
+                if (p >= 1 && blockIdx.x == 0 && tid < S) ls[tid].count[(p + 1) % 3] = 0;
+                if (!grid_sync(d, nb, st, TAG(2, j, l, p))) return;
 
                 // decide (identically in every block)
                 if (tid < S && (st.flags[tid] & F_SEARCH)) {
@@ -664,20 +643,19 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         tr->K[p] = K;
                         tr->iters = p + 1;
                     }
-                    st.iters[tid] = p + 1;
                     if (K > st.kmax[tid]) {
                         st.lo[tid] = s;
                     } else if (K < st.ml[tid]) {
                         st.hi[tid] = s;
                     } else {
                         st.s_star[tid] = s;
-                        st.sel[tid] = p & 1;
+                        st.sel[tid] = X;
                         st.flags[tid] = F_ACTIVE | F_ACCEPT;
                     }
                 }
                 __syncthreads();
             }
-            // no acceptance within t_max steps
+            // no acceptance within t_max steps: the table cleaned in the last pass is used
             if (tid < S && (st.flags[tid] & F_SEARCH)) {
                 const float s = (st.lo[tid] > 0.0f) ? st.lo[tid] : st.hi[tid];
                 st.s_star[tid] = s;
@@ -688,48 +666,114 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     st.flags[tid] = 0;
                     st.err[tid] = HAV_ERR_RANGE;
                 }
-            } else if (tid < S && (st.flags[tid] & F_ACCEPT)) {
-                make_grid(st.s_star[tid], P.aspect, st.mn[tid], &st.grid[tid]);  // succeeded at that s
             }
             __syncthreads();
 
             // ------------------------------------- Section 3.2 selection at s*
-            for (int t = blockIdx.x; t < st.tiles_total; t += P.nblocks) {
-                const int s = find_seg(st.tile0, S, t);
-                if (!(st.flags[s] & F_ACTIVE)) continue;
-                const long long g = st.off[s] + static_cast<long long>(t - st.tile0[s]) * kTile + tid;
-                int first = 0;
-                if (g < st.off[s] + st.n[s] && !(use_mask && is_taken(taken, g))) {
-                    float p3[3], f[3];
-                    unsigned long long key;
-                    load_point(pts, g, p3);
-                    if (cell_key(p3, st.grid[s], &key, f)) {
-                        bool fr;
-                        const long long slot =
-                            find_or_insert(d.tk[st.sel[s]] + st.tab_off[s], st.cap_log2[s], key, &fr);
-                        if (slot >= 0) {
-                            const float d2 = centre_d2(p3, st.grid[s], f);
-                            const unsigned long long packed =
-                                (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) |
-                                static_cast<unsigned long long>(g);
-                            const unsigned long long old = atomicMin(d.tv + st.tab_off[s] + slot, packed);
-                            if (old == kEmptyVal) {
-                                first = 1;
-                                atomicAdd(&hist[static_cast<long long>(s) * kHistBins +
-                                                (priority(key) >> (64 - kHistBits))],
-                                          1u);
-                            }
-                        } else {
-                            seg_error(d, s, HAV_ERR_TABLE_FULL);
-                        }
-                    } else {
-                        seg_error(d, s, HAV_ERR_RANGE);
+            {
+                if (tid == 0) st.set_clean = 0;
+                unsigned long long* skey = reinterpret_cast<unsigned long long*>(dyn);
+                unsigned long long* sval = skey + kSelSlots;
+                unsigned short* list = reinterpret_cast<unsigned short*>(sval + kSelSlots);
+                int li = 0;
+                for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
+                    int a, b;
+                    const int s = item_range(st, S, it, &a, &b);
+                    if (!(st.flags[s] & F_ACTIVE)) continue;
+                    for (int k = tid; k < kSelSlots; k += kThreads) {
+                        skey[k] = kEmptyKey;
+                        sval[k] = kEmptyVal;
                     }
+                    if (tid == 0) st.list_n = 0u;
+                    __syncthreads();
+                    const Grid& G = st.grid[s];
+                    const int sel = st.sel[s];
+                    unsigned long long* T = d.tk[sel] + st.tab_off[s];
+                    unsigned long long* V = d.tv + st.tab_off[s];
+                    const int cap = st.cap_log2[s];
+                    unsigned first = 0;
+                    int bad = 0;
+                    auto global_min = [&](unsigned long long key, long long slot, bool fr, unsigned long long packed) {
+                        if (fr) {
+                            const int k = atomicAdd(&st.dcnt[sel][li], 1);
+                            d.dirty[sel][a + k] = static_cast<uint32_t>(st.tab_off[s] + slot);
+                        }
+                        if (atomicMin(V + slot, packed) == kEmptyVal) {
+                            ++first;
+                            atomicAdd(&hist[static_cast<long long>(s) * kHistBins + (priority(key) >> (64 - kHistBits))],
+                                      1u);
+                        }
+                    };
+                    const int lane = tid & 31;
+                    for (int base = a + (tid - lane); base < b; base += kInFlight * kThreads) {  // warp-uniform
+                        float4 q4[kInFlight];
+#pragma unroll
+                        for (int u = 0; u < kInFlight; ++u) {
+                            const int i = base + lane + u * kThreads;
+                            q4[u] = (i < b) ? ord[i] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                        }
+#pragma unroll
+                        for (int u = 0; u < kInFlight; ++u) {
+                            const int g = __float_as_int(q4[u].w);
+                            bool ok = g >= 0 && !(use_mask && is_taken(taken, g));
+                            unsigned long long key = kEmptyKey, packed = kEmptyVal;
+                            if (ok) {
+                                const float p3[3] = {q4[u].x, q4[u].y, q4[u].z};
+                                float f[3];
+                                if (cell_key(p3, G, &key, f)) {
+                                    const float d2 = centre_d2(p3, G, f);
+                                    packed = (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) |
+                                             static_cast<unsigned>(g);
+                                } else {
+                                    bad = HAV_ERR_RANGE;
+                                    ok = false;
+                                }
+                            }
+                            int r = -2;
+                            bool nw = false;
+                            if (ok) r = smem_insert<kSelSlots>(skey, key, &nw);
+                            const int pos = warp_append(r >= 0 && nw, &st.list_n);
+                            if (pos >= 0) list[pos] = static_cast<unsigned short>(r);
+                            if (r >= 0) {
+                                atomicMin(sval + r, packed);
+                            } else if (r == -1) {  // block table saturated: straight to the global table
+                                bool fr;
+                                const long long slot = find_or_insert(T, cap, key, &fr);
+                                if (slot < 0) bad = HAV_ERR_TABLE_FULL;
+                                else global_min(key, slot, fr, packed);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    const int nl = static_cast<int>(st.list_n);
+                    for (int k0 = tid; k0 < nl; k0 += kProbes * kThreads) {
+                        unsigned long long key[kProbes];
+                        long long slot[kProbes];
+                        bool fr[kProbes];
+                        int sidx[kProbes];
+#pragma unroll
+                        for (int u = 0; u < kProbes; ++u) {
+                            const int k = k0 + u * kThreads;
+                            sidx[u] = (k < nl) ? static_cast<int>(list[k]) : 0;
+                            key[u] = (k < nl) ? skey[sidx[u]] : kEmptyKey;
+                        }
+                        find_or_insert_batch<kProbes>(T, cap, key, slot, fr);
+#pragma unroll
+                        for (int u = 0; u < kProbes; ++u) {
+                            if (key[u] == kEmptyKey) continue;
+                            if (slot[u] < 0) {
+                                bad = HAV_ERR_TABLE_FULL;
+                                continue;
+                            }
+                            global_min(key[u], slot[u], fr[u], sval[sidx[u]]);
+                        }
+                    }
+                    if (bad) seg_error(d, s, bad);
+                    const unsigned total = block_sum(first, st.scan_u);
+                    if (tid == 0 && total) atomicAdd(&ls[s].kstar, total);
                 }
-                const int cnt = __syncthreads_count(first);
-                if (tid == 0 && cnt) atomicAdd(&ls[s].kstar, static_cast<uint32_t>(cnt));
             }
-            if (!grid_sync(d, P.nblocks, st, TAG(3, j, l, 0))) return;
+            if (!grid_sync(d, nb, st, TAG(3, j, l, 0))) return;
 
             // ------------------------------------------- cut-off: classify
             if (tid < S) {
@@ -743,73 +787,77 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             }
             if (tid == 0) st.cut_seg = -1;
             __syncthreads();
-            for (int t = blockIdx.x; t < st.stiles_total; t += P.nblocks) {
-                const int s = find_seg(st.stile0, S, t);
-                if (!(st.flags[s] & F_ACTIVE)) continue;
-                const bool cut = st.kstar[s] > st.ml[s];
-                if (cut && st.cut_seg != s) {
-                    // boundary bin: smallest b with (voxels in bins <= b) >= m_l
-                    const uint32_t* h = hist + static_cast<long long>(s) * kHistBins;
-                    constexpr int kPer = kHistBins / kThreads;  // bins owned by each thread
-                    int mine[kPer];
-                    int sum = 0;
+            {
+                int li = 0;
+                for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
+                    int a, b;
+                    const int s = item_range(st, S, it, &a, &b);
+                    if (!(st.flags[s] & F_ACTIVE)) continue;
+                    const bool cut = st.kstar[s] > st.ml[s];
+                    if (cut && st.cut_seg != s) {
+                        // boundary bin: smallest b with (voxels in bins <= b) >= m_l
+                        const uint32_t* h = hist + static_cast<long long>(s) * kHistBins;
+                        constexpr int kPer = kHistBins / kThreads;
+                        int mine[kPer];
+                        int sum = 0;
 #pragma unroll
-                    for (int k = 0; k < kPer; ++k) {
-                        mine[k] = static_cast<int>(h[kPer * tid + k]);
-                        sum += mine[k];
-                    }
-                    int tot;
-                    int before = block_excl_scan<int>(sum, &tot, st.scan_i);
-                    const int need = st.ml[s];
-#pragma unroll
-                    for (int k = 0; k < kPer; ++k) {
-                        if (before < need && before + mine[k] >= need) {
-                            st.cut_bin = kPer * tid + k;
-                            st.cut_below = before;
+                        for (int k = 0; k < kPer; ++k) {
+                            mine[k] = static_cast<int>(h[kPer * tid + k]);
+                            sum += mine[k];
                         }
-                        before += mine[k];
+                        int tot;
+                        int before = block_excl_scan<int>(sum, &tot, st.scan_i);
+                        const int need = st.ml[s];
+#pragma unroll
+                        for (int k = 0; k < kPer; ++k) {
+                            if (before < need && before + mine[k] >= need) {
+                                st.cut_bin = kPer * tid + k;
+                                st.cut_below = before;
+                            }
+                            before += mine[k];
+                        }
+                        __syncthreads();
+                        if (tid == 0) {
+                            st.cut_seg = s;
+                            ls[s].bin = st.cut_bin;
+                            ls[s].below = static_cast<uint32_t>(st.cut_below);
+                        }
+                        __syncthreads();
                     }
-                    __syncthreads();
-                    if (tid == 0) {
-                        st.cut_seg = s;
-                        ls[s].bin = st.cut_bin;
-                        ls[s].below = static_cast<uint32_t>(st.cut_below);
+                    const int sel = st.sel[s];
+                    const int c = st.dcnt[sel][li];
+                    const long long C = 1ll << st.cap_log2[s];
+                    const int bin = st.cut_bin;
+                    for (int k = tid; k < c; k += kThreads) {
+                        const uint32_t gs = d.dirty[sel][a + k];
+                        const unsigned long long v = d.tv[gs];
+                        if (v == kEmptyVal) continue;
+                        const long long g = static_cast<long long>(v & 0xffffffffull);
+                        if (!cut) {
+                            set_taken(taken, g);
+                            continue;
+                        }
+                        const unsigned long long h = priority(d.tk[sel][gs]);
+                        const int hb = static_cast<int>(h >> (64 - kHistBits));
+                        if (hb < bin) {
+                            set_taken(taken, g);
+                        } else if (hb == bin) {
+                            const uint32_t ci = atomicAdd(&ls[s].cand, 1u);
+                            if (static_cast<long long>(ci) < (C >> 1)) {
+                                Cand* cd = d.cand + st.cand_off[s] + ci;
+                                cd->h = h;
+                                cd->g = static_cast<uint32_t>(g);
+                            } else {
+                                seg_error(d, s, HAV_ERR_TABLE_FULL);
+                            }
+                        }
                     }
                     __syncthreads();
                 }
-                const long long a0 = static_cast<long long>(t - st.stile0[s]) * kSlotTile;
-                const long long C = 1ll << st.cap_log2[s];
-                const unsigned long long* TK = d.tk[st.sel[s]] + st.tab_off[s];
-                const unsigned long long* TV = d.tv + st.tab_off[s];
-                const int bin = st.cut_bin;
-                for (long long i = a0 + tid; i < a0 + kSlotTile && i < C; i += kThreads) {
-                    const unsigned long long v = TV[i];
-                    if (v == kEmptyVal) continue;
-                    const long long g = static_cast<long long>(v & 0xffffffffull);
-                    if (!cut) {
-                        set_taken(taken, g);
-                        continue;
-                    }
-                    const unsigned long long h = priority(TK[i]);
-                    const int b = static_cast<int>(h >> (64 - kHistBits));
-                    if (b < bin) {
-                        set_taken(taken, g);
-                    } else if (b == bin) {
-                        const uint32_t c = atomicAdd(&ls[s].cand, 1u);
-                        if (static_cast<long long>(c) < (C >> 1)) {
-                            Cand* cd = d.cand + st.cand_off[s] + c;
-                            cd->h = h;
-                            cd->g = static_cast<uint32_t>(g);
-                        } else {
-                            seg_error(d, s, HAV_ERR_TABLE_FULL);
-                        }
-                    }
-                }
-                __syncthreads();
             }
-            if (!grid_sync(d, P.nblocks, st, TAG(4, j, l, 0))) return;
+            if (!grid_sync(d, nb, st, TAG(4, j, l, 0))) return;
 
-            // ------------------------------- cut-off: resolve; shortfall count
+            // --------------- cut-off: resolve; shortfall count; clean the tables
             {
                 int c = 0;
                 if (tid < S && (st.flags[tid] & F_ACTIVE) && st.kstar[tid] > st.ml[tid])
@@ -820,7 +868,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 if (tid == 0) st.cprefix[S] = ctot;
                 __syncthreads();
                 for (long long w = gtid; w < ctot; w += gstride) {
-                    const int s = find_seg(st.cprefix, S, static_cast<int>(w));
+                    const int s = find_seg(st.cprefix, S, w);
                     const int jdx = static_cast<int>(w) - st.cprefix[s];
                     const int cs = st.cprefix[s + 1] - st.cprefix[s];
                     const Cand* base = d.cand + st.cand_off[s];
@@ -830,10 +878,9 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     const int r = st.ml[s] - static_cast<int>(ls[s].below);
                     if (rank < r) set_taken(taken, base[jdx].g);
                 }
-                // shortfall: count the untaken points in this block's slice of each such segment
                 int sf = 0;
                 if (tid < S && (st.flags[tid] & F_ACTIVE) && st.kstar[tid] < st.ml[tid]) sf = 1;
-                st.any = 0;
+                if (tid == 0) st.any = 0;
                 __syncthreads();
                 if (sf) st.any = 1;
                 __syncthreads();
@@ -841,8 +888,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     for (int s = 0; s < S; ++s) {
                         if (!((st.flags[s] & F_ACTIVE) && st.kstar[s] < st.ml[s])) continue;
                         const long long n = st.n[s];
-                        const long long a = st.off[s] + n * blockIdx.x / P.nblocks;
-                        const long long b = st.off[s] + n * (blockIdx.x + 1) / P.nblocks;
+                        const long long a = st.off[s] + n * blockIdx.x / nb;
+                        const long long b = st.off[s] + n * (blockIdx.x + 1) / nb;
                         int cnt = 0;
                         for (long long g = a + tid; g < b; g += kThreads) cnt += is_taken(taken, g) ? 0 : 1;
                         int tot;
@@ -850,11 +897,28 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         if (tid == 0) d.psf[static_cast<long long>(s) * kMaxBlocks + blockIdx.x] = tot;
                     }
                 }
-                if (l + 1 < P.layers) {
-                    clear_tables(d, st, S, true, true, true, gtid, gstride);
-                    clear_layer_state(d, S, q ^ 1, gtid, gstride);
+                // both key tables and the value table back to empty, slot by slot
+                int li = 0;
+                for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
+                    int a, b;
+                    const int s = item_range(st, S, it, &a, &b);
+                    const bool sel_v = (st.flags[s] & F_ACTIVE) != 0;
+                    for (int t = 0; t < 2; ++t) {
+                        const int c2 = st.dcnt[t][li];
+                        const bool v_too = sel_v && st.sel[s] == t;
+                        for (int k = tid; k < c2; k += kThreads) {
+                            const uint32_t gs = d.dirty[t][a + k];
+                            d.tk[t][gs] = kEmptyKey;
+                            if (v_too) d.tv[gs] = kEmptyVal;
+                        }
+                    }
                 }
-                if (!grid_sync(d, P.nblocks, st, TAG(5, j, l, 0))) return;
+                __syncthreads();
+                if (tid < 2 * kLocalItems) st.dcnt[tid / kLocalItems][tid % kLocalItems] = 0;
+                if (l + 1 < P.layers) clear_layer_state(d, S, q ^ 1, gtid, gstride);
+                if (!grid_sync(d, nb, st, TAG(5, j, l, 0))) return;
+                if (j + 1 == P.L && l + 1 == P.layers && blockIdx.x == 0 && tid == 0)
+                    *(volatile unsigned*)d.clean = 1u;  // every table slot is empty again
             }
             // ------------------------------------------------ shortfall fill
             if (st.any) {
@@ -867,8 +931,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     block_excl_scan<int>(pre, &tot, st.scan_i);
                     int budget = (st.ml[s] - st.kstar[s]) - tot;
                     const long long n = st.n[s];
-                    const long long a = st.off[s] + n * blockIdx.x / P.nblocks;
-                    const long long b = st.off[s] + n * (blockIdx.x + 1) / P.nblocks;
+                    const long long a = st.off[s] + n * blockIdx.x / nb;
+                    const long long b = st.off[s] + n * (blockIdx.x + 1) / nb;
                     for (long long g0 = a; g0 < b && budget > 0; g0 += kThreads) {
                         const long long g = g0 + tid;
                         const int free_pt = (g < b && !is_taken(taken, g)) ? 1 : 0;
@@ -876,15 +940,14 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         const int rank = block_excl_scan<int>(free_pt, &chunk, st.scan_i);
                         if (free_pt && rank < budget) set_taken(taken, g);
                         budget -= chunk;
-                        __syncthreads();
                     }
                 }
-                if (!grid_sync(d, P.nblocks, st, TAG(6, j, l, 0))) return;
+                if (!grid_sync(d, nb, st, TAG(6, j, l, 0))) return;
             }
         }
 
         // ---------------------------------------------------- compaction
-        // Segments in error take their first m points so every other
+        // Segments in error take their first m points, so every other
         // segment's output positions stay exact.
         if (tid < S) st.err[tid] = ld_volatile(&d.sh[tid].status);
         if (tid == 0) st.any = 0;
@@ -892,16 +955,17 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
         if (tid < S && st.err[tid]) st.any = 1;
         __syncthreads();
         const bool any_err = st.any != 0;
+        const bool last_level = (j + 1 == P.L);
         const long long W = (NL + 31) / 32;
-        const long long wb = W * blockIdx.x / P.nblocks;
-        const long long we = W * (blockIdx.x + 1) / P.nblocks;
+        const long long wb = W * blockIdx.x / nb;
+        const long long we = W * (blockIdx.x + 1) / nb;
         auto eff_word = [&](long long w) -> uint32_t {
             uint32_t bits = taken[w];
             const long long g0 = w * 32;
             if (g0 + 32 > NL) bits &= (NL - g0 >= 32) ? 0xffffffffu : ((1u << (NL - g0)) - 1u);
             if (any_err) {
                 for (int k = 0; k < 32 && g0 + k < NL; ++k) {
-                    const int s = find_seg_ll(st.off, S, g0 + k);
+                    const int s = find_seg(st.off, S, g0 + k);
                     if (st.err[s]) {
                         const bool on = (g0 + k - st.off[s]) < st.m[s];
                         bits = on ? (bits | (1u << k)) : (bits & ~(1u << k));
@@ -910,56 +974,122 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             }
             return bits;
         };
+        auto eff_taken = [&](int s, long long g) -> bool {
+            if (st.err[s]) return (g - st.off[s]) < st.m[s];
+            return is_taken(taken, g);
+        };
         {
             // level j+1 accumulates its bounding box in the parity level j-1 used
             if (blockIdx.x == 0 && tid < S)
                 for (int a = 0; a < 6; ++a) d.sh[tid].bbox[(j + 1) & 1][a] = 0u;
-            int cnt = 0;
-            for (long long w = wb + tid; w < we; w += kThreads) cnt += __popc(eff_word(w));
-            int tot;
-            block_excl_scan<int>(cnt, &tot, st.scan_i);
-            if (tid == 0) d.pcmp[blockIdx.x] = tot;
-            if (!grid_sync(d, P.nblocks, st, TAG(7, j, 0, 0))) return;
-        }
-        {
-            int pre = 0;
-            for (int b = tid; b < static_cast<int>(blockIdx.x); b += kThreads) pre += d.pcmp[b];
-            int base;
-            block_excl_scan<int>(pre, &base, st.scan_i);
-            const bool last_level = (j + 1 == P.L);
-            float* pts_out = d.pts[j & 1];
-            int32_t* orig_out = d.orig[j & 1];
-            int32_t* out = P.out[j];
+            // ascending order: per-word block-local prefixes and the block total
+            unsigned run = 0;
             for (long long w0 = wb; w0 < we; w0 += kThreads) {
                 const long long w = w0 + tid;
-                const uint32_t bits = (w < we) ? eff_word(w) : 0u;
-                int chunk;
-                const int rank = block_excl_scan<int>(__popc(bits), &chunk, st.scan_i);
-                long long pos = static_cast<long long>(base) + rank;
-                uint32_t b = bits;
-                while (b) {
-                    const int k = __ffs(b) - 1;
-                    b &= b - 1;
+                const unsigned c = (w < we) ? __popc(eff_word(w)) : 0u;
+                unsigned tot;
+                const unsigned before = block_excl_scan<unsigned>(c, &tot, st.scan_u);
+                if (w < we) d.wpre[w] = run + before;
+                run += tot;
+            }
+            if (tid == 0) d.pcmp[blockIdx.x] = static_cast<int32_t>(run);
+            // processing order: kept points per owned item
+            if (!last_level) {
+                for (int it = blockIdx.x; it < st.items_total; it += nb) {
+                    int a, b;
+                    const int s = item_range(st, S, it, &a, &b);
+                    unsigned c = 0;
+                    for (int i = a + tid; i < b; i += kThreads)
+                        c += eff_taken(s, __float_as_int(ord[i].w)) ? 1u : 0u;
+                    const unsigned tot = block_sum(c, st.scan_u);
+                    if (tid == 0) d.pitem[it] = static_cast<int32_t>(tot);
+                }
+            }
+            if (!grid_sync(d, nb, st, TAG(7, j, 0, 0))) return;
+        }
+        {
+            // prefixes of every block's count and (next level) every item's count
+            if (tid == 0) st.set_clean = 0;
+            int* pre_blk = reinterpret_cast<int*>(dyn);
+            int* pre_item = pre_blk + kMaxBlocks;
+            {
+                int run = 0;
+                for (int b0 = 0; b0 < static_cast<int>(nb); b0 += kThreads) {
+                    const int b = b0 + tid;
+                    const int c = (b < static_cast<int>(nb)) ? d.pcmp[b] : 0;
+                    int tot;
+                    const int before = block_excl_scan<int>(c, &tot, st.scan_i);
+                    if (b < static_cast<int>(nb)) pre_blk[b] = run + before;
+                    run += tot;
+                }
+                if (!last_level) {
+                    run = 0;
+                    for (int i0 = 0; i0 < st.items_total; i0 += kThreads) {
+                        const int it = i0 + tid;
+                        const int c = (it < st.items_total) ? d.pitem[it] : 0;
+                        int tot;
+                        const int before = block_excl_scan<int>(c, &tot, st.scan_i);
+                        if (it < st.items_total) pre_item[it] = run + before;
+                        run += tot;
+                    }
+                }
+                __syncthreads();
+            }
+            // ascending position of a kept level index
+            auto pos_asc = [&](long long g) -> long long {
+                const long long w = g >> 5;
+                long long b = (w * static_cast<long long>(nb)) / W;
+                while (b + 1 < static_cast<long long>(nb) && W * (b + 1) / nb <= w) ++b;
+                while (b > 0 && W * b / nb > w) --b;
+                const uint32_t below = eff_word(w) & ((1u << (g & 31)) - 1u);
+                return static_cast<long long>(pre_blk[b]) + d.wpre[w] + __popc(below);
+            };
+            int32_t* out = P.out[j];
+            int32_t* orig_out = d.orig[j & 1];
+            for (long long w = wb + tid; w < we; w += kThreads) {
+                uint32_t bits = eff_word(w);
+                long long pos = static_cast<long long>(pre_blk[blockIdx.x]) + d.wpre[w];
+                while (bits) {
+                    const int k = __ffs(bits) - 1;
+                    bits &= bits - 1;
                     const long long g = w * 32 + k;
                     if (pos >= st.m_total) {  // cannot happen: every segment takes exactly m
                         atomicCAS(&d.gh->status, 0, static_cast<int>(HAV_ERR_TABLE_FULL));
                         break;
                     }
-                    const int s = find_seg_ll(st.off, S, g);
+                    const int s = find_seg(st.off, S, g);
                     const int32_t oi = orig_in ? orig_in[g] : static_cast<int32_t>(g - st.off[s]);
                     out[pos] = oi;
-                    if (!last_level) {
-                        pts_out[3 * pos + 0] = pts[3 * g + 0];
-                        pts_out[3 * pos + 1] = pts[3 * g + 1];
-                        pts_out[3 * pos + 2] = pts[3 * g + 2];
-                        orig_out[pos] = oi;
-                    }
+                    if (!last_level) orig_out[pos] = oi;
                     ++pos;
                 }
-                base += chunk;
             }
             if (!last_level) {
-                if (!grid_sync(d, P.nblocks, st, TAG(8, j, 0, 0))) return;
+                float4* ord_out = d.ord[(j + 1) & 1];
+                for (int it = blockIdx.x; it < st.items_total; it += nb) {
+                    int a, b;
+                    const int s = item_range(st, S, it, &a, &b);
+                    long long base = pre_item[it];
+                    for (int i0 = a; i0 < b; i0 += kThreads) {
+                        const int i = i0 + tid;
+                        float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        int keep = 0;
+                        if (i < b) {
+                            q4 = ord[i];
+                            keep = eff_taken(s, __float_as_int(q4.w)) ? 1 : 0;
+                        }
+                        int tot;
+                        const int rank = block_excl_scan<int>(keep, &tot, st.scan_i);
+                        if (keep) {
+                            const long long pos2 = base + rank;
+                            const long long ng = pos_asc(__float_as_int(q4.w));
+                            if (pos2 < st.m_total && ng < st.m_total)
+                                ord_out[pos2] = make_float4(q4.x, q4.y, q4.z, __int_as_float(static_cast<int>(ng)));
+                        }
+                        base += tot;
+                    }
+                }
+                if (!grid_sync(d, nb, st, TAG(8, j, 0, 0))) return;
             }
         }
     }
@@ -1028,7 +1158,10 @@ __global__ void fill_u64(unsigned long long* p, long long n, unsigned long long 
 int max_coresident_blocks(int device) {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hav_chain_kernel, kThreads, 0) != cudaSuccess)
+    if (cudaFuncSetAttribute(hav_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kDynSmem)) != cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hav_chain_kernel, kThreads, kDynSmem) != cudaSuccess)
         return -1;
     long long nb = static_cast<long long>(sms) * per_sm;
     if (nb > kMaxBlocks) nb = kMaxBlocks;
@@ -1039,7 +1172,7 @@ int launch_chain(const Plan& plan, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(plan.nblocks));
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kDynSmem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -1051,7 +1184,8 @@ int launch_chain(const Plan& plan, cudaStream_t stream) {
 
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3], unsigned char* ws,
                  const Layout& lay, int64_t* K, cudaStream_t stream) {
-    // scratch: reuse the level-0 table region and the segment header area
+    // scratch: the level-0 key table; it is left dirty, so the next sampler
+    // call on this workspace starts with a full clear
     int cap_log2 = kMinCapLog2;
     while ((1ll << cap_log2) < 2 * n) ++cap_log2;
     if ((1ll << cap_log2) > lay.tab_slots) return HAV_ERR_NOMEM;
@@ -1060,11 +1194,12 @@ int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
     uint32_t* enc6 = reinterpret_cast<uint32_t*>(scratch);
     unsigned long long* dK = reinterpret_cast<unsigned long long*>(scratch + 64);
     int* derr = reinterpret_cast<int*>(scratch + 128);
+    if (cudaMemsetAsync(ws + lay.clean, 0, sizeof(unsigned), stream) != cudaSuccess) return HAV_ERR_CUDA;
     if (cudaMemsetAsync(scratch, 0, 256, stream) != cudaSuccess) return HAV_ERR_CUDA;
     fill_u64<<<1024, 256, 0, stream>>>(T, 1ll << cap_log2, kEmptyKey);
     bbox_kernel<<<1024, 256, 0, stream>>>(points, n, enc6);
-    count_kernel<<<1024, 256, 0, stream>>>(points, n, s, aspect[0], aspect[1], aspect[2], enc6, T,
-                                           cap_log2, dK, derr);
+    count_kernel<<<1024, 256, 0, stream>>>(points, n, s, aspect[0], aspect[1], aspect[2], enc6, T, cap_log2, dK,
+                                           derr);
     if (cudaGetLastError() != cudaSuccess) return HAV_ERR_CUDA;
     unsigned long long hK = 0;
     int herr = 0;

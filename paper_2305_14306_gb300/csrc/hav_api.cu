@@ -160,6 +160,9 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
     plan->sigma_num = params->sigma_num;
     plan->sigma_den = params->sigma_den;
     plan->nblocks = ctx->nblocks;
+    plan->spec_n[0] = havk::kSpecN4;
+    plan->spec_n[1] = havk::kSpecN3;
+    plan->spec_n[2] = havk::kSpecN2;
     for (int a = 0; a < 3; ++a) plan->aspect[a] = params->aspect[a];
     for (int j = 0; j < num_levels; ++j) plan->out[j] = out_idx[j];
     if (params->flags & HAV_FLAG_PHASE_TIMES) {

@@ -142,7 +142,7 @@ __device__ __forceinline__ long long find_or_insert(unsigned long long* T, int c
 // before any result is used (memory-level parallelism); keys equal to
 // kEmptyKey are skipped.  slot[u] = -1 after a full sweep (table full).
 template <int U>
-__device__ __forceinline__ void find_or_insert_batch(unsigned long long* T, int cap_log2,
+__device__ __forceinline__ void find_or_insert_batch(unsigned long long* const (&T)[U], int cap_log2,
                                                      const unsigned long long (&key)[U],
                                                      long long (&slot)[U], bool (&fresh)[U]) {
     const unsigned mask = static_cast<unsigned>((1ull << cap_log2) - 1);
@@ -154,7 +154,7 @@ __device__ __forceinline__ void find_or_insert_batch(unsigned long long* T, int 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         sl[u] = static_cast<unsigned>(slot_mix(key[u]) >> (64 - cap_log2));
-        cur[u] = (key[u] != kEmptyKey) ? atomicCAS(T + sl[u], kEmptyKey, key[u]) : kEmptyKey;
+        cur[u] = (key[u] != kEmptyKey) ? atomicCAS(T[u] + sl[u], kEmptyKey, key[u]) : kEmptyKey;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -169,13 +169,13 @@ __device__ __forceinline__ void find_or_insert_batch(unsigned long long* T, int 
         // collision: linear probing from the next slot
         unsigned s2 = (sl[u] + 1) & mask;
         for (unsigned probe = 1; probe <= mask; ++probe) {
-            const unsigned long long c = ld_strong64(T + s2);
+            const unsigned long long c = ld_strong64(T[u] + s2);
             if (c == key[u]) {
                 slot[u] = s2;
                 break;
             }
             if (c == kEmptyKey) {
-                const unsigned long long prev = atomicCAS(T + s2, kEmptyKey, key[u]);
+                const unsigned long long prev = atomicCAS(T[u] + s2, kEmptyKey, key[u]);
                 if (prev == kEmptyKey || prev == key[u]) {
                     slot[u] = s2;
                     fresh[u] = (prev == kEmptyKey);
@@ -221,6 +221,28 @@ __device__ __forceinline__ int smem_insert(unsigned long long* set, unsigned lon
             if (prev == key) return static_cast<int>(slot);
         }
         slot = (slot + 1) & (kSlots - 1);
+    }
+    return -1;
+}
+
+// smem_insert on a set of (1 << log2) slots starting at set (runtime size).
+__device__ __forceinline__ int smem_insert_n(unsigned long long* set, int log2, unsigned long long key, bool* fresh) {
+    const unsigned m = (1u << log2) - 1u;
+    unsigned slot = static_cast<unsigned>(slot_mix(key)) & m;
+    *fresh = false;
+#pragma unroll 1
+    for (int probe = 0; probe < 32; ++probe) {
+        const unsigned long long cur = set[slot];
+        if (cur == key) return static_cast<int>(slot);
+        if (cur == kEmptyKey) {
+            const unsigned long long prev = atomicCAS(set + slot, kEmptyKey, key);
+            if (prev == kEmptyKey) {
+                *fresh = true;
+                return static_cast<int>(slot);
+            }
+            if (prev == key) return static_cast<int>(slot);
+        }
+        slot = (slot + 1) & m;
     }
     return -1;
 }

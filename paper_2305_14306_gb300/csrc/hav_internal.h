@@ -23,6 +23,12 @@ constexpr int kHistBins = 1 << kHistBits;
 constexpr int kMaxBlocks = 2048;
 constexpr int kMinCapLog2 = 6;             // smallest per-segment table: 64 slots
 constexpr int kPhaseTimes = 4096;          // (time, tag) records of the phase timer
+constexpr int kMaxSpecDepth = 4;           // bisection steps one pass may evaluate ahead
+constexpr int kMaxCand = (1 << kMaxSpecDepth) - 1;  // candidate sizes per pass (a full subtree)
+// default level sizes (points) up to which a pass evaluates 4, 3 or 2 steps ahead
+constexpr int64_t kSpecN4 = 32768;
+constexpr int64_t kSpecN3 = 131072;
+constexpr int64_t kSpecN2 = 262144;
 
 constexpr unsigned long long kEmptyKey = ~0ull;  // valid keys use 63 bits
 constexpr unsigned long long kEmptyVal = ~0ull;  // packed (d^2 bits, index) never reaches it
@@ -50,7 +56,8 @@ struct SegHdr {
 
 // Per segment, per layer parity: zeroed inside the kernel before use.
 struct LayerState {
-    uint32_t count[3];  // Cnt of the bisection pass, three-way rotation
+    uint32_t count[3][kMaxCand];  // Cnt per candidate of a bisection pass, three-way rotation
+    uint32_t cerr[3];   // candidates with a voxel key out of range, same rotation
     uint32_t kstar;     // occupied voxels at s*
     uint32_t cand;      // cut-off candidates in the boundary bin
     int32_t bin;        // boundary bin of the cut-off
@@ -69,9 +76,10 @@ struct Layout {
     int64_t max_points;
     int32_t max_segments;
     int32_t pad;
-    int64_t tab_slots;     // capacity bound of all per-segment tables of a level
+    int64_t tab_slots;     // slots of one key-table array (all segments, all candidates of a pass)
     int64_t cand_slots;
     int64_t taken_words;
+    int64_t dirty_slots;   // entries of one fresh-insert log array
     size_t barrier, ghdr, seghdr, zero_bytes;  // [barrier, barrier+zero_bytes) zeroed per call
     size_t clean;          // 1 when every hash-table slot is empty (kept across calls)
     size_t lstate, hist, partial_sf, partial_cmp, pitem, trace, ptimes;
@@ -84,13 +92,18 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr int kMaxItems = kMaxBlocks + kMaxSegments;  // work items of one level
 
-inline Layout make_layout(int64_t N, int32_t S) {
+inline Layout make_layout(int64_t N, int32_t S, bool spec_room = true) {
     Layout L{};
     L.max_points = N;
     L.max_segments = S;
-    // Per-segment capacity C = max(nextpow2(2 n), 64) < max(4 n, 128).
-    L.tab_slots = 4 * N + 128 * static_cast<int64_t>(S);
-    L.cand_slots = L.tab_slots / 2;
+    // Per-segment capacity C = max(nextpow2(2 n), 64) < max(4 n, 128); small
+    // levels (at most 32,768 points) also get room for kMaxCand tables per pass.
+    const int64_t plain = 4 * N + 128 * static_cast<int64_t>(S);
+    const int64_t spec = spec_room ? static_cast<int64_t>(kMaxCand) * (65536 + 128 * static_cast<int64_t>(S)) : 0;
+    L.tab_slots = plain > spec ? plain : spec;
+    L.cand_slots = (4 * N + 128 * static_cast<int64_t>(S)) / 2;
+    const int64_t dspec = spec_room ? static_cast<int64_t>(kMaxCand) * 32768 : 0;
+    L.dirty_slots = N > dspec ? N : dspec;
     L.taken_words = N / 32 + 2;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -114,7 +127,7 @@ inline Layout make_layout(int64_t N, int32_t S) {
         L.ord[b] = take(16 * static_cast<size_t>(N) + 16);
         L.orig[b] = take(sizeof(int32_t) * N + 16);
         L.taken[b] = take(sizeof(uint32_t) * L.taken_words);
-        L.dirty[b] = take(sizeof(uint32_t) * N + 16);
+        L.dirty[b] = take(sizeof(uint32_t) * L.dirty_slots + 16);
     }
     L.wpre = take(sizeof(uint32_t) * L.taken_words);
     L.bkt = take(sizeof(uint32_t) * 2 * 4096);
@@ -136,6 +149,7 @@ struct Plan {
     unsigned long long* ptimes;  // phase timer records, or null (HAV_FLAG_PHASE_TIMES)
     int32_t ptimes_cap;
     int32_t pad2;
+    int64_t spec_n[3];           // level sizes up to which a pass looks 4, 3, 2 steps ahead
     int32_t S, L, layers, ratio, t_max, sigma_num, sigma_den, nblocks;
     float aspect[3];
     int32_t pad;

@@ -100,7 +100,7 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
     st = setup_device(dev, &ds);
     if (st != HAV_OK) return st;
 
-    const havk::Layout lay = havk::make_layout(kNoAllocMaxPoints, 1);
+    const havk::Layout lay = havk::make_layout(kNoAllocMaxPoints, 1, /*spec_room=*/false);
     if (lay.total > kNoAllocScratchBytes) return HAV_ERR_NOMEM;
 
     cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);

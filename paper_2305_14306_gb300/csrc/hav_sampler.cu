@@ -74,16 +74,26 @@ struct Smem {
     float mx[kMaxSegments][3];
     float s_hi[kMaxSegments];
     // controller of the current layer
-    float lo[kMaxSegments], hi[kMaxSegments], s_cur[kMaxSegments], s_star[kMaxSegments];
+    float lo[kMaxSegments], hi[kMaxSegments], s_star[kMaxSegments];
     Grid grid[kMaxSegments];
+    int iters[kMaxSegments];
+    int sel_cand[kMaxSegments];
     int ml[kMaxSegments];
     int kmax[kMaxSegments];
     int flags[kMaxSegments];
     int sel[kMaxSegments];
     int kstar[kMaxSegments];
     int cprefix[kMaxSegments + 1];
-    // per-block logs of fresh global inserts, one per (table parity, owned item)
-    int dcnt[2][kLocalItems];
+    // per-block logs of fresh global inserts, one per (table set, owned item, candidate)
+    int dcnt[2][kLocalItems][kMaxCand];
+    // candidate grids of a speculative pass, per owned item
+    Grid cgrid[kLocalItems][kMaxCand];
+    int cvalid[kLocalItems][kMaxCand];
+    unsigned ccount[kMaxCand];
+    unsigned rbits;
+    int ncand;
+    int setc_log2;
+    long long tab_stride;
     // scratch
     long long scan_ll[32];
     int scan_i[32];
@@ -205,6 +215,22 @@ __device__ __forceinline__ unsigned bucket_of(const float p[3], const float mn[3
     return id;
 }
 
+// Size evaluated by node c (heap order) of the bisection subtree below
+// (lo, hi): the path from the root follows the bits of c + 1 below its
+// leading one (0: too few voxels, hi = s; 1: too many, lo = s), with the
+// same binary32 midpoint as the sequential search.
+__device__ __forceinline__ float cand_size(float lo, float hi, int c) {
+    const int x = c + 1;
+    const int depth = 31 - __clz(x);
+    float s = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+    for (int b = depth - 1; b >= 0; --b) {
+        if ((x >> b) & 1) lo = s;
+        else hi = s;
+        s = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+    }
+    return s;
+}
+
 // Level layout of every segment, computed identically by every block.
 __device__ void level_setup(const Plan& P, int j, Smem& st) {
     const int S = P.S;
@@ -229,8 +255,18 @@ __device__ void level_setup(const Plan& P, int j, Smem& st) {
     }
     __syncthreads();
     const long long nl = st.n_level;
-    long long chunk = (nl + P.nblocks - 1) / P.nblocks;
-    if (chunk < kThreads) chunk = kThreads;
+    // speculation depth: deeper on small levels, where a pass is latency-bound
+    int depth = nl <= P.spec_n[0] ? 4 : nl <= P.spec_n[1] ? 3 : nl <= P.spec_n[2] ? 2 : 1;
+    long long chunk = (nl + P.nblocks - 1) / P.nblocks;  // every block gets a share
+    if (chunk < 64) chunk = 64;
+    if (depth > 1) {
+        // a candidate's share of the block set must stay at most half full
+        const int ncand = (1 << depth) - 1;
+        int lg2 = 0;
+        while ((1 << (lg2 + 1)) * ncand <= kSetSlots) ++lg2;
+        const long long cap_pts = (1ll << lg2) / 2;
+        if (chunk > cap_pts) chunk = cap_pts;
+    }
     o = block_excl_scan<long long>(mm, &tot, st.scan_ll);
     if (s == 0) {
         st.m_total = tot;
@@ -248,7 +284,19 @@ __device__ void level_setup(const Plan& P, int j, Smem& st) {
         st.item0[S] = static_cast<int>(tot);
         st.items_total = static_cast<int>(tot);
     }
-    if (s < 2 * kLocalItems) st.dcnt[s / kLocalItems][s % kLocalItems] = 0;
+    for (int k = s; k < 2 * kLocalItems * kMaxCand; k += kThreads) (&st.dcnt[0][0][0])[k] = 0;
+    if (s == 0) {
+        const long long stride = st.tab_off[S - 1] + (1ll << st.cap_log2[S - 1]);
+        while (depth > 1 && (((1ll << depth) - 1) * stride > P.lay.tab_slots ||
+                             ((1ll << depth) - 1) * nl > P.lay.dirty_slots ||
+                             st.items_total > static_cast<int>(kLocalItems) * P.nblocks))
+            --depth;
+        st.tab_stride = stride;
+        st.ncand = (1 << depth) - 1;
+        int lg2 = 0;
+        while ((1 << (lg2 + 1)) * st.ncand <= kSetSlots) ++lg2;
+        st.setc_log2 = lg2;
+    }
     __syncthreads();
 }
 
@@ -466,6 +514,9 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
 
         // ------------------------------------------------------------ layers
         long long taken_before = 0;  // thread s: budgets of earlier layers of segment s
+        const int ncand = st.ncand;
+        const long long tstride = st.tab_stride;  // table slots of one candidate (all segments)
+        const long long dstride = NL;             // log entries of one candidate
         for (int l = 0; l < P.layers; ++l) {
             const int q = l & 1;
             LayerState* ls = d.ls + q * S;
@@ -481,6 +532,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 st.lo[tid] = 0.0f;
                 st.hi[tid] = st.s_hi[tid];
                 st.sel[tid] = 0;
+                st.sel_cand[tid] = 0;
+                st.iters[tid] = 0;
                 st.kstar[tid] = 0;
                 int fl = active ? F_ACTIVE : 0;
                 if (active && P.t_max > 0) fl |= F_SEARCH;
@@ -509,47 +562,57 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             __syncthreads();
 
             // --------------------------------------- Section 3.3 bisection
+            // One pass evaluates the whole depth-D subtree of the bisection below
+            // each segment's current (lo, hi): ncand = 2^D - 1 candidate sizes,
+            // each with its own table and count.  The decision then walks the
+            // subtree exactly as the sequential search does, so the sizes
+            // evaluated on the path, their counts and the outcome are those of the
+            // plain bisection; D = 1 is the plain bisection.
             for (int p = 0; p < P.t_max; ++p) {
-                int searching = 0;
-                if (tid < S && (st.flags[tid] & F_SEARCH)) {
-                    const float s = __fmul_rn(__fadd_rn(st.lo[tid], st.hi[tid]), 0.5f);
-                    st.s_cur[tid] = s;
-                    if (make_grid(s, P.aspect, st.mn[tid], &st.grid[tid])) {
-                        searching = 1;
-                    } else {
-                        seg_error(d, tid, HAV_ERR_RANGE);
-                        st.flags[tid] = 0;
-                        st.err[tid] = HAV_ERR_RANGE;
-                    }
-                }
+                const int searching = (tid < S && (st.flags[tid] & F_SEARCH)) ? 1 : 0;
                 if (!__syncthreads_or(searching)) break;
                 const int X = p & 1, Y = X ^ 1;
-                unsigned long long* TX = d.tk[X];
-                unsigned long long* TY = d.tk[Y];
 
-                // clean the other table, slot by slot, from this block's logs
+                // candidate grids of the owned items' segments
+                {
+                    int li = 0;
+                    for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
+                        const int s = find_seg(st.item0, S, it);
+                        if (tid < ncand && (st.flags[s] & F_SEARCH)) {
+                            const float sc = cand_size(st.lo[s], st.hi[s], tid);
+                            st.cvalid[li][tid] = make_grid(sc, P.aspect, st.mn[s], &st.cgrid[li][tid]) ? 1 : 0;
+                        }
+                    }
+                }
+                // clean the other table set, slot by slot, from this block's logs
                 if (p >= 1) {
                     int li = 0;
                     for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
                         int a, b;
                         const int s = item_range(st, S, it, &a, &b);
                         if (!(st.flags[s] & F_SEARCH)) continue;
-                        const int c = st.dcnt[Y][li];
-                        for (int k = tid; k < c; k += kThreads) TY[d.dirty[Y][a + k]] = kEmptyKey;
+                        for (int c = 0; c < ncand; ++c) {
+                            const int cnt = st.dcnt[Y][li][c];
+                            const uint32_t* lg = d.dirty[Y] + c * dstride + a;
+                            for (int k = tid; k < cnt; k += kThreads) d.tk[Y][lg[k]] = kEmptyKey;
+                        }
                     }
                     __syncthreads();
                     li = 0;
                     for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
                         const int s = find_seg(st.item0, S, it);
-                        if (tid == 0 && (st.flags[s] & F_SEARCH)) st.dcnt[Y][li] = 0;
+                        if (tid < ncand && (st.flags[s] & F_SEARCH)) st.dcnt[Y][li][tid] = 0;
                     }
                 }
+                __syncthreads();
 
-                // Cnt(P_l, s_p): (a) every point's key into the block set, the keys new
-                // to the block listed densely; (b) the listed keys into the global
-                // table, kProbes compare-and-swaps in flight per thread
+                // Cnt(P_l, s_c) for every candidate c: (a) every point's key into the
+                // candidate's part of the block set, keys new to the block listed
+                // densely; (b) the listed keys into the candidates' global tables,
+                // kProbes compare-and-swaps in flight per thread
                 unsigned long long* set = reinterpret_cast<unsigned long long*>(dyn);
                 unsigned short* list = reinterpret_cast<unsigned short*>(dyn + kSetSlots * sizeof(unsigned long long));
+                const int setc_log2 = st.setc_log2;
                 int li = 0;
                 for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
                     int a, b;
@@ -557,49 +620,60 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     if (!(st.flags[s] & F_SEARCH)) continue;
                     if (!st.set_clean)  // otherwise every slot is already empty
                         for (int k = tid; k < kSetSlots; k += kThreads) set[k] = kEmptyKey;
-                    if (tid == 0) st.list_n = 0u;
+                    if (tid == 0) {
+                        st.list_n = 0u;
+                        st.rbits = 0u;
+                    }
+                    if (tid < ncand) st.ccount[tid] = 0u;
                     __syncthreads();
-                    const Grid& G = st.grid[s];
-                    unsigned long long* T = TX + st.tab_off[s];
                     const int cap = st.cap_log2[s];
-                    unsigned fresh = 0;
+                    unsigned long long* Tb = d.tk[X] + st.tab_off[s];
                     int bad = 0;
-                    auto log_fresh = [&](long long slot) {
-                        ++fresh;
-                        const int k = atomicAdd(&st.dcnt[X][li], 1);
-                        d.dirty[X][a + k] = static_cast<uint32_t>(st.tab_off[s] + slot);
+                    unsigned rbits = 0;  // candidates with a key out of range
+                    auto log_fresh = [&](int c, long long slot) {
+                        atomicAdd(&st.ccount[c], 1u);
+                        const int k = atomicAdd(&st.dcnt[X][li][c], 1);
+                        d.dirty[X][c * dstride + a + k] = static_cast<uint32_t>(c * tstride + st.tab_off[s] + slot);
                     };
+                    // work units are (candidate, point) pairs, point-minor, so that a
+                    // warp reads consecutive points and the candidates run in parallel
                     const int lane = tid & 31;
-                    for (int base = a + (tid - lane); base < b; base += kInFlight * kThreads) {  // warp-uniform
+                    const int L = b - a;
+                    const int units = L * ncand;
+                    for (int base = tid - lane; base < units; base += kInFlight * kThreads) {  // warp-uniform
                         float4 q4[kInFlight];
+                        int cu[kInFlight];
 #pragma unroll
                         for (int u = 0; u < kInFlight; ++u) {
-                            const int i = base + lane + u * kThreads;
-                            q4[u] = (i < b) ? ord[i] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                            const int w = base + lane + u * kThreads;
+                            cu[u] = (ncand == 1) ? 0 : w / L;
+                            q4[u] = (w < units) ? ord[a + (w - cu[u] * L)]
+                                                : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
                         }
 #pragma unroll
                         for (int u = 0; u < kInFlight; ++u) {
                             const int g = __float_as_int(q4[u].w);
-                            bool ok = g >= 0 && !(use_mask && is_taken(taken, g));
+                            const int c = cu[u];
+                            bool ok = g >= 0 && !(use_mask && is_taken(taken, g)) && st.cvalid[li][c];
                             unsigned long long key = kEmptyKey;
                             if (ok) {
                                 const float p3[3] = {q4[u].x, q4[u].y, q4[u].z};
                                 float f[3];
-                                if (!cell_key(p3, G, &key, f)) {
-                                    bad = HAV_ERR_RANGE;
+                                if (!cell_key(p3, st.cgrid[li][c], &key, f)) {
+                                    rbits |= 1u << c;
                                     ok = false;
                                 }
                             }
                             int r = -2;
                             bool nw = false;
-                            if (ok) r = smem_insert<kSetSlots>(set, key, &nw);
+                            if (ok) r = smem_insert_n(set + (c << setc_log2), setc_log2, key, &nw);
                             const int pos = warp_append(r >= 0 && nw, &st.list_n);
-                            if (pos >= 0) list[pos] = static_cast<unsigned short>(r);
+                            if (pos >= 0) list[pos] = static_cast<unsigned short>((c << setc_log2) + r);
                             if (r == -1) {  // block set saturated: straight to the global table
                                 bool fr;
-                                const long long slot = find_or_insert(T, cap, key, &fr);
+                                const long long slot = find_or_insert(Tb + c * tstride, cap, key, &fr);
                                 if (slot < 0) bad = HAV_ERR_TABLE_FULL;
-                                else if (fr) log_fresh(slot);
+                                else if (fr) log_fresh(c, slot);
                             }
                         }
                     }
@@ -607,67 +681,103 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     const int nl = static_cast<int>(st.list_n);
                     for (int k0 = tid; k0 < nl; k0 += kProbes * kThreads) {
                         unsigned long long key[kProbes];
+                        unsigned long long* Tp[kProbes];
+                        int cc[kProbes];
                         long long slot[kProbes];
                         bool fr[kProbes];
 #pragma unroll
                         for (int u = 0; u < kProbes; ++u) {
                             const int k = k0 + u * kThreads;
-                            key[u] = (k < nl) ? set[list[k]] : kEmptyKey;
+                            const int idx = (k < nl) ? static_cast<int>(list[k]) : 0;
+                            cc[u] = idx >> setc_log2;
+                            key[u] = (k < nl) ? set[idx] : kEmptyKey;
+                            Tp[u] = Tb + cc[u] * tstride;
                         }
-                        find_or_insert_batch<kProbes>(T, cap, key, slot, fr);
+                        find_or_insert_batch<kProbes>(Tp, cap, key, slot, fr);
 #pragma unroll
                         for (int u = 0; u < kProbes; ++u) {
                             if (key[u] == kEmptyKey) continue;
                             if (slot[u] < 0) bad = HAV_ERR_TABLE_FULL;
-                            else if (fr[u]) log_fresh(slot[u]);
+                            else if (fr[u]) log_fresh(cc[u], slot[u]);
                         }
                     }
                     // empty the set again: exactly the listed slots are occupied
                     __syncthreads();
                     for (int k = tid; k < nl; k += kThreads) set[list[k]] = kEmptyKey;
                     if (tid == 0) st.set_clean = 1;
+                    if (rbits) atomicOr(&st.rbits, rbits);
                     if (bad) seg_error(d, s, bad);
-                    const unsigned total = block_sum(fresh, st.scan_u);
-                    if (tid == 0 && total) atomicAdd(&ls[s].count[p % 3], total);
+                    __syncthreads();
+                    if (tid < ncand && st.ccount[tid]) atomicAdd(&ls[s].count[p % 3][tid], st.ccount[tid]);
+                    if (tid == 0 && st.rbits) atomicOr(&ls[s].cerr[p % 3], st.rbits);
                 }
-                if (p >= 1 && blockIdx.x == 0 && tid < S) ls[tid].count[(p + 1) % 3] = 0;
+                if (p >= 1 && blockIdx.x == 0)
+                    for (int k = tid; k < S * (kMaxCand + 1); k += kThreads) {
+                        const int s = k / (kMaxCand + 1), c = k % (kMaxCand + 1);
+                        if (c < kMaxCand) ls[s].count[(p + 1) % 3][c] = 0u;
+                        else ls[s].cerr[(p + 1) % 3] = 0u;
+                    }
                 if (!grid_sync(d, nb, st, TAG(2, j, l, p))) return;
 
-                // decide (identically in every block)
-                if (tid < S && (st.flags[tid] & F_SEARCH)) {
-                    const long long K = ld_volatile(reinterpret_cast<const int*>(&ls[tid].count[p % 3]));
-                    const float s = st.s_cur[tid];
-                    if (blockIdx.x == 0) {
-                        hav_layer_trace* tr = d.tr + (static_cast<long long>(j) * S + tid) * kMaxLayers + l;
-                        tr->s[p] = s;
-                        tr->K[p] = K;
-                        tr->iters = p + 1;
+                // decide (identically in every block): walk the evaluated subtree
+                if (searching) {
+                    float lo = st.lo[tid], hi = st.hi[tid];
+                    int node = 0;
+                    int t = st.iters[tid];
+                    const unsigned cerr = ld_volatile_u(&ls[tid].cerr[p % 3]);
+                    hav_layer_trace* tr = d.tr + (static_cast<long long>(j) * S + tid) * kMaxLayers + l;
+                    while (node < ncand && t < P.t_max) {
+                        const float sv = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+                        Grid gv;
+                        if ((cerr >> node) & 1u || !make_grid(sv, P.aspect, st.mn[tid], &gv)) {
+                            seg_error(d, tid, HAV_ERR_RANGE);
+                            st.err[tid] = HAV_ERR_RANGE;
+                            st.flags[tid] = 0;
+                            break;
+                        }
+                        const long long K = ld_volatile(reinterpret_cast<const int*>(&ls[tid].count[p % 3][node]));
+                        if (blockIdx.x == 0) {
+                            tr->s[t] = sv;
+                            tr->K[t] = K;
+                            tr->iters = t + 1;
+                        }
+                        ++t;
+                        if (K > st.kmax[tid]) {
+                            lo = sv;
+                            node = 2 * node + 2;
+                        } else if (K < st.ml[tid]) {
+                            hi = sv;
+                            node = 2 * node + 1;
+                        } else {
+                            st.s_star[tid] = sv;
+                            st.grid[tid] = gv;
+                            st.sel[tid] = X;
+                            st.sel_cand[tid] = node;
+                            st.flags[tid] = F_ACTIVE | F_ACCEPT;
+                            break;
+                        }
                     }
-                    if (K > st.kmax[tid]) {
-                        st.lo[tid] = s;
-                    } else if (K < st.ml[tid]) {
-                        st.hi[tid] = s;
-                    } else {
-                        st.s_star[tid] = s;
-                        st.sel[tid] = X;
-                        st.flags[tid] = F_ACTIVE | F_ACCEPT;
+                    st.lo[tid] = lo;
+                    st.hi[tid] = hi;
+                    st.iters[tid] = t;
+                    if ((st.flags[tid] & F_SEARCH) && t >= P.t_max) {
+                        // no acceptance within t_max steps: the set cleaned in this pass is free
+                        const float sv = (lo > 0.0f) ? lo : hi;
+                        st.s_star[tid] = sv;
+                        st.sel[tid] = Y;
+                        st.sel_cand[tid] = 0;
+                        st.flags[tid] = F_ACTIVE;
+                        if (!make_grid(sv, P.aspect, st.mn[tid], &st.grid[tid])) {
+                            seg_error(d, tid, HAV_ERR_RANGE);
+                            st.flags[tid] = 0;
+                            st.err[tid] = HAV_ERR_RANGE;
+                        }
                     }
                 }
                 __syncthreads();
             }
-            // no acceptance within t_max steps: the table cleaned in the last pass is used
-            if (tid < S && (st.flags[tid] & F_SEARCH)) {
-                const float s = (st.lo[tid] > 0.0f) ? st.lo[tid] : st.hi[tid];
-                st.s_star[tid] = s;
-                st.sel[tid] = P.t_max & 1;
-                st.flags[tid] = F_ACTIVE;
-                if (!make_grid(s, P.aspect, st.mn[tid], &st.grid[tid])) {
-                    seg_error(d, tid, HAV_ERR_RANGE);
-                    st.flags[tid] = 0;
-                    st.err[tid] = HAV_ERR_RANGE;
-                }
-            }
-            __syncthreads();
+            // (every searching segment takes at least one step per pass, so none is
+            // still searching after t_max passes)
 
             // ------------------------------------- Section 3.2 selection at s*
             {
@@ -688,15 +798,17 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     __syncthreads();
                     const Grid& G = st.grid[s];
                     const int sel = st.sel[s];
-                    unsigned long long* T = d.tk[sel] + st.tab_off[s];
+                    const int sc = st.sel_cand[s];
+                    unsigned long long* T = d.tk[sel] + sc * tstride + st.tab_off[s];
                     unsigned long long* V = d.tv + st.tab_off[s];
                     const int cap = st.cap_log2[s];
                     unsigned first = 0;
                     int bad = 0;
                     auto global_min = [&](unsigned long long key, long long slot, bool fr, unsigned long long packed) {
                         if (fr) {
-                            const int k = atomicAdd(&st.dcnt[sel][li], 1);
-                            d.dirty[sel][a + k] = static_cast<uint32_t>(st.tab_off[s] + slot);
+                            const int k = atomicAdd(&st.dcnt[sel][li][sc], 1);
+                            d.dirty[sel][sc * dstride + a + k] =
+                                static_cast<uint32_t>(sc * tstride + st.tab_off[s] + slot);
                         }
                         if (atomicMin(V + slot, packed) == kEmptyVal) {
                             ++first;
@@ -748,6 +860,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     const int nl = static_cast<int>(st.list_n);
                     for (int k0 = tid; k0 < nl; k0 += kProbes * kThreads) {
                         unsigned long long key[kProbes];
+                        unsigned long long* Tp[kProbes];
                         long long slot[kProbes];
                         bool fr[kProbes];
                         int sidx[kProbes];
@@ -756,8 +869,9 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             const int k = k0 + u * kThreads;
                             sidx[u] = (k < nl) ? static_cast<int>(list[k]) : 0;
                             key[u] = (k < nl) ? skey[sidx[u]] : kEmptyKey;
+                            Tp[u] = T;
                         }
-                        find_or_insert_batch<kProbes>(T, cap, key, slot, fr);
+                        find_or_insert_batch<kProbes>(Tp, cap, key, slot, fr);
 #pragma unroll
                         for (int u = 0; u < kProbes; ++u) {
                             if (key[u] == kEmptyKey) continue;
@@ -825,14 +939,17 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         __syncthreads();
                     }
                     const int sel = st.sel[s];
-                    const int c = st.dcnt[sel][li];
+                    const int sc = st.sel_cand[s];
+                    const int c = st.dcnt[sel][li][sc];
+                    const uint32_t* lg = d.dirty[sel] + sc * dstride + a;
+                    const long long voff = sc * tstride;
                     const long long C = 1ll << st.cap_log2[s];
                     const int bin = st.cut_bin;
                     for (int k = tid; k < c; k += kThreads) {
-                        const uint32_t gs = d.dirty[sel][a + k];
-                        const unsigned long long v = d.tv[gs];
+                        const uint32_t gs = lg[k];
+                        const unsigned long long v = d.tv[gs - voff];
                         if (v == kEmptyVal) continue;
-                        const long long g = static_cast<long long>(v & 0xffffffffull);
+                        const int g = static_cast<int>(v & 0xffffffffull);
                         if (!cut) {
                             set_taken(taken, g);
                             continue;
@@ -876,7 +993,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     int rank = 0;
                     for (int k = 0; k < cs; ++k) rank += (base[k].h < hj) ? 1 : 0;
                     const int r = st.ml[s] - static_cast<int>(ls[s].below);
-                    if (rank < r) set_taken(taken, base[jdx].g);
+                    if (rank < r) set_taken(taken, static_cast<int>(base[jdx].g));
                 }
                 int sf = 0;
                 if (tid < S && (st.flags[tid] & F_ACTIVE) && st.kstar[tid] < st.ml[tid]) sf = 1;
@@ -887,34 +1004,40 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 if (st.any) {
                     for (int s = 0; s < S; ++s) {
                         if (!((st.flags[s] & F_ACTIVE) && st.kstar[s] < st.ml[s])) continue;
-                        const long long n = st.n[s];
-                        const long long a = st.off[s] + n * blockIdx.x / nb;
-                        const long long b = st.off[s] + n * (blockIdx.x + 1) / nb;
+                        const int n = st.n[s];
+                        const int a = static_cast<int>(st.off[s] + static_cast<long long>(n) * blockIdx.x / nb);
+                        const int b = static_cast<int>(st.off[s] + static_cast<long long>(n) * (blockIdx.x + 1) / nb);
                         int cnt = 0;
-                        for (long long g = a + tid; g < b; g += kThreads) cnt += is_taken(taken, g) ? 0 : 1;
+                        for (int g = a + tid; g < b; g += kThreads) cnt += is_taken(taken, g) ? 0 : 1;
                         int tot;
                         block_excl_scan<int>(cnt, &tot, st.scan_i);
                         if (tid == 0) d.psf[static_cast<long long>(s) * kMaxBlocks + blockIdx.x] = tot;
                     }
                 }
-                // both key tables and the value table back to empty, slot by slot
+                // every candidate table of both sets, and the value table, back to
+                // empty, slot by slot
                 int li = 0;
                 for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
                     int a, b;
                     const int s = item_range(st, S, it, &a, &b);
-                    const bool sel_v = (st.flags[s] & F_ACTIVE) != 0;
+                    const bool act = (st.flags[s] & F_ACTIVE) != 0;
                     for (int t = 0; t < 2; ++t) {
-                        const int c2 = st.dcnt[t][li];
-                        const bool v_too = sel_v && st.sel[s] == t;
-                        for (int k = tid; k < c2; k += kThreads) {
-                            const uint32_t gs = d.dirty[t][a + k];
-                            d.tk[t][gs] = kEmptyKey;
-                            if (v_too) d.tv[gs] = kEmptyVal;
+                        for (int cd = 0; cd < ncand; ++cd) {
+                            const int c2 = st.dcnt[t][li][cd];
+                            const bool v_too = act && st.sel[s] == t && st.sel_cand[s] == cd;
+                            const uint32_t* lg = d.dirty[t] + cd * dstride + a;
+                            const long long voff = cd * tstride;
+                            for (int k = tid; k < c2; k += kThreads) {
+                                const uint32_t gs = lg[k];
+                                d.tk[t][gs] = kEmptyKey;
+                                if (v_too) d.tv[gs - voff] = kEmptyVal;
+                            }
                         }
                     }
                 }
                 __syncthreads();
-                if (tid < 2 * kLocalItems) st.dcnt[tid / kLocalItems][tid % kLocalItems] = 0;
+                for (int k = tid; k < 2 * kLocalItems * kMaxCand; k += kThreads)
+                    (&st.dcnt[0][0][0])[k] = 0;
                 if (l + 1 < P.layers) clear_layer_state(d, S, q ^ 1, gtid, gstride);
                 if (!grid_sync(d, nb, st, TAG(5, j, l, 0))) return;
                 if (j + 1 == P.L && l + 1 == P.layers && blockIdx.x == 0 && tid == 0)
@@ -930,11 +1053,11 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     int tot;
                     block_excl_scan<int>(pre, &tot, st.scan_i);
                     int budget = (st.ml[s] - st.kstar[s]) - tot;
-                    const long long n = st.n[s];
-                    const long long a = st.off[s] + n * blockIdx.x / nb;
-                    const long long b = st.off[s] + n * (blockIdx.x + 1) / nb;
-                    for (long long g0 = a; g0 < b && budget > 0; g0 += kThreads) {
-                        const long long g = g0 + tid;
+                    const int n = st.n[s];
+                    const int a = static_cast<int>(st.off[s] + static_cast<long long>(n) * blockIdx.x / nb);
+                    const int b = static_cast<int>(st.off[s] + static_cast<long long>(n) * (blockIdx.x + 1) / nb);
+                    for (int g0 = a; g0 < b && budget > 0; g0 += kThreads) {
+                        const int g = g0 + tid;
                         const int free_pt = (g < b && !is_taken(taken, g)) ? 1 : 0;
                         int chunk;
                         const int rank = block_excl_scan<int>(free_pt, &chunk, st.scan_i);

@@ -42,6 +42,9 @@ WORKLOADS = {
                     "n": None, "levels": [16384, 4096, 1024, 512]},
     "uniform-16k": {"desc": "16,384 uniform points in the KITTI range, one level to 4,096",
                     "n": 16384, "levels": [4096]},
+    "serving": {"desc": "Poisson arrivals of scenes with N log-uniform in [10k, 1M] (LiDAR up to 200k, room above), "
+                        "M in {N/4, N/16, 4096}; continuous batching on co-resident slots vs the plain per-cloud path",
+                "n": None, "levels": None},
     "batch64": {"desc": "64 LiDAR clouds, N log-uniform in [20k, 200k], per cloud M = N/4 then N/16, "
                         "one persistent segmented launch (also replayed from a CUDA graph) vs 64 per-cloud calls",
                 "n": None, "levels": None},
@@ -163,6 +166,20 @@ def clocks_bad(c) -> bool:
     if c["sm_mhz"] and c["sm_max_mhz"] and not c["reasons"] and c["sm_mhz"] < 0.6 * c["sm_max_mhz"]:
         return True
     return False
+
+
+def whole_job(local_seconds: float, points_per_rank: int, world: int, device=None) -> tuple:
+    """Replicas: every rank timed its own steps; the job takes as long as the
+    slowest rank, and `value` counts every rank's points.  Returns
+    (max seconds over ranks, whole-job Mpoints/s)."""
+    t = local_seconds
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        x = torch.tensor([local_seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t, points_per_rank * world / t / 1e6
 
 
 def dist_setup():
@@ -295,12 +312,7 @@ def run_batched(args, world, rank, local):
     ms_g = time_it(graph.replay, steps)
     ms_p = time_it(step_per_cloud, max(5, steps // 4))
     clocks = clk.stop()
-    tb = sum(ms_b) / 1e3
-    if world > 1:
-        t = torch.tensor([tb], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tb = float(t.item())
-    value = total * len(ms_b) * world / tb / 1e6
+    tb, value = whole_job(sum(ms_b) / 1e3, total * len(ms_b), world, device="cuda")
     v_graph = total * len(ms_g) / (sum(ms_g) / 1e3) / 1e6
     v_per = total * len(ms_p) / (sum(ms_p) / 1e3) / 1e6
     if rank == 0:
@@ -328,6 +340,78 @@ def run_batched(args, world, rank, local):
     return 0
 
 
+# ----------------------------------------------------------------- serving arm
+def run_serving(args, world, rank, local):
+    """C5: closed-loop capacity and open-loop latency (Poisson arrivals at 0.8x the
+    plain path's capacity) of the served path vs the plain per-cloud path."""
+    import torch
+    from paper_2305_14306_gb300 import serving
+
+    rng = np.random.default_rng(1000 + rank)
+    pool_n = scenes.log_uniform_sizes(16, 10_000, 1_000_000, seed=1000 + rank)
+    pool = [torch.from_numpy(scenes.scene_for(int(n), seed=5000 + i)).pin_memory() for i, n in enumerate(pool_n)]
+    R = max(20, min(args.steps, 400))
+    picks = rng.integers(0, len(pool), size=R)
+    choice = rng.integers(0, 3, size=R)
+
+    def make(arrivals):
+        out = []
+        for i in range(len(arrivals)):
+            pts = pool[picks[i]]
+            n = pts.shape[0]
+            m = [n // 4, n // 16, min(4096, n)][choice[i]]
+            out.append(serving.Request(i, float(arrivals[i]), pts, int(m)))
+        return out
+
+    slot_points = int(pool_n.max()) * 2
+    served = serving.Server(slots=args.serve_slots, slot_points=slot_points, max_segments=64)
+    plain = serving.Server(slots=1, slot_points=int(pool_n.max()), max_segments=1, share_sms=False)
+    try:
+        zero = np.zeros(R)
+        plain.serve(make(zero[:min(R, 8)]))  # warm-up
+        served.serve(make(zero[:min(R, 8)]))
+        t0 = time.perf_counter()
+        res_p = plain.serve(make(zero))
+        cap_plain = R / (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        res_s = served.serve(make(zero))
+        cap_served = R / (time.perf_counter() - t0)
+        same = all(np.array_equal(res_p[i].indices, res_s[i].indices) for i in range(R))
+        lam = 0.8 * cap_plain
+        arr = np.cumsum(np.random.default_rng(7 + rank).exponential(1.0 / lam, size=R))
+        arr -= arr[0]
+        clk = Clocks(local)
+        lat_p = [r.latency for r in plain.serve(make(arr)).values()]
+        lat_s_res = served.serve(make(arr))
+        clocks = clk.stop()
+        lat_s = [r.latency for r in lat_s_res.values()]
+    finally:
+        served.close()
+        plain.close()
+    pts_total = int(sum(pool[picks[i]].shape[0] for i in range(R)))
+    if rank == 0:
+        line = {
+            "metric": "input Mpoints/s", "value": pts_total / R * cap_served / 1e6, "unit": "Mpoints/s",
+            "n_gpus": world, "steps": R, "warmup": 8, "ms_per_step": 1e3 / cap_served,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving", "desc": WORKLOADS["serving"]["desc"], "requests": R,
+                       "slots": args.serve_slots, "slot_points": slot_points, "pool_scenes": len(pool)},
+            "scenes_per_s": cap_served,
+            "plain": {"scenes_per_s": cap_plain, "value": pts_total / R * cap_plain / 1e6},
+            "speedup_vs_per_cloud": cap_served / cap_plain,
+            "open_loop": {"arrival_rate_hz": lam,
+                          "served": {"p50_ms": 1e3 * serving.percentile(lat_s, 0.5),
+                                     "p99_ms": 1e3 * serving.percentile(lat_s, 0.99)},
+                          "plain": {"p50_ms": 1e3 * serving.percentile(lat_p, 0.5),
+                                    "p99_ms": 1e3 * serving.percentile(lat_p, 0.99)},
+                          "mean_batch": float(np.mean([r.batch for r in lat_s_res.values()]))},
+            "identical_outputs": bool(same),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -338,6 +422,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="indoor-1m")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-slots", type=int, default=2)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -359,8 +444,8 @@ def main():
     if world > 1:
         dist.barrier()
     hav.load()
-    if args.workload == "batch64":
-        rc = run_batched(args, world, rank, local)
+    if args.workload in ("batch64", "serving"):
+        rc = (run_batched if args.workload == "batch64" else run_serving)(args, world, rank, local)
         if world > 1:
             dist.destroy_process_group()
         return rc
@@ -426,12 +511,7 @@ def main():
     if st != hav.HAV_OK:
         raise SystemExit(f"hav status {st} in the timed region")
 
-    total_s = sum(ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = n * args.steps * world / total_s / 1e6
+    total_s, value = whole_job(sum(ms) / 1e3, n * args.steps, world, device="cuda")
     mean_ms = statistics.fmean(ms)
     ms_sorted = sorted(ms)
     p50 = ms_sorted[len(ms) // 2]
@@ -454,12 +534,7 @@ def main():
         b.synchronize()
         if k >= 3:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_total = sum(e2e_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = n * len(e2e_ms) * world / e2e_total / 1e6
+    e2e_total, e2e_value = whole_job(sum(e2e_ms) / 1e3, n * len(e2e_ms), world, device="cuda")
 
     peak, peak_kind = read_peaks()
     achieved = B / (mean_ms / 1e3) / 1e9

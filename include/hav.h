@@ -107,6 +107,12 @@ void hav_params_default(hav_params* p);
  * HAV_ERR_CUDA if the device cannot run the kernels (e.g. not sm_103). */
 hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_segments);
 
+/* Number of thread blocks (one per SM) the context's sampler launches use:
+ * 1..the device's co-resident maximum, or 0 for that maximum (the default).
+ * Contexts limited to disjoint shares of the SMs can run their calls
+ * concurrently on different streams (the serving loop does this). */
+hav_status hav_context_set_blocks(hav_ctx* ctx, int32_t nblocks);
+
 /* Release the context and its device memory.  Waits for the device.  NULL is ignored. */
 void hav_context_destroy(hav_ctx* ctx);
 
@@ -171,6 +177,16 @@ int32_t hav_phase_times_get(hav_ctx* ctx, hav_stream stream, uint64_t* t_ns, uin
  * Synchronous: *K (HOST) is valid on return. */
 hav_status hav_count(hav_ctx* ctx, const float* points, int64_t n, float s,
                      const float aspect[3], int64_t* K, hav_stream stream);
+
+/* Farthest point sampling, the comparator of Section 3.1 (Eq. 1): start at
+ * index 0, repeatedly take the point farthest (squared binary32 distance,
+ * ties to the lowest index) from the points taken so far.  points: device,
+ * n*3 floats; out_idx: device, m int32 in selection order.  0 <= m <= n <=
+ * the context's max_points.  One cooperative launch with one grid barrier
+ * per selected point; asynchronous on `stream`; a barrier timeout is read
+ * with hav_status_get. */
+hav_status hav_fps(hav_ctx* ctx, const float* points, int64_t n, int64_t m, int32_t* out_idx,
+                   hav_stream stream);
 
 /* Static description of a status code. */
 const char* hav_status_string(hav_status s);

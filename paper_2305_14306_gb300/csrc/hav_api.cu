@@ -14,6 +14,8 @@
 struct hav_ctx {
     int device;
     int nblocks;
+    int max_blocks;
+    int fps_nblocks;
     havk::Layout lay;
     unsigned char* ws;
     int32_t last_S;
@@ -90,10 +92,13 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (major != 10 || minor != 3 || !coop) return HAV_ERR_CUDA;  // built for sm_103a only
     const int nb = havk::max_coresident_blocks(dev);
-    if (nb < 1) return HAV_ERR_CUDA;
+    const int fnb = havk::fps_coresident_blocks(dev);
+    if (nb < 1 || fnb < 1) return HAV_ERR_CUDA;
     hav_ctx* c = new hav_ctx();
     c->device = dev;
     c->nblocks = nb;
+    c->max_blocks = nb;
+    c->fps_nblocks = fnb;
     c->lay = havk::make_layout(max_points, max_segments);
     if (cudaMalloc(&c->ws, c->lay.total) != cudaSuccess) {
         delete c;
@@ -106,6 +111,12 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
         return HAV_ERR_CUDA;
     }
     *out = c;
+    return HAV_OK;
+}
+
+hav_status hav_context_set_blocks(hav_ctx* ctx, int32_t nblocks) {
+    if (!ctx || nblocks < 0 || nblocks > ctx->max_blocks) return HAV_ERR_INVALID;
+    ctx->nblocks = nblocks == 0 ? ctx->max_blocks : nblocks;
     return HAV_OK;
 }
 
@@ -262,6 +273,23 @@ int32_t hav_phase_times_get(hav_ctx* ctx, hav_stream stream, uint64_t* t_ns, uin
         ++w;
     }
     return w;
+}
+
+hav_status hav_fps(hav_ctx* ctx, const float* points, int64_t n, int64_t m, int32_t* out_idx,
+                   hav_stream stream) {
+    if (!ctx || n < 0 || m < 0 || m > n || n > ctx->lay.max_points) return HAV_ERR_INVALID;
+    if (m > 0 && (!points || !out_idx)) return HAV_ERR_INVALID;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != ctx->device) return HAV_ERR_INVALID;
+    cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);
+    ctx->last_S = 1;
+    ctx->last_L = 0;
+    if (cudaMemsetAsync(ctx->ws + ctx->lay.barrier, 0, ctx->lay.zero_bytes, strm) != cudaSuccess) return HAV_ERR_CUDA;
+    if (m == 0) return HAV_OK;
+    if (havk::launch_fps(points, static_cast<int>(n), static_cast<int>(m), out_idx, ctx->ws, ctx->lay,
+                         ctx->fps_nblocks, strm) != 0)
+        return HAV_ERR_CUDA;
+    return HAV_OK;
 }
 
 hav_status hav_count(hav_ctx* ctx, const float* points, int64_t n, float s, const float aspect[3],

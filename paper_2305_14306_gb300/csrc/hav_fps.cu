@@ -1,0 +1,134 @@
+// Farthest point sampling (Eq. 1 of Section 3.1), the comparator the paper
+// measures HAVSampler against: one cooperative launch, one bounded grid
+// barrier per selected point.
+//
+// Start at index 0; every point keeps its squared distance to the selected
+// set (binary32, (dx*dx + dy*dy) + dz*dz without contraction); the next pick
+// is the largest distance, ties to the lowest index; picked points are never
+// picked again.
+
+#include <cuda_runtime.h>
+
+#include "hav_device.cuh"
+#include "hav_internal.h"
+
+namespace havk {
+namespace {
+
+constexpr int kFpsThreads = 1024;
+
+// packed (distance bits, inverted index): the maximum is the farthest point,
+// ties to the lowest index; picked points pack to 0 and never win
+__device__ __forceinline__ unsigned long long fps_pack(float d2, int i) {
+    return (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) |
+           static_cast<unsigned long long>(0xffffffffu - static_cast<unsigned>(i));
+}
+
+__global__ void __launch_bounds__(kFpsThreads, 1)
+    fps_kernel(const float* pts, int n, int m, int32_t* out, float* dist, unsigned long long* bmax, Barrier* bar,
+               GlobalHdr* gh, int nblocks) {
+    __shared__ unsigned long long red[32];
+    __shared__ int s_flag;
+    __shared__ unsigned epoch;
+    __shared__ int s_last;
+    const int tid = threadIdx.x;
+    if (tid == 0) epoch = 0u;
+    const int chunk = (n + nblocks - 1) / nblocks;
+    const int a = blockIdx.x * chunk;
+    const int b = min(n, a + chunk);
+    for (int i = a + tid; i < b; i += kFpsThreads) dist[i] = INFINITY;
+    int last = 0;
+    if (blockIdx.x == 0 && tid == 0) out[0] = 0;
+    __syncthreads();
+    for (int j = 1; j < m; ++j) {
+        const float qx = pts[3 * last], qy = pts[3 * last + 1], qz = pts[3 * last + 2];
+        unsigned long long best = 0ull;
+        for (int i = a + tid; i < b; i += kFpsThreads) {
+            float di = dist[i];
+            if (i == last) {
+                di = -1.0f;  // picked: never again
+                dist[i] = di;
+            }
+            if (di < 0.0f) continue;
+            const float dx = __fsub_rn(pts[3 * i], qx);
+            const float dy = __fsub_rn(pts[3 * i + 1], qy);
+            const float dz = __fsub_rn(pts[3 * i + 2], qz);
+            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            if (d2 < di) {
+                di = d2;
+                dist[i] = di;
+            }
+            const unsigned long long k = fps_pack(di, i);
+            best = k > best ? k : best;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+            best = v > best ? v : best;
+        }
+        if ((tid & 31) == 0) red[tid >> 5] = best;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long bb = red[0];
+            for (int w = 1; w < kFpsThreads / 32; ++w) bb = red[w] > bb ? red[w] : bb;
+            bmax[(j & 1) * kMaxBlocks + blockIdx.x] = bb;
+        }
+        if (!grid_sync_impl(bar, gh, static_cast<unsigned>(nblocks), &epoch, &s_flag)) return;
+        // every block finds the same maximum over the block maxima
+        unsigned long long bb = 0ull;
+        for (int k = tid; k < nblocks; k += kFpsThreads) {
+            const unsigned long long v = bmax[(j & 1) * kMaxBlocks + k];
+            bb = v > bb ? v : bb;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, bb, o);
+            bb = v > bb ? v : bb;
+        }
+        if ((tid & 31) == 0) red[tid >> 5] = bb;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long m2 = red[0];
+            for (int w = 1; w < kFpsThreads / 32; ++w) m2 = red[w] > m2 ? red[w] : m2;
+            const int pick = static_cast<int>(0xffffffffu - static_cast<unsigned>(m2 & 0xffffffffull));
+            s_last = (m2 != 0ull && pick >= 0 && pick < n) ? pick : 0;  // m <= n: an unpicked point exists
+            if (blockIdx.x == 0) out[j] = s_last;
+        }
+        __syncthreads();
+        last = s_last;
+    }
+}
+
+}  // namespace
+
+int fps_coresident_blocks(int device) {
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fps_kernel, kFpsThreads, 0) != cudaSuccess) return -1;
+    long long nb = static_cast<long long>(sms) * per_sm;
+    if (nb > kMaxBlocks) nb = kMaxBlocks;
+    return static_cast<int>(nb);
+}
+
+int launch_fps(const float* points, int n, int m, int32_t* out, unsigned char* ws, const Layout& lay, int nblocks,
+               cudaStream_t stream) {
+    // scratch: the distance array in the first log array, block maxima in the phase-timer region
+    float* dist = reinterpret_cast<float*>(ws + lay.dirty[0]);
+    unsigned long long* bmax = reinterpret_cast<unsigned long long*>(ws + lay.ptimes);
+    Barrier* bar = reinterpret_cast<Barrier*>(ws + lay.barrier);
+    GlobalHdr* gh = reinterpret_cast<GlobalHdr*>(ws + lay.ghdr);
+    // fewer blocks than points per block of work would only add barrier arrivals
+    int nb = nblocks;
+    const int want = (n + kFpsThreads - 1) / kFpsThreads;
+    if (want < nb) nb = want < 1 ? 1 : want;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(nb));
+    cfg.blockDim = dim3(kFpsThreads);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fps_kernel, points, n, m, out, dist, bmax, bar, gh, nb) == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace havk

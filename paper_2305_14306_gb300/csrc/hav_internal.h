@@ -162,5 +162,8 @@ int max_coresident_blocks(int device);
 int launch_chain(const Plan& plan, cudaStream_t stream);
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
                  unsigned char* ws, const Layout& lay, int64_t* K, cudaStream_t stream);
+int fps_coresident_blocks(int device);
+int launch_fps(const float* points, int n, int m, int32_t* out, unsigned char* ws, const Layout& lay, int nblocks,
+               cudaStream_t stream);
 
 }  // namespace havk

@@ -63,7 +63,8 @@ _lib = None
 EXPORTS = [
     "hav_params_default", "hav_context_create", "hav_context_destroy", "hav_workspace_bytes",
     "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
-    "hav_count", "hav_status_string", "hav_sample_noalloc", "hav_phase_times_get",
+    "hav_count", "hav_status_string", "hav_sample_noalloc", "hav_phase_times_get", "hav_fps",
+    "hav_context_set_blocks",
 ]
 HAV_FLAG_PHASE_TIMES = 1
 
@@ -106,6 +107,10 @@ def load(path: str = LIB_PATH):
         L.hav_count.restype = C.c_int
         L.hav_status_string.argtypes = [C.c_int]
         L.hav_status_string.restype = C.c_char_p
+        L.hav_context_set_blocks.argtypes = [vp, i32]
+        L.hav_context_set_blocks.restype = C.c_int
+        L.hav_fps.argtypes = [vp, vp, i64, i64, vp, vp]
+        L.hav_fps.restype = C.c_int
         L.hav_phase_times_get.argtypes = [vp, vp, P(C.c_uint64), P(C.c_uint32), i32]
         L.hav_phase_times_get.restype = C.c_int32
         L.hav_sample_noalloc.argtypes = [vp, i64, i64, P(hav_params), vp, vp, vp]
@@ -156,6 +161,10 @@ class Context:
         self.handle = h
         self.max_points = int(max_points)
         self.max_segments = int(max_segments)
+
+    def set_blocks(self, nblocks: int):
+        """Limit the sampler launches of this context to nblocks SMs (0: all)."""
+        _check(load().hav_context_set_blocks(self.handle, int(nblocks)), "hav_context_set_blocks")
 
     def close(self):
         if self.handle:
@@ -253,6 +262,31 @@ def hav_phase_times_get(ctx: Context, max_records: int = 4096, stream=None):
     if w < 0:
         raise HavError(HAV_ERR_CUDA, "hav_phase_times_get")
     return [(int(t[k]), int(g[k])) for k in range(w)]
+
+
+def hav_fps(ctx: Context, points, m: int, out=None, stream=None):
+    """Farthest point sampling (the paper's comparator): m int32 indices in selection order."""
+    import torch
+    points = _points(points)
+    if out is None:
+        out = torch.empty(int(m), dtype=torch.int32, device=points.device)
+    st = load().hav_fps(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0], int(m),
+                        C.c_void_p(out.data_ptr()), _stream_handle(stream))
+    _check(st, "hav_fps")
+    return out
+
+
+def coverage(points, idx, chunk: int = 8192) -> float:
+    """Subset coverage: the largest distance from any input point to its nearest
+    selected point (a measurement for the comparison, computed with torch)."""
+    import torch
+    pts = points.double()
+    sel = pts[idx.long()]
+    worst = torch.zeros((), dtype=torch.float64, device=pts.device)
+    for a in range(0, pts.shape[0], chunk):
+        d = torch.cdist(pts[a:a + chunk], sel)
+        worst = torch.maximum(worst, d.min(dim=1).values.max())
+    return float(worst.item())
 
 
 def hav_count(ctx: Context, points, s: float, aspect=(1.0, 1.0, 1.0), stream=None) -> int:

@@ -1,0 +1,152 @@
+"""Continuous-batching serving loop for the sampler.
+
+Requests (a cloud and its budget m) arrive over time.  The server keeps a
+few *slots*; each slot owns a CUDA stream, a libhav context limited to its
+share of the SMs and device buffers, so the slots' launches run side by
+side on the GPU; requests bring their points in pinned host memory.  Whenever a slot is free, the
+requests that have arrived and wait are packed, first come first served,
+into one segmented ``hav_sample_batched`` launch, as many as fit the slot's
+point capacity and segment limit (admission by workspace memory).  A
+request's points stay on the device from admission to completion; its
+latency runs from its arrival to the moment the host sees its slot's
+completion event.
+
+The plain per-cloud path is the same loop with one slot and one request per
+launch.  Either way every request's indices equal a stand-alone call's.
+This module only orchestrates: every step of the sampling runs in libhav's
+kernels.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import hav
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the run
+    points: object          # (n, 3) float32 torch tensor in pinned host memory
+    m: int                  # budget (one level)
+
+
+@dataclass
+class Result:
+    indices: np.ndarray
+    latency: float          # seconds from arrival to completion seen by the host
+    batch: int              # requests in the launch that served it
+
+
+@dataclass
+class _Slot:
+    stream: object
+    ctx: hav.Context
+    d_pts: object           # device float32 (cap, 3)
+    d_out: object           # device int32 (cap,)
+    h_out: object           # pinned int32 (cap,)
+    event: object = None
+    batch: list = field(default_factory=list)
+    offsets: np.ndarray = None
+
+
+class Server:
+    def __init__(self, slots: int = 4, slot_points: int = 2_000_000, max_segments: int = 64,
+                 params: hav.hav_params | None = None, share_sms: bool = True):
+        import torch
+        self.torch = torch
+        self.params = params or hav.params()
+        self.max_segments = max_segments
+        self.slot_points = slot_points
+        self.slots = []
+        for _ in range(slots):
+            ctx = hav.Context(slot_points, max_segments)
+            self.slots.append(_Slot(
+                stream=torch.cuda.Stream(), ctx=ctx,
+                d_pts=torch.empty((slot_points, 3), dtype=torch.float32, device="cuda"),
+                d_out=torch.empty(slot_points, dtype=torch.int32, device="cuda"),
+                h_out=torch.empty(slot_points, dtype=torch.int32).pin_memory()))
+        if share_sms and slots > 1:
+            # co-resident launches: each slot gets an equal share of the SMs
+            full = self._max_blocks()
+            for s in self.slots:
+                s.ctx.set_blocks(max(1, full // slots))
+
+    def _max_blocks(self):
+        props = self.torch.cuda.get_device_properties(self.torch.cuda.current_device())
+        return props.multi_processor_count
+
+    def close(self):
+        for s in self.slots:
+            s.ctx.close()
+
+    # ------------------------------------------------------------------
+    def _launch(self, slot: _Slot, batch):
+        torch = self.torch
+        sizes = np.array([r.points.shape[0] for r in batch], dtype=np.int64)
+        offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        ms = np.array([[r.m for r in batch]], dtype=np.int64)
+        total, mt = int(offs[-1]), int(ms.sum())
+        with torch.cuda.stream(slot.stream):
+            for r, a in zip(batch, offs[:-1]):  # pinned host -> the slot's device buffer
+                slot.d_pts[int(a):int(a) + r.points.shape[0]].copy_(r.points, non_blocking=True)
+            out = slot.d_out[:mt]
+            hav.hav_sample_batched(slot.ctx, slot.d_pts[:total], offs, ms, self.params, outs=[out],
+                                   stream=slot.stream)
+            slot.h_out[:mt].copy_(out, non_blocking=True)
+            slot.event = torch.cuda.Event()
+            slot.event.record(slot.stream)
+        slot.batch = batch
+        slot.offsets = np.concatenate([[0], np.cumsum(ms[0])])
+
+    def _finish(self, slot: _Slot, now: float, results: dict):
+        st, per = hav.hav_status_get(slot.ctx, len(slot.batch), stream=slot.stream)
+        if st != hav.HAV_OK:
+            raise hav.HavError(st, "serving batch")
+        ho = slot.h_out.numpy()
+        for r, a, b in zip(slot.batch, slot.offsets[:-1], slot.offsets[1:]):
+            results[r.rid] = Result(ho[a:b].copy(), now - r.arrival, len(slot.batch))
+        slot.batch = []
+        slot.event = None
+
+    def serve(self, requests, clock=time.perf_counter) -> dict:
+        """Run the requests with their arrival times (real time); returns rid -> Result."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        for r in pending:
+            if r.points.shape[0] > self.slot_points:
+                raise ValueError(f"request {r.rid} has more points than a slot holds")
+        waiting = collections.deque()
+        results = {}
+        t0 = clock()
+        while pending or waiting or any(s.batch for s in self.slots):
+            now = clock() - t0
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.popleft())
+            progressed = False
+            for s in self.slots:
+                if s.batch and s.event.query():
+                    self._finish(s, clock() - t0, results)
+                    progressed = True
+            for s in self.slots:
+                if s.batch or not waiting:
+                    continue
+                batch, pts = [], 0
+                while waiting and len(batch) < self.max_segments and \
+                        pts + waiting[0].points.shape[0] <= self.slot_points:
+                    r = waiting.popleft()
+                    batch.append(r)
+                    pts += r.points.shape[0]
+                self._launch(s, batch)
+                progressed = True
+            if not progressed:
+                time.sleep(20e-6)
+        return results
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))]

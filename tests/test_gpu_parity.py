@@ -245,3 +245,31 @@ def test_c4_batch_64_lidar_clouds(hv):
         check_batched(hv, ctx, clouds, [[n // 4 for n in sizes], [n // 16 for n in sizes]])
     finally:
         ctx.close()
+
+
+# ------------------------------------------------------ FPS comparator
+@pytest.mark.parametrize("n,m,seed", [(16384, 512, 0), (16384, 4096, 1), (1000, 100, 2), (5, 5, 3), (3000, 1, 4)])
+def test_fps_matches_oracle(hv, ctx, oracle_mod, n, m, seed):
+    pts = scenes.uniform_box(n, seed)
+    got = hv.hav_fps(ctx, dev(pts), m).cpu().numpy()
+    assert hv.hav_status_get(ctx)[0] == 0
+    assert np.array_equal(got, oracle_mod.fps(pts, m))
+
+
+def test_fps_hand_case_and_duplicates(hv, ctx, oracle_mod):
+    line = np.array([[x, 0, 0] for x in range(11)], dtype=np.float32)
+    assert list(hv.hav_fps(ctx, dev(line), 4).cpu().numpy()) == [0, 10, 5, 2]
+    dup = np.repeat(scenes.uniform_box(50, 8), 4, axis=0)
+    assert np.array_equal(hv.hav_fps(ctx, dev(dup), 120).cpu().numpy(), oracle_mod.fps(dup, 120))
+
+
+def test_coverage_fps_vs_hav(hv, ctx):
+    # informative comparison (Section 3.1): FPS bounds the covering radius best;
+    # HAV is close to it, a uniform random subset is far worse
+    pts = scenes.uniform_box(16384, 3)
+    d = dev(pts)
+    hav_idx = hv.hav_sample(ctx, d, 4096)
+    fps_idx = hv.hav_fps(ctx, d, 4096)
+    rnd = torch.from_numpy(np.sort(np.random.default_rng(0).choice(16384, 4096, replace=False))).cuda()
+    c_hav, c_fps, c_rnd = hv.coverage(d, hav_idx), hv.coverage(d, fps_idx), hv.coverage(d, rnd)
+    assert c_fps <= c_hav < c_rnd

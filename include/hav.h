@@ -110,8 +110,32 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
 /* Number of thread blocks (one per SM) the context's sampler launches use:
  * 1..the device's co-resident maximum, or 0 for that maximum (the default).
  * Contexts limited to disjoint shares of the SMs can run their calls
- * concurrently on different streams (the serving loop does this). */
+ * concurrently on different streams (the serving loop does this).  A call
+ * with S segments uses at least ceil(S / 7) blocks whatever the setting
+ * (HAV_ERR_INVALID if that exceeds the co-resident maximum). */
 hav_status hav_context_set_blocks(hav_ctx* ctx, int32_t nblocks);
+
+/* Launch-shape knobs of a context (the autotuner sets them; the paper has no
+ * counterpart).  No setting changes a result: every call returns the same
+ * indices, status and trace for every tuning, because the bisection's
+ * decisions (Section 3.3) and the per-voxel choices (Section 3.2) depend only
+ * on the points, never on how the work is cut. */
+typedef struct {
+    int64_t spec_points[3];  /* level sizes (points, all segments) up to which one
+                                pass evaluates 4, 3 or 2 bisection steps at once
+                                (larger levels: one step per pass); 0 <= [0] <= [1]
+                                <= [2] <= 2^31 */
+    int32_t chunk_min;       /* smallest work item in points, 1..65536 */
+    int32_t nblocks;         /* as in hav_context_set_blocks (0: all co-resident) */
+} hav_tuning;
+
+/* Copy the context's tuning into *out (the defaults after creation:
+ * {32768, 131072, 262144}, 64, the co-resident maximum). */
+hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out);
+
+/* Replace the context's tuning.  HAV_ERR_INVALID (and no change) on a value
+ * outside the ranges above.  Takes effect from the next call. */
+hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t);
 
 /* Release the context and its device memory.  Waits for the device.  NULL is ignored. */
 void hav_context_destroy(hav_ctx* ctx);

@@ -15,6 +15,8 @@ struct hav_ctx {
     int device;
     int nblocks;
     int max_blocks;
+    int chunk_min;
+    int64_t spec_n[3];
     int fps_nblocks;
     havk::Layout lay;
     unsigned char* ws;
@@ -99,6 +101,10 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
     c->nblocks = nb;
     c->max_blocks = nb;
     c->fps_nblocks = fnb;
+    c->chunk_min = havk::kChunkMin;
+    c->spec_n[0] = havk::kSpecN4;
+    c->spec_n[1] = havk::kSpecN3;
+    c->spec_n[2] = havk::kSpecN2;
     c->lay = havk::make_layout(max_points, max_segments);
     if (cudaMalloc(&c->ws, c->lay.total) != cudaSuccess) {
         delete c;
@@ -117,6 +123,27 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
 hav_status hav_context_set_blocks(hav_ctx* ctx, int32_t nblocks) {
     if (!ctx || nblocks < 0 || nblocks > ctx->max_blocks) return HAV_ERR_INVALID;
     ctx->nblocks = nblocks == 0 ? ctx->max_blocks : nblocks;
+    return HAV_OK;
+}
+
+hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out) {
+    if (!ctx || !out) return HAV_ERR_INVALID;
+    for (int k = 0; k < 3; ++k) out->spec_points[k] = ctx->spec_n[k];
+    out->chunk_min = ctx->chunk_min;
+    out->nblocks = ctx->nblocks;
+    return HAV_OK;
+}
+
+hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t) {
+    if (!ctx || !t) return HAV_ERR_INVALID;
+    for (int k = 0; k < 3; ++k)
+        if (t->spec_points[k] < 0 || t->spec_points[k] > (1ll << 31)) return HAV_ERR_INVALID;
+    if (t->spec_points[0] > t->spec_points[1] || t->spec_points[1] > t->spec_points[2]) return HAV_ERR_INVALID;
+    if (t->chunk_min < 1 || t->chunk_min > 65536) return HAV_ERR_INVALID;
+    if (t->nblocks < 0 || t->nblocks > ctx->max_blocks) return HAV_ERR_INVALID;
+    for (int k = 0; k < 3; ++k) ctx->spec_n[k] = t->spec_points[k];
+    ctx->chunk_min = t->chunk_min;
+    ctx->nblocks = t->nblocks == 0 ? ctx->max_blocks : t->nblocks;
     return HAV_OK;
 }
 
@@ -170,10 +197,16 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
     plan->t_max = params->t_max;
     plan->sigma_num = params->sigma_num;
     plan->sigma_den = params->sigma_den;
-    plan->nblocks = ctx->nblocks;
-    plan->spec_n[0] = havk::kSpecN4;
-    plan->spec_n[1] = havk::kSpecN3;
-    plan->spec_n[2] = havk::kSpecN2;
+    // a block tracks at most kLocalItems work items of a level, and a level
+    // has at most nblocks + S of them at the smallest speculation depth
+    const int min_blocks = (num_segments + havk::kLocalItems - 2) / (havk::kLocalItems - 1);
+    plan->nblocks = ctx->nblocks < min_blocks ? min_blocks : ctx->nblocks;
+    if (plan->nblocks > ctx->max_blocks) {
+        delete plan;
+        return HAV_ERR_INVALID;
+    }
+    plan->chunk_min = ctx->chunk_min;
+    for (int k = 0; k < 3; ++k) plan->spec_n[k] = ctx->spec_n[k];
     for (int a = 0; a < 3; ++a) plan->aspect[a] = params->aspect[a];
     for (int j = 0; j < num_levels; ++j) plan->out[j] = out_idx[j];
     if (params->flags & HAV_FLAG_PHASE_TIMES) {

@@ -29,6 +29,8 @@ constexpr int kMaxCand = (1 << kMaxSpecDepth) - 1;  // candidate sizes per pass 
 constexpr int64_t kSpecN4 = 32768;
 constexpr int64_t kSpecN3 = 131072;
 constexpr int64_t kSpecN2 = 262144;
+constexpr int kChunkMin = 64;              // default smallest work item (points)
+constexpr int kLocalItems = 8;             // work items one block can own in a level
 
 constexpr unsigned long long kEmptyKey = ~0ull;  // valid keys use 63 bits
 constexpr unsigned long long kEmptyVal = ~0ull;  // packed (d^2 bits, index) never reaches it
@@ -148,7 +150,7 @@ struct Plan {
     int32_t* out[kMaxLevels]; // per-level outputs (device)
     unsigned long long* ptimes;  // phase timer records, or null (HAV_FLAG_PHASE_TIMES)
     int32_t ptimes_cap;
-    int32_t pad2;
+    int32_t chunk_min;           // smallest work item (points)
     int64_t spec_n[3];           // level sizes up to which a pass looks 4, 3, 2 steps ahead
     int32_t S, L, layers, ratio, t_max, sigma_num, sigma_den, nblocks;
     float aspect[3];

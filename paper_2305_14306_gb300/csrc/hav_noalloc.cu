@@ -122,6 +122,7 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
         plan.sigma_num = params->sigma_num;
         plan.sigma_den = params->sigma_den;
         plan.nblocks = ds->nblocks;
+        plan.chunk_min = havk::kChunkMin;
         for (int a = 0; a < 3; ++a) plan.aspect[a] = params->aspect[a];
         plan.out[0] = out_idx;
         plan.off0[0] = 0;

@@ -49,7 +49,6 @@ namespace {
 static_assert(kHistBins % kThreads == 0, "the cut-off scan gives each thread whole bins");
 constexpr int kSetSlots = 16384;   // block-local dedupe set of a bisection pass (128 KB + 32 KB list)
 constexpr int kSelSlots = 8192;    // block-local argmin table of the selection (128 KB + 16 KB list)
-constexpr int kLocalItems = 8;     // work items one block can own in a level
 constexpr int kBucketMin = 1 << 17;
 constexpr size_t kDynSmem = 163840;
 constexpr int kInFlight = 4;       // points loaded ahead per thread in a pass
@@ -255,47 +254,47 @@ __device__ void level_setup(const Plan& P, int j, Smem& st) {
     }
     __syncthreads();
     const long long nl = st.n_level;
-    // speculation depth: deeper on small levels, where a pass is latency-bound
-    int depth = nl <= P.spec_n[0] ? 4 : nl <= P.spec_n[1] ? 3 : nl <= P.spec_n[2] ? 2 : 1;
-    long long chunk = (nl + P.nblocks - 1) / P.nblocks;  // every block gets a share
-    if (chunk < 64) chunk = 64;
-    if (depth > 1) {
-        // a candidate's share of the block set must stay at most half full
-        const int ncand = (1 << depth) - 1;
-        int lg2 = 0;
-        while ((1 << (lg2 + 1)) * ncand <= kSetSlots) ++lg2;
-        const long long cap_pts = (1ll << lg2) / 2;
-        if (chunk > cap_pts) chunk = cap_pts;
-    }
     o = block_excl_scan<long long>(mm, &tot, st.scan_ll);
-    if (s == 0) {
-        st.m_total = tot;
-        st.chunk = static_cast<int>(chunk);
-    }
+    if (s == 0) st.m_total = tot;
     o = block_excl_scan<long long>(C, &tot, st.scan_ll);
     if (s < S) {
         st.tab_off[s] = o;
         st.cand_off[s] = o / 2;
     }
-    const long long items = (s < S) ? (n + chunk - 1) / chunk : 0;
-    o = block_excl_scan<long long>(items, &tot, st.scan_ll);
-    if (s < S) st.item0[s] = static_cast<int>(o);
-    if (s == 0) {
-        st.item0[S] = static_cast<int>(tot);
-        st.items_total = static_cast<int>(tot);
-    }
     for (int k = s; k < 2 * kLocalItems * kMaxCand; k += kThreads) (&st.dcnt[0][0][0])[k] = 0;
-    if (s == 0) {
-        const long long stride = st.tab_off[S - 1] + (1ll << st.cap_log2[S - 1]);
-        while (depth > 1 && (((1ll << depth) - 1) * stride > P.lay.tab_slots ||
-                             ((1ll << depth) - 1) * nl > P.lay.dirty_slots ||
-                             st.items_total > static_cast<int>(kLocalItems) * P.nblocks))
-            --depth;
-        st.tab_stride = stride;
-        st.ncand = (1 << depth) - 1;
+    __syncthreads();
+    const long long stride = st.tab_off[S - 1] + (1ll << st.cap_log2[S - 1]);
+    // speculation depth: deeper on small levels, where a pass is latency-bound;
+    // a shallower one wherever the candidate tables, their logs or the work
+    // items a block tracks would not fit
+    int depth = nl <= P.spec_n[0] ? 4 : nl <= P.spec_n[1] ? 3 : nl <= P.spec_n[2] ? 2 : 1;
+    while (depth > 1 && (((1ll << depth) - 1) * stride > P.lay.tab_slots ||
+                         ((1ll << depth) - 1) * nl > P.lay.dirty_slots))
+        --depth;
+    for (;; --depth) {
+        long long chunk = (nl + P.nblocks - 1) / P.nblocks;  // every block gets a share
+        if (chunk < P.chunk_min) chunk = P.chunk_min;
+        const int ncand = (1 << depth) - 1;
         int lg2 = 0;
-        while ((1 << (lg2 + 1)) * st.ncand <= kSetSlots) ++lg2;
-        st.setc_log2 = lg2;
+        while ((1 << (lg2 + 1)) * ncand <= kSetSlots) ++lg2;
+        // a candidate's share of the block set must stay at most half full
+        if (depth > 1 && chunk > (1ll << lg2) / 2) chunk = (1ll << lg2) / 2;
+        const long long items = (s < S) ? (n + chunk - 1) / chunk : 0;
+        o = block_excl_scan<long long>(items, &tot, st.scan_ll);
+        // (depth 1 always fits: chunk >= nl / nblocks gives at most nblocks + S
+        // items, and the host keeps S <= (kLocalItems - 1) * nblocks)
+        if (depth == 1 || (tot <= static_cast<long long>(kLocalItems) * P.nblocks && tot <= kMaxItems)) {
+            if (s < S) st.item0[s] = static_cast<int>(o);
+            if (s == 0) {
+                st.item0[S] = static_cast<int>(tot);
+                st.items_total = static_cast<int>(tot);
+                st.chunk = static_cast<int>(chunk);
+                st.tab_stride = stride;
+                st.ncand = ncand;
+                st.setc_log2 = lg2;
+            }
+            break;
+        }
     }
     __syncthreads();
 }

@@ -50,6 +50,14 @@ class hav_layer_trace(C.Structure):
     ]
 
 
+class hav_tuning(C.Structure):
+    _fields_ = [
+        ("spec_points", C.c_int64 * 3),
+        ("chunk_min", C.c_int32),
+        ("nblocks", C.c_int32),
+    ]
+
+
 class HavError(RuntimeError):
     def __init__(self, status: int, where: str = ""):
         self.status = status
@@ -64,7 +72,7 @@ EXPORTS = [
     "hav_params_default", "hav_context_create", "hav_context_destroy", "hav_workspace_bytes",
     "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
     "hav_count", "hav_status_string", "hav_sample_noalloc", "hav_phase_times_get", "hav_fps",
-    "hav_context_set_blocks",
+    "hav_context_set_blocks", "hav_context_get_tuning", "hav_context_set_tuning",
 ]
 HAV_FLAG_PHASE_TIMES = 1
 
@@ -109,6 +117,10 @@ def load(path: str = LIB_PATH):
         L.hav_status_string.restype = C.c_char_p
         L.hav_context_set_blocks.argtypes = [vp, i32]
         L.hav_context_set_blocks.restype = C.c_int
+        L.hav_context_get_tuning.argtypes = [vp, P(hav_tuning)]
+        L.hav_context_get_tuning.restype = C.c_int
+        L.hav_context_set_tuning.argtypes = [vp, P(hav_tuning)]
+        L.hav_context_set_tuning.restype = C.c_int
         L.hav_fps.argtypes = [vp, vp, i64, i64, vp, vp]
         L.hav_fps.restype = C.c_int
         L.hav_phase_times_get.argtypes = [vp, vp, P(C.c_uint64), P(C.c_uint32), i32]
@@ -165,6 +177,23 @@ class Context:
     def set_blocks(self, nblocks: int):
         """Limit the sampler launches of this context to nblocks SMs (0: all)."""
         _check(load().hav_context_set_blocks(self.handle, int(nblocks)), "hav_context_set_blocks")
+
+    def get_tuning(self) -> dict:
+        """The context's launch-shape knobs (no knob changes a result)."""
+        t = hav_tuning()
+        _check(load().hav_context_get_tuning(self.handle, C.byref(t)), "hav_context_get_tuning")
+        return {"spec_points": list(t.spec_points), "chunk_min": t.chunk_min, "nblocks": t.nblocks}
+
+    def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None):
+        """Change some of the knobs; the others keep their values."""
+        cur = self.get_tuning()
+        t = hav_tuning()
+        sp = cur["spec_points"] if spec_points is None else list(spec_points)
+        for k in range(3):
+            t.spec_points[k] = int(sp[k])
+        t.chunk_min = int(cur["chunk_min"] if chunk_min is None else chunk_min)
+        t.nblocks = int(cur["nblocks"] if nblocks is None else nblocks)
+        _check(load().hav_context_set_tuning(self.handle, C.byref(t)), "hav_context_set_tuning")
 
     def close(self):
         if self.handle:

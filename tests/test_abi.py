@@ -49,8 +49,9 @@ def test_struct_layouts_match_header(libhav, tmp_path):
     src = tmp_path / "s.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "hav.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(hav_params), sizeof(hav_layer_trace),'
-        ' offsetof(hav_layer_trace, s), offsetof(hav_layer_trace, K)); return 0;}\n')
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(hav_params), sizeof(hav_layer_trace),'
+        ' offsetof(hav_layer_trace, s), offsetof(hav_layer_trace, K), sizeof(hav_tuning),'
+        ' offsetof(hav_tuning, chunk_min)); return 0;}\n')
     exe = tmp_path / "s"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
@@ -60,6 +61,8 @@ def test_struct_layouts_match_header(libhav, tmp_path):
     assert int(out[1]) == ctypes.sizeof(hav.hav_layer_trace)
     assert int(out[2]) == hav.hav_layer_trace.s.offset
     assert int(out[3]) == hav.hav_layer_trace.K.offset
+    assert int(out[4]) == ctypes.sizeof(hav.hav_tuning)
+    assert int(out[5]) == hav.hav_tuning.chunk_min.offset
 
 
 def test_params_default_and_status_strings(libhav):
@@ -83,3 +86,5 @@ def test_argument_errors_need_no_device(libhav):
     assert L.hav_context_create(ctypes.byref(h), 10, 257) == hav.HAV_ERR_INVALID
     assert L.hav_sample(None, None, 10, 5, None, None, None) == hav.HAV_ERR_INVALID
     assert L.hav_workspace_bytes(1 << 20, 1) > 0
+    assert L.hav_context_get_tuning(None, None) == hav.HAV_ERR_INVALID
+    assert L.hav_context_set_tuning(None, None) == hav.HAV_ERR_INVALID

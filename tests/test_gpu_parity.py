@@ -235,6 +235,61 @@ def test_batched_error_is_contained(hv, ctx):
     assert list(parts[2]) == list(range(700))
 
 
+TUNINGS = [
+    {"spec_points": [0, 0, 0], "chunk_min": 64},                       # plain bisection
+    {"spec_points": [1 << 31, 1 << 31, 1 << 31], "chunk_min": 32},     # depth 4 wherever it fits
+    {"spec_points": [65536, 262144, 524288], "chunk_min": 1024},
+    {"spec_points": [32768, 131072, 262144], "chunk_min": 64, "nblocks": 5},
+]
+
+
+def test_tuning_never_changes_results(hv):
+    # the launch-shape knobs cut the work differently; indices, status and
+    # traces stay those of the default tuning (which the oracle pins above)
+    sizes = [20000, 1, 0, 513, 70000, 4096, 33333, 12, 150000, 999]
+    clouds = [scenes.lidar_exact(n, 40 + i) if n >= 20000 else scenes.uniform_box(n, 40 + i)
+              for i, n in enumerate(sizes)]
+    ms = [[n // 4 for n in sizes], [n // 16 for n in sizes]]
+    big = scenes.room_scene(300_000, seed=3)
+    c = hv.Context(1 << 20, 16)
+    try:
+        ref_b = _batched(hv, c, clouds, ms)
+        ref_c = run_levels(hv, c, big, [75_000, 18_750, 4_687])
+        for t in TUNINGS:
+            c.set_tuning(**t)
+            got_b = _batched(hv, c, clouds, ms)
+            got_c = run_levels(hv, c, big, [75_000, 18_750, 4_687])
+            for a, b in zip(got_b[0], ref_b[0]):
+                assert np.array_equal(a, b), t
+            assert got_b[1] == ref_b[1] and got_b[2] == ref_b[2], t
+            for j in range(len(ref_c[0])):
+                assert np.array_equal(got_c[0][j], ref_c[0][j]), (t, j)
+            assert len(got_b[3]) == len(ref_b[3]) and len(got_c[2]) == len(ref_c[2])
+            for x, y in zip(got_b[3] + got_c[2], ref_b[3] + ref_c[2]):
+                assert G.traces_equal(x, y) is None, (t, G.traces_equal(x, y))
+            c.set_tuning(spec_points=[32768, 131072, 262144], chunk_min=64, nblocks=0)
+        assert c.get_tuning()["chunk_min"] == 64
+        with pytest.raises(hv.HavError):
+            c.set_tuning(spec_points=[3, 2, 1])
+        with pytest.raises(hv.HavError):
+            c.set_tuning(chunk_min=0)
+    finally:
+        c.close()
+
+
+def test_many_segments_on_few_blocks(hv):
+    # 200 segments on a context limited to one block: the call widens to
+    # ceil(200 / 7) blocks so that no block owns more work items than it tracks
+    clouds = [scenes.uniform_box(300 + 37 * i, 500 + i) for i in range(200)]
+    total = sum(c.shape[0] for c in clouds)
+    c = hv.Context(total, 200)
+    try:
+        c.set_blocks(1)
+        check_batched(hv, c, clouds, [[x.shape[0] // 4 for x in clouds]])
+    finally:
+        c.close()
+
+
 @pytest.mark.slow
 def test_c4_batch_64_lidar_clouds(hv):
     clouds = scenes.lidar_batch(64, seed=0)

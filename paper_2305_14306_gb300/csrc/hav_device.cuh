@@ -51,6 +51,12 @@ __device__ __forceinline__ unsigned long long slot_mix(unsigned long long k) {
     k ^= k >> 32;
     return k;
 }
+// Slot hash of the block-local sets (any mixing works there): multiplicative
+// hashing of the two 32-bit halves, top bits.
+__device__ __forceinline__ unsigned smem_hash(unsigned long long k, int log2) {
+    const unsigned h = static_cast<unsigned>(k) * 0x9E3779B1u + static_cast<unsigned>(k >> 32) * 0x85EBCA77u;
+    return h >> (32 - log2);
+}
 // Cut-off priority: the SplitMix64 output finaliser (Steele, Lea, Flood 2014).
 __device__ __forceinline__ unsigned long long priority(unsigned long long z) {
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
@@ -148,41 +154,49 @@ __device__ __forceinline__ void find_or_insert_batch(unsigned long long* const (
     const unsigned mask = static_cast<unsigned>((1ull << cap_log2) - 1);
     unsigned sl[U];
     unsigned long long cur[U];
-    // the home slot of every key is claimed with a compare-and-swap straight
-    // away (one round trip for a fresh key), all U of them before any result
-    // is used
+    // every probe is a compare-and-swap (it returns the slot's key whether or
+    // not it swaps: one round trip per probe), and the probes of all U keys
+    // are in flight together
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         sl[u] = static_cast<unsigned>(slot_mix(key[u]) >> (64 - cap_log2));
         cur[u] = (key[u] != kEmptyKey) ? atomicCAS(T[u] + sl[u], kEmptyKey, key[u]) : kEmptyKey;
     }
+    bool open[U];
+    bool any = false;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         fresh[u] = false;
         slot[u] = -1;
+        open[u] = false;
         if (key[u] == kEmptyKey) continue;
         if (cur[u] == kEmptyKey || cur[u] == key[u]) {
             slot[u] = sl[u];
             fresh[u] = (cur[u] == kEmptyKey);
-            continue;
+        } else {
+            open[u] = true;
+            any = true;
         }
-        // collision: linear probing from the next slot
-        unsigned s2 = (sl[u] + 1) & mask;
-        for (unsigned probe = 1; probe <= mask; ++probe) {
-            const unsigned long long c = ld_strong64(T[u] + s2);
-            if (c == key[u]) {
-                slot[u] = s2;
-                break;
+    }
+    // collisions: linear probing from the next slot
+    for (unsigned probe = 1; any && probe <= mask; ++probe) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!open[u]) continue;
+            sl[u] = (sl[u] + 1) & mask;
+            cur[u] = atomicCAS(T[u] + sl[u], kEmptyKey, key[u]);
+        }
+        any = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!open[u]) continue;
+            if (cur[u] == kEmptyKey || cur[u] == key[u]) {
+                slot[u] = sl[u];
+                fresh[u] = (cur[u] == kEmptyKey);
+                open[u] = false;
+            } else {
+                any = true;
             }
-            if (c == kEmptyKey) {
-                const unsigned long long prev = atomicCAS(T[u] + s2, kEmptyKey, key[u]);
-                if (prev == kEmptyKey || prev == key[u]) {
-                    slot[u] = s2;
-                    fresh[u] = (prev == kEmptyKey);
-                    break;
-                }
-            }
-            s2 = (s2 + 1) & mask;
         }
     }
 }
@@ -190,15 +204,35 @@ __device__ __forceinline__ void find_or_insert_batch(unsigned long long* const (
 // Warp-aggregated append to a shared-memory list: every lane of the warp
 // calls it (flag false for lanes with nothing to add); returns the lane's
 // position, or -1.
-__device__ __forceinline__ int warp_append(bool flag, unsigned* counter) {
+template <typename T>
+__device__ __forceinline__ int warp_append(bool flag, T* counter) {
     const unsigned m = __ballot_sync(0xffffffffu, flag);
     if (!m) return -1;
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(m) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(counter, static_cast<unsigned>(__popc(m)));
+    T base = 0;
+    if (lane == leader) base = atomicAdd(counter, static_cast<T>(__popc(m)));
     base = __shfl_sync(0xffffffffu, base, leader);
-    return flag ? static_cast<int>(base + __popc(m & ((1u << lane) - 1u))) : -1;
+    return flag ? static_cast<int>(base) + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
+// As warp_append with one counter per key (key indexes counters): the lanes
+// of each key share one atomic add.  Whole warp calls, converged.
+template <typename T>
+__device__ __forceinline__ int warp_append_keyed(bool flag, int key, T* counters) {
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (!m) return -1;
+    int pos = -1;
+    if (flag) {
+        const int lane = threadIdx.x & 31;
+        const unsigned grp = __match_any_sync(m, key);
+        const int leader = __ffs(grp) - 1;
+        T base = 0;
+        if (lane == leader) base = atomicAdd(counters + key, static_cast<T>(__popc(grp)));
+        base = __shfl_sync(m, base, leader);
+        pos = static_cast<int>(base) + __popc(grp & ((1u << lane) - 1u));
+    }
+    return pos;
 }
 
 // Block-local set in shared memory (a filter in front of the global table):
@@ -206,7 +240,8 @@ __device__ __forceinline__ int warp_append(bool flag, unsigned* counter) {
 // when the probe limit is reached (the caller then goes to the global table).
 template <int kSlots>
 __device__ __forceinline__ int smem_insert(unsigned long long* set, unsigned long long key, bool* fresh) {
-    unsigned slot = static_cast<unsigned>(slot_mix(key)) & (kSlots - 1);
+    static_assert(kSlots > 1 && (kSlots & (kSlots - 1)) == 0, "power of two");
+    unsigned slot = smem_hash(key, __builtin_ctz(kSlots));
     *fresh = false;
 #pragma unroll 1
     for (int probe = 0; probe < 32; ++probe) {
@@ -228,7 +263,7 @@ __device__ __forceinline__ int smem_insert(unsigned long long* set, unsigned lon
 // smem_insert on a set of (1 << log2) slots starting at set (runtime size).
 __device__ __forceinline__ int smem_insert_n(unsigned long long* set, int log2, unsigned long long key, bool* fresh) {
     const unsigned m = (1u << log2) - 1u;
-    unsigned slot = static_cast<unsigned>(slot_mix(key)) & m;
+    unsigned slot = smem_hash(key, log2);
     *fresh = false;
 #pragma unroll 1
     for (int probe = 0; probe < 32; ++probe) {

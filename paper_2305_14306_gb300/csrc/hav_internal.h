@@ -85,7 +85,7 @@ struct Layout {
     size_t barrier, ghdr, seghdr, zero_bytes;  // [barrier, barrier+zero_bytes) zeroed per call
     size_t clean;          // 1 when every hash-table slot is empty (kept across calls)
     size_t lstate, hist, partial_sf, partial_cmp, pitem, trace, ptimes;
-    size_t ord[2], orig[2], taken[2], wpre, dirty[2], bkt;
+    size_t ord[2], orig[2], taken[2], wpre, posof, dirty[2], bkt;
     size_t tabk[2], tabv, cand;
     size_t total;
 };
@@ -132,6 +132,7 @@ inline Layout make_layout(int64_t N, int32_t S, bool spec_room = true) {
         L.dirty[b] = take(sizeof(uint32_t) * L.dirty_slots + 16);
     }
     L.wpre = take(sizeof(uint32_t) * L.taken_words);
+    L.posof = take(sizeof(int32_t) * N + 16);
     L.bkt = take(sizeof(uint32_t) * 2 * 4096);
     L.tabk[0] = take(sizeof(unsigned long long) * L.tab_slots);
     L.tabk[1] = take(sizeof(unsigned long long) * L.tab_slots);

@@ -11,7 +11,7 @@
 // library is loaded, so no call allocates.
 //
 // The scratch holds the workspace of one cloud of up to
-// kNoAllocMaxPoints = 32,768 points (5.06 MB of the 6 MiB array).  Every GPU
+// kNoAllocMaxPoints = 32,768 points (6.07 MB of the 6.29 MB array).  Every GPU
 // that loads libhav.so keeps this array until the process exits.
 
 #include <cuda_runtime.h>

@@ -48,10 +48,12 @@ namespace {
 
 static_assert(kHistBins % kThreads == 0, "the cut-off scan gives each thread whole bins");
 constexpr int kSetSlots = 16384;   // block-local dedupe set of a bisection pass (128 KB + 32 KB list)
+constexpr size_t kPassSmem = static_cast<size_t>(kSetSlots) * 10;
 constexpr int kSelSlots = 8192;    // block-local argmin table of the selection (128 KB + 16 KB list)
+constexpr size_t kSelSmem = static_cast<size_t>(kSelSlots) * 18;
+constexpr size_t kDynSmem = kPassSmem > kSelSmem ? kPassSmem : kSelSmem;
 constexpr int kBucketMin = 1 << 17;
-constexpr size_t kDynSmem = 163840;
-constexpr int kInFlight = 4;       // points loaded ahead per thread in a pass
+constexpr int kInFlight = 4;       // points loaded ahead per thread
 constexpr int kProbes = 2;         // global first probes issued together per thread
 static_assert(kSetSlots % (kProbes * kThreads) == 0 && kSelSlots % (kProbes * kThreads) == 0,
               "flush loops take kProbes slots per thread per step");
@@ -88,7 +90,6 @@ struct Smem {
     // candidate grids of a speculative pass, per owned item
     Grid cgrid[kLocalItems][kMaxCand];
     int cvalid[kLocalItems][kMaxCand];
-    unsigned ccount[kMaxCand];
     unsigned rbits;
     int ncand;
     int setc_log2;
@@ -127,6 +128,7 @@ struct Dev {
     hav_layer_trace* tr;   // [L][S][kMaxLayers]
     float4* ord[2];        // level input in processing order: x, y, z, level index
     int32_t* orig[2];      // original (segment-local) index by level index
+    int32_t* posof;        // staged position by level index (current level)
     uint32_t* taken[2];    // by level index
     uint32_t* wpre;        // block-local prefix of taken bits per mask word
     uint32_t* dirty[2];    // fresh-insert logs, item-owned ranges of the level index space
@@ -170,6 +172,16 @@ __device__ __forceinline__ bool is_taken(const uint32_t* tk, int g) {
 }
 __device__ __forceinline__ void set_taken(uint32_t* tk, int g) {
     atomicOr(&tk[g >> 5], 1u << (g & 31));
+}
+// A taken point also carries -(g + 2) in its staged entry, so that later
+// layers skip it without reading the mask.
+__device__ __forceinline__ void mark_taken(uint32_t* tk, float4* ord, const int32_t* posof, int g) {
+    set_taken(tk, g);
+    reinterpret_cast<int*>(ord + posof[g])[3] = -(g + 2);
+}
+__device__ __forceinline__ int level_index(float w) {
+    const int x = __float_as_int(w);
+    return x >= 0 ? x : -x - 2;
 }
 
 template <typename T>
@@ -278,8 +290,21 @@ __device__ void level_setup(const Plan& P, int j, Smem& st) {
         int lg2 = 0;
         while ((1 << (lg2 + 1)) * ncand <= kSetSlots) ++lg2;
         // a candidate's share of the block set must stay at most half full
-        if (depth > 1 && chunk > (1ll << lg2) / 2) chunk = (1ll << lg2) / 2;
-        const long long items = (s < S) ? (n + chunk - 1) / chunk : 0;
+        const long long half = (1ll << lg2) / 2;
+        if (depth > 1 && chunk > half) chunk = half;
+        long long items = (s < S) ? (n + chunk - 1) / chunk : 0;
+        if (depth == 1 && chunk > half) {
+            // several smaller items per block, evenly spread, where they fit
+            const long long k = (chunk + half - 1) / half;
+            long long c2 = (nl + k * P.nblocks - 1) / (k * P.nblocks);
+            if (c2 < P.chunk_min) c2 = P.chunk_min;
+            const long long items2 = (s < S) ? (n + c2 - 1) / c2 : 0;
+            block_excl_scan<long long>(items2, &tot, st.scan_ll);
+            if (tot <= static_cast<long long>(kLocalItems) * P.nblocks && tot <= kMaxItems) {
+                chunk = c2;
+                items = items2;
+            }
+        }
         o = block_excl_scan<long long>(items, &tot, st.scan_ll);
         // (depth 1 always fits: chunk >= nl / nblocks gives at most nblocks + S
         // items, and the host keeps S <= (kLocalItems - 1) * nblocks)
@@ -325,6 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
     for (int b = 0; b < 2; ++b) {
         d.ord[b] = reinterpret_cast<float4*>(ws + P.lay.ord[b]);
         d.orig[b] = reinterpret_cast<int32_t*>(ws + P.lay.orig[b]);
+    d.posof = reinterpret_cast<int32_t*>(ws + P.lay.posof);
         d.taken[b] = reinterpret_cast<uint32_t*>(ws + P.lay.taken[b]);
         d.dirty[b] = reinterpret_cast<uint32_t*>(ws + P.lay.dirty[b]);
         d.tk[b] = reinterpret_cast<unsigned long long*>(ws + P.lay.tabk[b]);
@@ -372,7 +398,10 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         p[0] = q[0];
                         p[1] = q[1];
                         p[2] = q[2];
-                        if (!bucketing) ord[i] = make_float4(p[0], p[1], p[2], __int_as_float(static_cast<int>(i)));
+                        if (!bucketing) {
+                            ord[i] = make_float4(p[0], p[1], p[2], __int_as_float(static_cast<int>(i)));
+                            d.posof[i] = static_cast<int32_t>(i);
+                        }
                     } else {
                         const float4 q = ord[i];
                         p[0] = q.x;
@@ -503,8 +532,10 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         const float* q = P.points + 3 * i;
                         const float p[3] = {q[0], q[1], q[2]};
                         const unsigned r = atomicAdd(&h[bucket_of(p, st.mn[0], st.mx[0])], 1u);
-                        if (r < static_cast<unsigned>(NL))
+                        if (r < static_cast<unsigned>(NL)) {
                             ord[r] = make_float4(p[0], p[1], p[2], __int_as_float(static_cast<int>(i)));
+                            d.posof[i] = static_cast<int32_t>(r);
+                        }
                     }
                 }
             }
@@ -520,7 +551,6 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             const int q = l & 1;
             LayerState* ls = d.ls + q * S;
             uint32_t* hist = d.hist + static_cast<long long>(q) * S * kHistBins;
-            const bool use_mask = l > 0;
 
             if (tid < S) {
                 const long long ml = layer_budget(st.m[tid], P.layers, P.ratio, l);
@@ -623,16 +653,20 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         st.list_n = 0u;
                         st.rbits = 0u;
                     }
-                    if (tid < ncand) st.ccount[tid] = 0u;
                     __syncthreads();
                     const int cap = st.cap_log2[s];
                     unsigned long long* Tb = d.tk[X] + st.tab_off[s];
                     int bad = 0;
                     unsigned rbits = 0;  // candidates with a key out of range
-                    auto log_fresh = [&](int c, long long slot) {
-                        atomicAdd(&st.ccount[c], 1u);
-                        const int k = atomicAdd(&st.dcnt[X][li][c], 1);
-                        d.dirty[X][c * dstride + a + k] = static_cast<uint32_t>(c * tstride + st.tab_off[s] + slot);
+                    // log a fresh insert (whole warp calls, converged): one shared
+                    // counter add per candidate present in the warp, and the warp's
+                    // log entries of a candidate land side by side.  The set X logs
+                    // are empty when a pass starts, so dcnt[X] ends as the count.
+                    auto log_fresh = [&](bool fresh, int c, long long slot) {
+                        const int k = (ncand == 1) ? warp_append(fresh, &st.dcnt[X][li][0])
+                                                   : warp_append_keyed(fresh, c, st.dcnt[X][li]);
+                        if (fresh)
+                            d.dirty[X][c * dstride + a + k] = static_cast<uint32_t>(c * tstride + st.tab_off[s] + slot);
                     };
                     // work units are (candidate, point) pairs, point-minor, so that a
                     // warp reads consecutive points and the candidates run in parallel
@@ -649,36 +683,43 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             q4[u] = (w < units) ? ord[a + (w - cu[u] * L)]
                                                 : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
                         }
+                        // the keys of all units first (independent arithmetic), then
+                        // their inserts one after the other
+                        unsigned long long key[kInFlight];
 #pragma unroll
                         for (int u = 0; u < kInFlight; ++u) {
-                            const int g = __float_as_int(q4[u].w);
+                            key[u] = kEmptyKey;
                             const int c = cu[u];
-                            bool ok = g >= 0 && !(use_mask && is_taken(taken, g)) && st.cvalid[li][c];
-                            unsigned long long key = kEmptyKey;
-                            if (ok) {
+                            // w < 0: padding, or taken by an earlier layer
+                            if (__float_as_int(q4[u].w) >= 0 && st.cvalid[li][c]) {
                                 const float p3[3] = {q4[u].x, q4[u].y, q4[u].z};
                                 float f[3];
-                                if (!cell_key(p3, st.cgrid[li][c], &key, f)) {
+                                if (!cell_key(p3, st.cgrid[li][c], &key[u], f)) {
                                     rbits |= 1u << c;
-                                    ok = false;
+                                    key[u] = kEmptyKey;
                                 }
                             }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kInFlight; ++u) {
+                            const int c = cu[u];
                             int r = -2;
                             bool nw = false;
-                            if (ok) r = smem_insert_n(set + (c << setc_log2), setc_log2, key, &nw);
+                            if (key[u] != kEmptyKey) r = smem_insert_n(set + (c << setc_log2), setc_log2, key[u], &nw);
                             const int pos = warp_append(r >= 0 && nw, &st.list_n);
                             if (pos >= 0) list[pos] = static_cast<unsigned short>((c << setc_log2) + r);
+                            bool fr = false;
+                            long long slot = -1;
                             if (r == -1) {  // block set saturated: straight to the global table
-                                bool fr;
-                                const long long slot = find_or_insert(Tb + c * tstride, cap, key, &fr);
+                                slot = find_or_insert(Tb + c * tstride, cap, key[u], &fr);
                                 if (slot < 0) bad = HAV_ERR_TABLE_FULL;
-                                else if (fr) log_fresh(c, slot);
                             }
+                            log_fresh(r == -1 && slot >= 0 && fr, c, slot);
                         }
                     }
                     __syncthreads();
                     const int nl = static_cast<int>(st.list_n);
-                    for (int k0 = tid; k0 < nl; k0 += kProbes * kThreads) {
+                    for (int k0 = tid - lane; k0 < nl; k0 += kProbes * kThreads) {  // warp-uniform
                         unsigned long long key[kProbes];
                         unsigned long long* Tp[kProbes];
                         int cc[kProbes];
@@ -686,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         bool fr[kProbes];
 #pragma unroll
                         for (int u = 0; u < kProbes; ++u) {
-                            const int k = k0 + u * kThreads;
+                            const int k = k0 + lane + u * kThreads;
                             const int idx = (k < nl) ? static_cast<int>(list[k]) : 0;
                             cc[u] = idx >> setc_log2;
                             key[u] = (k < nl) ? set[idx] : kEmptyKey;
@@ -695,9 +736,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         find_or_insert_batch<kProbes>(Tp, cap, key, slot, fr);
 #pragma unroll
                         for (int u = 0; u < kProbes; ++u) {
-                            if (key[u] == kEmptyKey) continue;
-                            if (slot[u] < 0) bad = HAV_ERR_TABLE_FULL;
-                            else if (fr[u]) log_fresh(cc[u], slot[u]);
+                            if (key[u] != kEmptyKey && slot[u] < 0) bad = HAV_ERR_TABLE_FULL;
+                            log_fresh(key[u] != kEmptyKey && slot[u] >= 0 && fr[u], cc[u], slot[u]);
                         }
                     }
                     // empty the set again: exactly the listed slots are occupied
@@ -707,7 +747,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     if (rbits) atomicOr(&st.rbits, rbits);
                     if (bad) seg_error(d, s, bad);
                     __syncthreads();
-                    if (tid < ncand && st.ccount[tid]) atomicAdd(&ls[s].count[p % 3][tid], st.ccount[tid]);
+                    if (tid < ncand && st.dcnt[X][li][tid])
+                        atomicAdd(&ls[s].count[p % 3][tid], static_cast<unsigned>(st.dcnt[X][li][tid]));
                     if (tid == 0 && st.rbits) atomicOr(&ls[s].cerr[p % 3], st.rbits);
                 }
                 if (p >= 1 && blockIdx.x == 0)
@@ -825,8 +866,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         }
 #pragma unroll
                         for (int u = 0; u < kInFlight; ++u) {
-                            const int g = __float_as_int(q4[u].w);
-                            bool ok = g >= 0 && !(use_mask && is_taken(taken, g));
+                            const int g = __float_as_int(q4[u].w);  // < 0: padding, or taken by an earlier layer
+                            bool ok = g >= 0;
                             unsigned long long key = kEmptyKey, packed = kEmptyVal;
                             if (ok) {
                                 const float p3[3] = {q4[u].x, q4[u].y, q4[u].z};
@@ -950,13 +991,13 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         if (v == kEmptyVal) continue;
                         const int g = static_cast<int>(v & 0xffffffffull);
                         if (!cut) {
-                            set_taken(taken, g);
+                            mark_taken(taken, ord, d.posof, g);
                             continue;
                         }
                         const unsigned long long h = priority(d.tk[sel][gs]);
                         const int hb = static_cast<int>(h >> (64 - kHistBits));
                         if (hb < bin) {
-                            set_taken(taken, g);
+                            mark_taken(taken, ord, d.posof, g);
                         } else if (hb == bin) {
                             const uint32_t ci = atomicAdd(&ls[s].cand, 1u);
                             if (static_cast<long long>(ci) < (C >> 1)) {
@@ -992,7 +1033,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     int rank = 0;
                     for (int k = 0; k < cs; ++k) rank += (base[k].h < hj) ? 1 : 0;
                     const int r = st.ml[s] - static_cast<int>(ls[s].below);
-                    if (rank < r) set_taken(taken, static_cast<int>(base[jdx].g));
+                    if (rank < r) mark_taken(taken, ord, d.posof, static_cast<int>(base[jdx].g));
                 }
                 int sf = 0;
                 if (tid < S && (st.flags[tid] & F_ACTIVE) && st.kstar[tid] < st.ml[tid]) sf = 1;
@@ -1060,7 +1101,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         const int free_pt = (g < b && !is_taken(taken, g)) ? 1 : 0;
                         int chunk;
                         const int rank = block_excl_scan<int>(free_pt, &chunk, st.scan_i);
-                        if (free_pt && rank < budget) set_taken(taken, g);
+                        if (free_pt && rank < budget) mark_taken(taken, ord, d.posof, g);
                         budget -= chunk;
                     }
                 }
@@ -1122,7 +1163,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     const int s = item_range(st, S, it, &a, &b);
                     unsigned c = 0;
                     for (int i = a + tid; i < b; i += kThreads)
-                        c += eff_taken(s, __float_as_int(ord[i].w)) ? 1u : 0u;
+                        c += eff_taken(s, level_index(ord[i].w)) ? 1u : 0u;
                     const unsigned tot = block_sum(c, st.scan_u);
                     if (tid == 0) d.pitem[it] = static_cast<int32_t>(tot);
                 }
@@ -1198,15 +1239,17 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         int keep = 0;
                         if (i < b) {
                             q4 = ord[i];
-                            keep = eff_taken(s, __float_as_int(q4.w)) ? 1 : 0;
+                            keep = eff_taken(s, level_index(q4.w)) ? 1 : 0;
                         }
                         int tot;
                         const int rank = block_excl_scan<int>(keep, &tot, st.scan_i);
                         if (keep) {
                             const long long pos2 = base + rank;
-                            const long long ng = pos_asc(__float_as_int(q4.w));
-                            if (pos2 < st.m_total && ng < st.m_total)
+                            const long long ng = pos_asc(level_index(q4.w));
+                            if (pos2 < st.m_total && ng < st.m_total) {
                                 ord_out[pos2] = make_float4(q4.x, q4.y, q4.z, __int_as_float(static_cast<int>(ng)));
+                                d.posof[ng] = static_cast<int32_t>(pos2);
+                            }
                         }
                         base += tot;
                     }

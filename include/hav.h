@@ -130,7 +130,7 @@ typedef struct {
 } hav_tuning;
 
 /* Copy the context's tuning into *out (the defaults after creation:
- * {32768, 131072, 262144}, 64, the co-resident maximum). */
+ * {0, 16384, 262144}, 64, the co-resident maximum). */
 hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out);
 
 /* Replace the context's tuning.  HAV_ERR_INVALID (and no change) on a value

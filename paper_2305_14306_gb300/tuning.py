@@ -3,9 +3,9 @@
 A context has three knobs (``hav_tuning`` in include/hav.h):
 
 * the level sizes up to which one bisection pass evaluates 4, 3 or 2 steps of
-  the search at once (Section 3.3 run speculatively: a pass costs about the
-  same on a small level whether it evaluates one size or fifteen, so deeper
-  passes mean fewer grid-wide passes);
+  the search at once (Section 3.3 run speculatively: on a small level a pass
+  is mostly fixed latency, so evaluating several sizes per pass means fewer
+  grid-wide passes, until the work per candidate catches up);
 * the smallest work item, in points;
 * the number of blocks (one per SM).
 
@@ -25,8 +25,12 @@ import os
 import tempfile
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hav_tuning.json")
-BASE_SPEC = (32768, 131072, 262144)
-SPEC_SCALES = (0.0, 0.5, 1.0, 2.0, 4.0, 8.0)
+BASE_SPEC = (0, 16384, 262144)
+# speculation thresholds tried (depth 4 up to [0], 3 up to [1], 2 up to [2] points)
+SPEC_CHOICES = (
+    (0, 0, 0), (0, 0, 65536), (0, 0, 262144), (0, 8192, 131072), (0, 16384, 262144),
+    (0, 32768, 262144), (0, 65536, 524288), (8192, 16384, 262144), (32768, 131072, 262144),
+)
 CHUNK_MINS = (32, 64, 128, 256, 512, 1024)
 
 
@@ -39,6 +43,7 @@ def signature(seg_sizes, levels: int) -> str:
 
 
 def spec_for(scale: float, base=BASE_SPEC):
+    """The thresholds scaled (clamped to 2^31)."""
     return [min(1 << 31, int(round(b * scale))) for b in base]
 
 
@@ -102,8 +107,8 @@ def autotune(ctx, run, key: str, gpu: str, cache: str | None = DEFAULT_CACHE, fo
 
     default_ms = measure(start["spec_points"], start["chunk_min"])
     best = (default_ms, list(start["spec_points"]), int(start["chunk_min"]))
-    for sc in SPEC_SCALES:  # stage 1: speculation thresholds at the current work-item size
-        spec = spec_for(sc)
+    for choice in SPEC_CHOICES:  # stage 1: speculation thresholds at the current work-item size
+        spec = list(choice)
         if spec == best[1]:
             continue
         ms = measure(spec, best[2])

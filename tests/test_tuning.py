@@ -20,17 +20,20 @@ class FakeCtx:
             self.t["chunk_min"] = int(chunk_min)
 
 
+BEST_SPEC = [0, 8192, 131072]
+
+
 def cost_of(ctx):
-    # a made-up landscape with its minimum at spec scale 2 and chunk 256
-    sp = ctx.t["spec_points"][0]
-    return abs(sp - 2 * tuning.BASE_SPEC[0]) / 1e4 + abs(ctx.t["chunk_min"] - 256) / 100 + 1.0
+    # a made-up landscape with its minimum at one listed threshold choice and chunk 256
+    sp = ctx.t["spec_points"]
+    return sum(abs(a - b) for a, b in zip(sp, BEST_SPEC)) / 1e4 + abs(ctx.t["chunk_min"] - 256) / 100 + 1.0
 
 
 def test_search_finds_the_minimum_and_caches(tmp_path):
     path = str(tmp_path / "c.json")
     ctx = FakeCtx()
     t, rep = tuning.autotune(ctx, None, "S64-N8388608-L2", "GB300", cache=path, timer=lambda: cost_of(ctx))
-    assert t == {"spec_points": tuning.spec_for(2.0), "chunk_min": 256}
+    assert t == {"spec_points": BEST_SPEC, "chunk_min": 256}
     assert ctx.t["spec_points"] == t["spec_points"] and ctx.t["chunk_min"] == 256
     assert rep["tuned_ms"] <= rep["default_ms"] and not rep["cached"]
     data = json.load(open(path))
@@ -50,7 +53,7 @@ def test_default_kept_when_nothing_is_faster():
     ctx = FakeCtx()
     t, rep = tuning.autotune(ctx, None, "k", "g", cache=None, timer=lambda: 1.0)
     assert t == {"spec_points": list(tuning.BASE_SPEC), "chunk_min": 64}
-    assert rep["tried"] == 1 + (len(tuning.SPEC_SCALES) - 1) + (len(tuning.CHUNK_MINS) - 1)
+    assert rep["tried"] == 1 + (len(tuning.SPEC_CHOICES) - 1) + (len(tuning.CHUNK_MINS) - 1)
 
 
 def test_signature_and_corrupt_cache(tmp_path):
@@ -62,3 +65,6 @@ def test_signature_and_corrupt_cache(tmp_path):
     assert tuning.load_cache(str(bad)) == {}
     assert tuning.spec_for(0.0) == [0, 0, 0]
     assert tuning.spec_for(1e9)[2] == 1 << 31
+    assert list(tuning.BASE_SPEC) in [list(c) for c in tuning.SPEC_CHOICES]
+    for c in tuning.SPEC_CHOICES:
+        assert c[0] <= c[1] <= c[2]

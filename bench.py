@@ -45,6 +45,9 @@ WORKLOADS = {
     "serving": {"desc": "Poisson arrivals of scenes with N log-uniform in [10k, 1M] (LiDAR up to 200k, room above), "
                         "M in {N/4, N/16, 4096}; continuous batching on co-resident slots vs the plain per-cloud path",
                 "n": None, "levels": None},
+    "compare": {"desc": "HAV vs the plain GPU FPS comparator (Eq. 1): C1 16,384 -> 4,096; C2 LiDAR returns -> 16,384; "
+                        "C4 64 LiDAR clouds -> N/4 each; C3 1,048,576 -> 262,144 (level 1); time and coverage",
+                "n": None, "levels": None},
     "batch64": {"desc": "64 LiDAR clouds, N log-uniform in [20k, 200k], per cloud M = N/4 then N/16, "
                         "one persistent segmented launch (also replayed from a CUDA graph) vs 64 per-cloud calls",
                 "n": None, "levels": None},
@@ -354,17 +357,123 @@ def run_batched(args, world, rank, local):
     return 0
 
 
+# ----------------------------------------------------------------- comparator arm
+def coverage_fast(pts, idx, queries=None, chunk=2048):
+    """max over query points of the distance to the nearest selected point, fp32 on
+    centred coordinates with matmul distances (about 1e-4 m error at these extents)."""
+    import torch
+    c = pts - pts.mean(dim=0, keepdim=True)
+    sel = c[idx.long()]
+    q = c if queries is None else c[queries]
+    worst = 0.0
+    for a in range(0, q.shape[0], chunk):
+        d = torch.cdist(q[a:a + chunk], sel, compute_mode="use_mm_for_euclid_dist")
+        worst = max(worst, float(d.min(dim=1).values.max()))
+    return worst
+
+
+def run_compare(args, world, rank, local):
+    import torch
+    from paper_2305_14306_gb300 import hav
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    rng = np.random.default_rng(11)
+    p = hav.params()
+    cases = []
+
+    def single(name, pts_np, m, exact_cov, sample_q=None):
+        n = pts_np.shape[0]
+        ctx = hav.Context(n, 1)
+        d = torch.from_numpy(pts_np).cuda()
+        out = torch.empty(m, dtype=torch.int32, device="cuda")
+        fout = torch.empty(m, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            hav.hav_sample_levels(ctx, d, [m], p, outs=[out])
+        hav.hav_fps(ctx, d, min(m, 64), out=fout[:min(m, 64)])
+        ms_h = min(timed(lambda: hav.hav_sample_levels(ctx, d, [m], p, outs=[out]))[1] for _ in range(5))
+        _, ms_f = timed(lambda: hav.hav_fps(ctx, d, m, out=fout))
+        st, _ = hav.hav_status_get(ctx, 1)
+        rnd = torch.from_numpy(rng.choice(n, size=m, replace=False).astype(np.int32)).cuda()
+        q = None if sample_q is None else torch.from_numpy(rng.choice(n, size=sample_q, replace=False)).cuda()
+        if exact_cov:
+            cov = [hav.coverage(d, x) for x in (out, fout, rnd)]
+        else:
+            cov = [coverage_fast(d, x, q) for x in (out, fout, rnd)]
+        ctx.close()
+        cases.append({"case": name, "n": n, "m": m, "hav_ms": ms_h, "fps_ms": ms_f, "fps_over_hav": ms_f / ms_h,
+                      "coverage_m": {"hav": cov[0], "fps": cov[1], "random": cov[2]},
+                      "coverage": "exact (fp64)" if exact_cov else
+                      ("fp32, all points" if q is None else f"fp32, {sample_q} sampled query points"),
+                      "status": st})
+
+    single("C1 uniform", scenes.uniform_box(16384, seed=0), 4096, True)
+    single("C2 LiDAR first level", scenes.lidar_min(16384, seed=0)[0], 16384, True)
+    single("C3 indoor level 1", scenes.room_scene(1 << 20, seed=0), 1 << 18, False, sample_q=65536)
+
+    # C4: 64 clouds, M = N/4: one batched HAV launch vs 64 FPS calls
+    clouds = scenes.lidar_batch(64, seed=0)
+    pts, offs = scenes.concat(clouds)
+    sizes = np.diff(offs)
+    ms4 = (sizes // 4).astype(np.int64)
+    ctx = hav.Context(int(offs[-1]), 64)
+    d = torch.from_numpy(pts).cuda()
+    out = torch.empty(int(ms4.sum()), dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        hav.hav_sample_batched(ctx, d, offs, ms4[None, :], p, outs=[out])
+    ms_h = min(timed(lambda: hav.hav_sample_batched(ctx, d, offs, ms4[None, :], p, outs=[out]))[1] for _ in range(5))
+    fouts = [torch.empty(int(ms4[s]), dtype=torch.int32, device="cuda") for s in range(64)]
+    views = [d[int(offs[s]):int(offs[s + 1])] for s in range(64)]
+
+    def fps_all():
+        for s in range(64):
+            hav.hav_fps(ctx, views[s], int(ms4[s]), out=fouts[s])
+    _, ms_f = timed(fps_all)
+    cut = np.concatenate([[0], np.cumsum(ms4)])
+    covs = {"hav": [], "fps": [], "random": []}
+    for s in range(64):
+        n = int(sizes[s])
+        rnd = torch.from_numpy(rng.choice(n, size=int(ms4[s]), replace=False).astype(np.int32)).cuda()
+        covs["hav"].append(coverage_fast(views[s], out[int(cut[s]):int(cut[s + 1])]))
+        covs["fps"].append(coverage_fast(views[s], fouts[s]))
+        covs["random"].append(coverage_fast(views[s], rnd))
+    ctx.close()
+    cases.append({"case": "C4 64 LiDAR clouds, N/4 each", "n": int(offs[-1]), "m": int(ms4.sum()), "hav_ms": ms_h,
+                  "fps_ms": ms_f, "fps_over_hav": ms_f / ms_h,
+                  "coverage_m": {k: float(np.mean(v)) for k, v in covs.items()},
+                  "coverage": "fp32, all points; mean over the 64 clouds",
+                  "hav_launches": 1, "fps_launches": 64})
+    if rank == 0:
+        tot_n = sum(c["n"] for c in cases)
+        tot_ms = sum(c["hav_ms"] for c in cases)
+        line = {"metric": "input Mpoints/s", "value": tot_n / tot_ms / 1e3, "unit": "Mpoints/s", "n_gpus": world,
+                "steps": 5, "warmup": 3, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "compare", "desc": WORKLOADS["compare"]["desc"],
+                           "l2": "not flushed (each case timed as the best of 5 calls)"},
+                "cases": cases}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------- serving arm
 def run_serving(args, world, rank, local):
-    """C5: closed-loop capacity and open-loop latency (Poisson arrivals at 0.8x the
-    plain path's capacity) of the served path vs the plain per-cloud path."""
+    """C5: closed-loop capacity and open-loop latency (Poisson arrivals at 0.5, 0.8
+    and 0.95 x the plain path's capacity) of the served path vs the plain per-cloud path."""
     import torch
     from paper_2305_14306_gb300 import serving
 
     rng = np.random.default_rng(1000 + rank)
     pool_n = scenes.log_uniform_sizes(16, 10_000, 1_000_000, seed=1000 + rank)
     pool = [torch.from_numpy(scenes.scene_for(int(n), seed=5000 + i)).pin_memory() for i, n in enumerate(pool_n)]
-    R = max(20, min(args.steps, 400))
+    R = max(20, min(args.steps, 2000))
     picks = rng.integers(0, len(pool), size=R)
     choice = rng.integers(0, 3, size=R)
 
@@ -391,14 +500,24 @@ def run_serving(args, world, rank, local):
         res_s = served.serve(make(zero))
         cap_served = R / (time.perf_counter() - t0)
         same = all(np.array_equal(res_p[i].indices, res_s[i].indices) for i in range(R))
-        lam = 0.8 * cap_plain
-        arr = np.cumsum(np.random.default_rng(7 + rank).exponential(1.0 / lam, size=R))
-        arr -= arr[0]
         clk = Clocks(local)
-        lat_p = [r.latency for r in plain.serve(make(arr)).values()]
-        lat_s_res = served.serve(make(arr))
+        open_loop = []
+        for load in (0.5, 0.8, 0.95):  # Poisson arrivals at these fractions of the plain capacity
+            lam = load * cap_plain
+            arr = np.cumsum(np.random.default_rng(7 + rank).exponential(1.0 / lam, size=R))
+            arr -= arr[0]
+            lat_p = [r.latency for r in plain.serve(make(arr)).values()]
+            res_s2 = served.serve(make(arr))
+            lat_s = [r.latency for r in res_s2.values()]
+            same = same and all(np.array_equal(res_p[i].indices, res_s2[i].indices) for i in range(R))
+            open_loop.append({
+                "load": load, "arrival_rate_hz": lam,
+                "served": {"p50_ms": 1e3 * serving.percentile(lat_s, 0.5),
+                           "p99_ms": 1e3 * serving.percentile(lat_s, 0.99)},
+                "plain": {"p50_ms": 1e3 * serving.percentile(lat_p, 0.5),
+                          "p99_ms": 1e3 * serving.percentile(lat_p, 0.99)},
+                "mean_batch": float(np.mean([r.batch for r in res_s2.values()]))})
         clocks = clk.stop()
-        lat_s = [r.latency for r in lat_s_res.values()]
     finally:
         served.close()
         plain.close()
@@ -413,12 +532,7 @@ def run_serving(args, world, rank, local):
             "scenes_per_s": cap_served,
             "plain": {"scenes_per_s": cap_plain, "value": pts_total / R * cap_plain / 1e6},
             "speedup_vs_per_cloud": cap_served / cap_plain,
-            "open_loop": {"arrival_rate_hz": lam,
-                          "served": {"p50_ms": 1e3 * serving.percentile(lat_s, 0.5),
-                                     "p99_ms": 1e3 * serving.percentile(lat_s, 0.99)},
-                          "plain": {"p50_ms": 1e3 * serving.percentile(lat_p, 0.5),
-                                    "p99_ms": 1e3 * serving.percentile(lat_p, 0.99)},
-                          "mean_batch": float(np.mean([r.batch for r in lat_s_res.values()]))},
+            "open_loop": open_loop,
             "identical_outputs": bool(same),
             "clocks": clocks,
         }
@@ -460,8 +574,9 @@ def main():
     if world > 1:
         dist.barrier()
     hav.load()
-    if args.workload in ("batch64", "serving"):
-        rc = (run_batched if args.workload == "batch64" else run_serving)(args, world, rank, local)
+    if args.workload in ("batch64", "serving", "compare"):
+        rc = {"batch64": run_batched, "serving": run_serving, "compare": run_compare}[args.workload](
+            args, world, rank, local)
         if world > 1:
             dist.destroy_process_group()
         return rc

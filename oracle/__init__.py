@@ -38,7 +38,13 @@ class Params(C.Structure):
         ("layer_ratio", C.c_int32),
         ("aspect", C.c_float * 3),
         ("flags", C.c_uint32),
+        ("select", C.c_int32),
+        ("seed", C.c_uint32),
+        ("fixed_s", C.c_float),
     ]
+
+
+SELECT = {"cc": 0, "random": 1, "mean": 2, "centre": 3}
 
 
 class LayerTrace(C.Structure):
@@ -56,14 +62,19 @@ class LayerTrace(C.Structure):
     ]
 
 
-def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 1.0)):
-    """Paper defaults (Section 4.1): sigma = 0.05, t_max = 20, k = 2."""
+def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 1.0),
+           select="cc", seed=0, fixed_s=0.0):
+    """Paper defaults (Section 4.1): sigma = 0.05, t_max = 20, k = 2, centre-closest
+    selection, adaptive voxel.  select / fixed_s: the Table 6 variants."""
     p = Params()
     p.sigma_num, p.sigma_den = sigma
     p.t_max, p.layers, p.layer_ratio = t_max, layers, layer_ratio
     for a in range(3):
         p.aspect[a] = aspect[a]
     p.flags = 0
+    p.select = SELECT[select] if isinstance(select, str) else int(select)
+    p.seed = int(seed)
+    p.fixed_s = float(fixed_s)
     return p
 
 
@@ -105,6 +116,11 @@ def lib():
             L.hor_s_hi.restype = C.c_float
             L.hor_fps.argtypes = [fp, i64, i64, C.POINTER(C.c_int32)]
             L.hor_fps.restype = C.c_int
+            L.hor_random.argtypes = [C.c_uint32, C.c_uint64]
+            L.hor_random.restype = C.c_uint64
+            L.hor_sample_xyz.argtypes = [fp, i64, i64, C.POINTER(Params), C.POINTER(C.c_int32), fp,
+                                         C.POINTER(LayerTrace)]
+            L.hor_sample_xyz.restype = C.c_int
             _lib = L
     return _lib
 
@@ -207,6 +223,28 @@ def select(points, s, aspect=(1.0, 1.0, 1.0)):
 
 def priority(key: int) -> int:
     return int(lib().hor_priority(C.c_uint64(int(key))))
+
+
+def random_draw(seed: int, counter: int) -> int:
+    """Draw `counter` of the counter-based SplitMix64 generator started at `seed`."""
+    return int(lib().hor_random(C.c_uint32(int(seed)), C.c_uint64(int(counter))))
+
+
+def sample_xyz(points, m, p: Params | None = None, want_trace: bool = False):
+    """One-layer call returning (ascending indices, representative coordinates (m, 3))."""
+    p = p or params(layers=1)
+    a = _pts(points)
+    out = np.zeros(max(int(m), 1), dtype=np.int32)
+    xyz = np.zeros((max(int(m), 1), 3), dtype=np.float32)
+    tr = LayerTrace()
+    st = lib().hor_sample_xyz(_fp(a), a.shape[0], int(m), C.byref(p), out.ctypes.data_as(C.POINTER(C.c_int32)),
+                              _fp(xyz), C.byref(tr))
+    if st != OK:
+        raise OracleError(st)
+    res = (out[: int(m)], xyz[: int(m)])
+    if want_trace:
+        return res + ([trace_dict(tr)],)
+    return res
 
 
 def s_hi(points, aspect=(1.0, 1.0, 1.0)) -> np.float32:

@@ -27,6 +27,10 @@
 //   * Eq. 3 layer budgets with ratio 4: m_l = floor(m * 4^(l-1) / S) for the
 //     first k-1 layers, the last layer takes the remainder, S = sum 4^(l-1).
 //   * Output is every taken index in ascending order.
+//   * Table 6 variants (Section 4.5): RA keeps, per voxel, the point with the
+//     smallest counter-based SplitMix64 draw (seed, index); ME and CE keep the
+//     centre-closest index and report the voxel's mean (fixed-point sums, see
+//     voxel_mean) or centre v * (g + 0.5); a fixed voxel size skips the search.
 //
 // Parity: the voxel grouping, the centre-closest argmin, Cnt, the bisection
 // trace and the layer recursion are pinned by tests that do not call this
@@ -42,6 +46,13 @@
 #include <vector>
 
 namespace {
+
+enum {
+    OR_SEL_CC = 0,
+    OR_SEL_RA = 1,
+    OR_SEL_ME = 2,
+    OR_SEL_CE = 3,
+};
 
 enum {
     OR_OK = 0,
@@ -67,6 +78,9 @@ typedef struct {
     int32_t layer_ratio;  // m_l = ratio * m_(l-1) (4)
     float aspect[3];      // r, v = s * r (1, 1, 1)
     uint32_t flags;       // unused, must be 0
+    int32_t select;       // 0 centre-closest, 1 random, 2 mean, 3 centre (Table 6)
+    uint32_t seed;        // draws of the random selection
+    float fixed_s;        // > 0: fixed voxel size s (no search); 0: adaptive
 } hor_params;
 
 // Per-layer record of one call: what the bisection evaluated and decided.
@@ -163,6 +177,14 @@ uint64_t splitmix_finalise(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+// Counter-based draw number `counter` of the SplitMix64 generator started at
+// `seed` (Steele, Lea, Flood 2014): the state after counter + 1 increments of
+// the golden-ratio step, finalised.
+uint64_t random_draw(uint32_t seed, uint64_t counter) {
+    const uint64_t z = static_cast<uint64_t>(seed) + (counter + 1) * 0x9E3779B97F4A7C15ull;
+    return splitmix_finalise(z);
+}
+
 // Cnt(P_l, s) of Section 3.3: number of distinct voxel keys among the points
 // listed in `active`.
 int count_voxels(const float* pts, const std::vector<int32_t>& active,
@@ -215,6 +237,11 @@ int check_params(const hor_params* p) {
     for (int a = 0; a < 3; ++a)
         if (!(p->aspect[a] > 0.0f) || !std::isfinite(p->aspect[a])) return OR_ERR_INVALID;
     if (p->flags != 0) return OR_ERR_INVALID;
+    if (p->select < OR_SEL_CC || p->select > OR_SEL_CE) return OR_ERR_INVALID;
+    if (!(p->fixed_s >= 0.0f) || !std::isfinite(p->fixed_s)) return OR_ERR_INVALID;
+    // the ablation variants run one layer, as in Table 6
+    if ((p->fixed_s > 0.0f || p->select == OR_SEL_ME || p->select == OR_SEL_CE) && p->layers != 1)
+        return OR_ERR_INVALID;
     return OR_OK;
 }
 
@@ -260,10 +287,11 @@ int sample_one(const float* pts, int64_t n, int64_t m, const hor_params* p,
             if (!taken[i]) active.push_back(static_cast<int32_t>(i));
         rec.n_in = static_cast<int64_t>(active.size());
 
-        // Section 3.3 adaptive voxel search.
+        // Section 3.3 adaptive voxel search (skipped for a fixed voxel size).
         float lo = 0.0f, hi = c.s_hi, s_star = 0.0f;
         bool accepted = false;
-        for (int t = 0; t < p->t_max; ++t) {
+        const bool fixed = p->fixed_s > 0.0f;
+        for (int t = 0; t < (fixed ? 0 : p->t_max); ++t) {
             float s = (lo + hi) * 0.5f;
             int64_t K;
             st = count_voxels(pts, active, c, s, &K);
@@ -282,6 +310,7 @@ int sample_one(const float* pts, int64_t n, int64_t m, const hor_params* p,
             }
         }
         if (!accepted) s_star = (lo > 0.0f) ? lo : hi;
+        if (fixed) s_star = p->fixed_s;
         rec.accepted = accepted ? 1 : 0;
         rec.s_star = s_star;
 
@@ -296,9 +325,14 @@ int sample_one(const float* pts, int64_t n, int64_t m, const hor_params* p,
             float f[3];
             const float* pi = pts + 3 * int64_t(i);
             if (!voxel_key(pi, v, fmin, &key, f)) return OR_ERR_RANGE;
-            float d2 = centre_dist2(pi, v, f);
-            uint64_t packed = (static_cast<uint64_t>(float_bits(d2)) << 32) |
-                              static_cast<uint32_t>(i);
+            // the voxel's representative minimises this word: the squared
+            // distance to the centre (CC, and ME / CE, which report other
+            // coordinates for the same voxel) or a random draw (RA); ties
+            // go to the lowest index
+            uint32_t hi32;
+            if (p->select == OR_SEL_RA) hi32 = static_cast<uint32_t>(random_draw(p->seed, uint64_t(i)) >> 32);
+            else hi32 = float_bits(centre_dist2(pi, v, f));
+            uint64_t packed = (static_cast<uint64_t>(hi32) << 32) | static_cast<uint32_t>(i);
             auto it = table.find(key);
             if (it == table.end()) table.emplace(key, packed);
             else if (packed < it->second) it->second = packed;
@@ -459,6 +493,92 @@ int hor_select(const float* pts, int64_t n, float s, const float aspect[3],
 }
 
 uint64_t hor_priority(uint64_t key) { return splitmix_finalise(key); }
+
+uint64_t hor_random(uint32_t seed, uint64_t counter) { return random_draw(seed, counter); }
+
+// Representative coordinates of a one-layer call (Table 6 point-selection
+// strategies).  out_idx receives the m ascending indices hor_sample gives;
+// out_xyz (3m floats) the coordinates that stand for each: for an index that
+// represents its voxel at s* (the voxel's centre-closest point, or its random
+// draw for RA), the point itself (CC, RA), the voxel centre v * (g + 0.5) in
+// binary32 (CE), or the voxel mean (ME); for an index added by the shortfall
+// fill, the point itself.
+//
+// The mean is computed in fixed point so that it does not depend on the
+// order of summation: with M the largest |coordinate| of the cloud and
+// 2^(k-1) <= M < 2^k (k = 0 when M = 0), every coordinate x is taken as the
+// integer X = round-half-even(x * 2^(30 - k)); a voxel's mean on one axis is
+// RN32(RN64(RN64(sum X) / count) * 2^(k - 30)).
+int hor_sample_xyz(const float* pts, int64_t n, int64_t m, const hor_params* p,
+                   int32_t* out_idx, float* out_xyz, hor_layer_trace* tr) {
+    int st = check_params(p);
+    if (st != OR_OK) return st;
+    if (p->layers != 1) return OR_ERR_INVALID;
+    hor_layer_trace rec;
+    std::memset(&rec, 0, sizeof rec);
+    st = hor_sample(pts, n, m, p, out_idx, &rec);
+    if (st != OR_OK || m == 0) {
+        if (tr) *tr = rec;
+        return st;
+    }
+    if (tr) *tr = rec;
+    for (int64_t r = 0; r < m; ++r)
+        for (int a = 0; a < 3; ++a) out_xyz[3 * r + a] = pts[3 * int64_t(out_idx[r]) + a];
+    if (p->select == OR_SEL_CC || p->select == OR_SEL_RA) return OR_OK;
+
+    Ctx c;
+    st = bounding_box(pts, n, p->aspect, &c);
+    if (st != OR_OK) return st;
+    float v[3];
+    int64_t fmin[3];
+    if (!voxel_size(c, rec.s_star, v) || !min_cells(c, v, fmin)) return OR_ERR_RANGE;
+    // the centre-closest point of every voxel, and the fixed-point sums
+    float M = 0.0f;
+    for (int64_t i = 0; i < 3 * n; ++i) M = std::max(M, std::fabs(pts[i]));
+    int k = 0;
+    if (M > 0.0f) std::frexp(M, &k);  // M = f * 2^k, f in [0.5, 1)
+    const int q = 30 - k;
+    struct Acc { uint64_t best; int64_t sum[3]; int64_t count; float f[3]; };
+    std::unordered_map<uint64_t, Acc> vox;
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t key;
+        float f[3];
+        if (!voxel_key(pts + 3 * i, v, fmin, &key, f)) return OR_ERR_RANGE;
+        uint64_t packed = (static_cast<uint64_t>(float_bits(centre_dist2(pts + 3 * i, v, f))) << 32) |
+                          static_cast<uint32_t>(i);
+        auto it = vox.find(key);
+        if (it == vox.end()) {
+            Acc acc;
+            acc.best = packed;
+            acc.count = 0;
+            for (int a = 0; a < 3; ++a) { acc.sum[a] = 0; acc.f[a] = f[a]; }
+            it = vox.emplace(key, acc).first;
+        }
+        Acc& acc = it->second;
+        if (packed < acc.best) acc.best = packed;
+        for (int a = 0; a < 3; ++a)
+            acc.sum[a] += std::llrint(std::ldexp(static_cast<double>(pts[3 * i + a]), q));
+        acc.count += 1;
+    }
+    for (int64_t r = 0; r < m; ++r) {
+        const int32_t i = out_idx[r];
+        uint64_t key;
+        float f[3];
+        voxel_key(pts + 3 * int64_t(i), v, fmin, &key, f);
+        const Acc& acc = vox.at(key);
+        if (static_cast<int32_t>(acc.best & 0xffffffffu) != i) continue;  // shortfall fill
+        for (int a = 0; a < 3; ++a) {
+            if (p->select == OR_SEL_CE) {
+                const float cen = acc.f[a] + 0.5f;
+                out_xyz[3 * r + a] = v[a] * cen;
+            } else {
+                const double mean = static_cast<double>(acc.sum[a]) / static_cast<double>(acc.count);
+                out_xyz[3 * r + a] = static_cast<float>(std::ldexp(mean, -q));
+            }
+        }
+    }
+    return OR_OK;
+}
 
 float hor_s_hi(const float* pts, int64_t n, const float aspect[3]) {
     Ctx c;

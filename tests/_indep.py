@@ -93,6 +93,26 @@ def lexsort_select(p, s, aspect=(1.0, 1.0, 1.0), active=None):
     return np.sort(idx[order[first]]).astype(np.int32)
 
 
+def select_by_word(p, s, word, aspect=(1.0, 1.0, 1.0), active=None):
+    """Per occupied cell, the point with the smallest (word, index): sort by
+    (cell, word, index) and keep the first of each cell; ascending."""
+    idx = np.arange(p.shape[0]) if active is None else np.asarray(active)
+    u, _, _ = rel_cells(p, s, aspect)
+    u, w = u[idx], np.asarray(word, dtype=np.uint64)[idx]
+    order = np.lexsort((idx, w, u[:, 2], u[:, 1], u[:, 0]))
+    us = u[order]
+    first = np.ones(len(order), dtype=bool)
+    first[1:] = (us[1:] != us[:-1]).any(axis=1)
+    return np.sort(idx[order[first]]).astype(np.int32)
+
+
+def splitmix64_draw(seed: int, counter: int) -> int:
+    """SplitMix64 as published: the state starts at `seed` and advances by the
+    golden-ratio step before each output; draw `counter` (0-based)."""
+    M = (1 << 64) - 1
+    return splitmix64_finalise((seed + (counter + 1) * 0x9E3779B97F4A7C15) & M)
+
+
 def splitmix64_finalise(z: int) -> int:
     M = (1 << 64) - 1
     z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
@@ -126,18 +146,30 @@ def bisection(p, m_l, s_hi, sigma=(5, 100), t_max=20, aspect=(1.0, 1.0, 1.0), ac
     return trace, (lo if lo > 0 else hi), False
 
 
-def hav_reference_small(p, m, layers=2, ratio=4, sigma=(5, 100), t_max=20, aspect=(1.0, 1.0, 1.0)):
+def hav_reference_small(p, m, layers=2, ratio=4, sigma=(5, 100), t_max=20, aspect=(1.0, 1.0, 1.0),
+                        select="cc", seed=0, fixed_s=0.0):
     """Whole sampler on a tiny cloud with numpy pieces (bisection + lexsort select +
-    priority truncation + shortfall), for cross-checking the oracle end to end."""
+    priority truncation + shortfall), for cross-checking the oracle end to end.
+    select "random": per cell the smallest SplitMix64 draw (high 32 bits) wins;
+    fixed_s > 0: no search, s* = fixed_s."""
     n = p.shape[0]
     taken = np.zeros(n, dtype=bool)
     _, s_hi = bbox_s_hi(p, aspect)
+    word = None
+    if select == "random":
+        word = np.array([splitmix64_draw(seed, i) >> 32 for i in range(n)], dtype=np.uint64)
     for m_l in budgets(m, layers, ratio):
         if m_l == 0:
             continue
         active = np.nonzero(~taken)[0]
-        _, s_star, _ = bisection(p, m_l, s_hi, sigma, t_max, aspect, active)
-        reps = lexsort_select(p, s_star, aspect, active)
+        if fixed_s > 0:
+            s_star = F32(fixed_s)
+        else:
+            _, s_star, _ = bisection(p, m_l, s_hi, sigma, t_max, aspect, active)
+        if word is None:
+            reps = lexsort_select(p, s_star, aspect, active)
+        else:
+            reps = select_by_word(p, s_star, word, aspect, active)
         K = len(reps)
         if K > m_l:
             u, _, _ = rel_cells(p, s_star, aspect)

@@ -72,7 +72,27 @@ typedef struct {
     int32_t layer_ratio;  /* budget ratio between consecutive layers, 1..64 */
     float aspect[3];      /* r: the voxel is v = s * r; each component finite, > 0 */
     uint32_t flags;       /* 0, or HAV_FLAG_PHASE_TIMES (context calls only) */
+    int32_t select;       /* representative of a voxel (Table 6 of Section 4.5):
+                             HAV_SELECT_CENTRE_CLOSEST (the method, default),
+                             HAV_SELECT_RANDOM, HAV_SELECT_MEAN, HAV_SELECT_CENTRE */
+    uint32_t seed;        /* draws of HAV_SELECT_RANDOM */
+    float fixed_s;        /* 0: adaptive voxel (Section 3.3); > 0: fixed voxel
+                             v = fixed_s * aspect, no search (Table 6 "Fix") */
 } hav_params;
+
+/* Voxel representatives (hav_params.select).  CENTRE_CLOSEST keeps the point
+ * nearest the voxel centre (Section 3.2).  RANDOM keeps, per voxel, the point
+ * with the smallest draw of the counter-based SplitMix64 generator (Steele,
+ * Lea, Flood 2014) started at `seed`, counter = the point's index in the
+ * call's input (per segment); the high 32 bits of the draw decide, ties go to
+ * the lowest index.  MEAN and CENTRE are not points of the cloud: they keep the
+ * centre-closest indices, and hav_sample_xyz reports the voxel mean or the
+ * voxel centre as their coordinates.  MEAN, CENTRE and fixed_s > 0 need
+ * layers == 1, as in Table 6. */
+#define HAV_SELECT_CENTRE_CLOSEST 0
+#define HAV_SELECT_RANDOM 1
+#define HAV_SELECT_MEAN 2
+#define HAV_SELECT_CENTRE 3
 
 /* Record a device timestamp after every grid-wide phase of the call (for
  * profiling; read back with hav_phase_times_get). */
@@ -97,7 +117,8 @@ typedef struct {
 typedef struct hav_ctx hav_ctx;
 typedef struct CUstream_st* hav_stream;  /* same type as cudaStream_t */
 
-/* Fill *p with the paper's defaults.  p must not be NULL. */
+/* Fill *p with the paper's defaults (centre-closest, adaptive voxel).  p must
+ * not be NULL. */
 void hav_params_default(hav_params* p);
 
 /* Create a context on the CURRENT device with workspace for calls of up to
@@ -148,6 +169,21 @@ size_t hav_workspace_bytes(int64_t max_points, int32_t max_segments);
  * 0 <= m <= n < 2^31; m == 0 enqueues nothing.  Section 3, Eq. 3. */
 hav_status hav_sample(hav_ctx* ctx, const float* points, int64_t n, int64_t m,
                       const hav_params* params, int32_t* out_idx, hav_stream stream);
+
+/* hav_sample, plus the coordinates that stand for each selected index
+ * (Table 6 point-selection strategies): out_xyz (device, 3m floats) receives,
+ * for an index that represents its voxel at the chosen size, the point itself
+ * (CENTRE_CLOSEST, RANDOM), the voxel centre v * (g + 0.5) in binary32
+ * (CENTRE) or the voxel mean (MEAN); for an index added by the shortfall fill,
+ * the point itself.  The mean is order-independent: with 2^(k-1) <= M < 2^k
+ * for M the largest |coordinate| of the cloud (k = 0 when M = 0), each
+ * coordinate x is taken as X = round-half-even(x * 2^(30-k)) and a voxel's
+ * mean is RN32(RN64(RN64(sum X) / count) * 2^(k-30)).  Needs layers == 1.
+ * Runs after the sampler on the same stream; the context's workspace is the
+ * scratch. */
+hav_status hav_sample_xyz(hav_ctx* ctx, const float* points, int64_t n, int64_t m,
+                          const hav_params* params, int32_t* out_idx, float* out_xyz,
+                          hav_stream stream);
 
 /* Level chain on one cloud: level j+1 samples the points kept by level j (in
  * ascending order), the way successive set-abstraction stages of a point

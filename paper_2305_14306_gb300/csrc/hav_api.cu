@@ -44,7 +44,7 @@ hav_status check_params(const hav_params* p) {
     for (int a = 0; a < 3; ++a)
         if (!(p->aspect[a] > 0.0f) || !std::isfinite(p->aspect[a])) return HAV_ERR_INVALID;
     if ((p->flags & ~static_cast<uint32_t>(HAV_FLAG_PHASE_TIMES)) != 0) return HAV_ERR_INVALID;
-    return HAV_OK;
+    return havk::check_variant_params(p);
 }
 
 }  // namespace
@@ -60,6 +60,9 @@ void hav_params_default(hav_params* p) {
     p->layer_ratio = 4;
     p->aspect[0] = p->aspect[1] = p->aspect[2] = 1.0f;
     p->flags = 0;
+    p->select = HAV_SELECT_CENTRE_CLOSEST;
+    p->seed = 0;
+    p->fixed_s = 0.0f;
 }
 
 const char* hav_status_string(hav_status s) {
@@ -208,6 +211,9 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
     plan->chunk_min = ctx->chunk_min;
     for (int k = 0; k < 3; ++k) plan->spec_n[k] = ctx->spec_n[k];
     for (int a = 0; a < 3; ++a) plan->aspect[a] = params->aspect[a];
+    plan->select = params->select;
+    plan->seed = params->seed;
+    plan->fixed_s = params->fixed_s;
     for (int j = 0; j < num_levels; ++j) plan->out[j] = out_idx[j];
     if (params->flags & HAV_FLAG_PHASE_TIMES) {
         plan->ptimes = reinterpret_cast<unsigned long long*>(ctx->ws + ctx->lay.ptimes);
@@ -250,6 +256,19 @@ hav_status hav_sample(hav_ctx* ctx, const float* points, int64_t n, int64_t m,
     const int64_t offs[2] = {0, n};
     int32_t* outs[1] = {out_idx};
     return hav_sample_batched(ctx, points, offs, &m, 1, 1, params, outs, stream);
+}
+
+hav_status hav_sample_xyz(hav_ctx* ctx, const float* points, int64_t n, int64_t m,
+                          const hav_params* params, int32_t* out_idx, float* out_xyz, hav_stream stream) {
+    if (!params || params->layers != 1) return HAV_ERR_INVALID;
+    if (m > 0 && !out_xyz) return HAV_ERR_INVALID;
+    hav_status st = hav_sample(ctx, points, n, m, params, out_idx, stream);
+    if (st != HAV_OK || m == 0) return st;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return HAV_ERR_CUDA;
+    if (havk::launch_repr(points, n, m, out_idx, out_xyz, params->select, params->aspect, ctx->ws, ctx->lay,
+                          reinterpret_cast<cudaStream_t>(stream)) != 0)
+        return HAV_ERR_CUDA;
+    return HAV_OK;
 }
 
 hav_status hav_status_get(hav_ctx* ctx, hav_stream stream, int32_t* per_segment) {

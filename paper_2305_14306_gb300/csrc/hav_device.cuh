@@ -64,6 +64,13 @@ __device__ __forceinline__ unsigned long long priority(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
+// Draw `counter` of the SplitMix64 generator (Steele, Lea, Flood 2014)
+// started at `seed`: the state advances by the golden-ratio step before each
+// output, so draw c finalises seed + (c + 1) * step.
+__device__ __forceinline__ unsigned long long random_draw(unsigned seed, unsigned long long counter) {
+    return priority(static_cast<unsigned long long>(seed) + (counter + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+
 // ------------------------------------------------------------ Eq. 2 voxel keys
 // The cell indices are kept as integral binary32 values: floor(x / v) and
 // floor(min / v) are exact floats, and their difference u is exact whenever

@@ -2,6 +2,7 @@
 // Not part of the public interface (include/hav.h is).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -157,10 +158,23 @@ struct Plan {
     int64_t spec_n[3];           // level sizes up to which a pass looks 4, 3, 2 steps ahead
     int32_t S, L, layers, ratio, t_max, sigma_num, sigma_den, nblocks;
     float aspect[3];
-    int32_t pad;
+    int32_t select;              // HAV_SELECT_*
+    uint32_t seed;               // draws of HAV_SELECT_RANDOM
+    float fixed_s;               // > 0: fixed voxel size, no search
     int64_t off0[kMaxSegments + 1];       // level-0 segment offsets
     int32_t m[kMaxLevels][kMaxSegments];  // budgets per level and segment
 };
+
+// The Table 6 fields of hav_params: a representative rule, its seed, a fixed
+// voxel size; the variants that report other coordinates or skip the search
+// run one layer.
+inline hav_status check_variant_params(const hav_params* p) {
+    if (p->select < HAV_SELECT_CENTRE_CLOSEST || p->select > HAV_SELECT_CENTRE) return HAV_ERR_INVALID;
+    if (!(p->fixed_s >= 0.0f) || !std::isfinite(p->fixed_s)) return HAV_ERR_INVALID;
+    if ((p->fixed_s > 0.0f || p->select == HAV_SELECT_MEAN || p->select == HAV_SELECT_CENTRE) && p->layers != 1)
+        return HAV_ERR_INVALID;
+    return HAV_OK;
+}
 
 // Launchers (hav_sampler.cu).
 int max_coresident_blocks(int device);
@@ -168,6 +182,9 @@ int launch_chain(const Plan& plan, cudaStream_t stream);
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
                  unsigned char* ws, const Layout& lay, int64_t* K, cudaStream_t stream);
 int fps_coresident_blocks(int device);
+// Representative coordinates after a one-layer call (hav_repr.cu).
+int launch_repr(const float* points, long long n, long long m, const int32_t* idx, float* xyz, int select,
+                const float aspect[3], unsigned char* ws, const Layout& lay, cudaStream_t stream);
 int launch_fps(const float* points, int n, int m, int32_t* out, unsigned char* ws, const Layout& lay, int nblocks,
                cudaStream_t stream);
 

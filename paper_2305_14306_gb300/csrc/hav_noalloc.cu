@@ -80,7 +80,7 @@ hav_status check_noalloc_params(const hav_params* p) {
     for (int a = 0; a < 3; ++a)
         if (!(p->aspect[a] > 0.0f) || !std::isfinite(p->aspect[a])) return HAV_ERR_INVALID;
     if (p->flags != 0) return HAV_ERR_INVALID;
-    return HAV_OK;
+    return havk::check_variant_params(p);
 }
 
 }  // namespace
@@ -124,6 +124,9 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
         plan.nblocks = ds->nblocks;
         plan.chunk_min = havk::kChunkMin;
         for (int a = 0; a < 3; ++a) plan.aspect[a] = params->aspect[a];
+        plan.select = params->select;
+        plan.seed = params->seed;
+        plan.fixed_s = params->fixed_s;
         plan.out[0] = out_idx;
         plan.off0[0] = 0;
         plan.off0[1] = n;

@@ -1,0 +1,236 @@
+// Representative coordinates of a one-layer call: the point-selection
+// strategies of Table 6 (Section 4.5).  The centre-closest indices that
+// hav_sample returns stand for the voxel centre (CENTRE) or the voxel mean
+// (MEAN); CENTRE_CLOSEST and RANDOM report the points themselves.
+//
+// Four grid-stride kernels run after the sampler on the caller's stream, on
+// the context's workspace (free once the sampler is done):
+//   1. every output inserts its voxel key into a hash table; the first output
+//      of a voxel owns the voxel's accumulators and clears them;
+//   2. every input point of a selected voxel adds its fixed-point coordinates
+//      and a count, and lowers the voxel's packed (d^2 bits, index) minimum;
+//   3. an output that is its voxel's centre-closest point writes the centre or
+//      the mean, any other (a shortfall fill) writes itself;
+//   4. the table slots go back to empty.
+// The mean is order-independent: with 2^(k-1) <= M < 2^k for M the largest
+// |coordinate| (k = 0 when M = 0), each coordinate is the integer
+// round-half-even(x * 2^(30-k)) (exact products, |X| < 2^30, 64-bit sums),
+// and the mean is RN32(RN64(RN64(sum) / count) * 2^(k-30)).
+
+#include <cuda_runtime.h>
+
+#include "hav.h"
+#include "hav_device.cuh"
+#include "hav_internal.h"
+
+namespace havk {
+namespace {
+
+struct ReprArgs {
+    const float* pts;
+    long long n;
+    long long m;
+    const int32_t* idx;
+    float* xyz;
+    int select;
+    float aspect[3];
+    unsigned long long* keys;   // table keys (one key-table array of the workspace)
+    unsigned long long* first;  // table values: the first output of the voxel
+    int cap_log2;
+    int32_t* slot_of;           // per output: its voxel's table slot
+    long long* acc_xy;          // per output: x and y fixed-point sums
+    long long* acc_zc;          // per output: z sum and count
+    unsigned long long* best;   // per output: the voxel's packed (d^2, index) minimum
+    const hav_layer_trace* tr;  // the call's trace (level 0, segment 0, layer 0)
+    const SegHdr* sh;           // segment 0's bounding box
+    const GlobalHdr* gh;
+    const unsigned* clean;
+};
+
+struct ReprGrid {
+    Grid G;
+    double to_fixed, from_fixed;  // 2^(30-k), 2^(k-30)
+};
+
+// The grid at s* and the fixed-point scale, from the bounding box the sampler
+// computed (level parity 0 keeps it after a one-level call).
+__device__ bool repr_setup(const ReprArgs& A, ReprGrid* R) {
+    float mn[3], M = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = dec_f(~A.sh->bbox[0][a]);
+        const float mx = dec_f(A.sh->bbox[0][3 + a]);
+        M = fmaxf(M, fmaxf(fabsf(mn[a]), fabsf(mx)));
+    }
+    int k = 0;
+    if (M > 0.0f) frexpf(M, &k);
+    R->to_fixed = ldexp(1.0, 30 - k);
+    R->from_fixed = ldexp(1.0, k - 30);
+    return make_grid(A.tr->s_star, A.aspect, mn, &R->G);
+}
+
+// The table is used only after a clean, error-free sampler call.
+__device__ __forceinline__ bool repr_usable(const ReprArgs& A) {
+    return *reinterpret_cast<const volatile unsigned*>(A.clean) == 1u &&
+           *reinterpret_cast<const volatile int32_t*>(&A.gh->status) == 0;
+}
+
+__device__ __forceinline__ long long lookup(const unsigned long long* T, int cap_log2, unsigned long long key) {
+    const unsigned long long mask = (1ull << cap_log2) - 1;
+    unsigned long long slot = slot_mix(key) >> (64 - cap_log2);
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+        const unsigned long long c = T[slot];
+        if (c == key) return static_cast<long long>(slot);
+        if (c == kEmptyKey) return -1;
+        slot = (slot + 1) & mask;
+    }
+    return -1;
+}
+
+// Every output's slot is written (-1: not in the table), so the later kernels
+// touch only slots this call filled.
+__global__ void repr_insert(ReprArgs A) {
+    ReprGrid R;
+    const bool ok = repr_usable(A) && repr_setup(A, &R);
+    for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r < A.m;
+         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+        A.slot_of[r] = -1;
+        if (!ok) continue;
+        const float* p = A.pts + 3ll * A.idx[r];
+        const float p3[3] = {p[0], p[1], p[2]};
+        unsigned long long key;
+        float f[3];
+        if (!cell_key(p3, R.G, &key, f)) continue;
+        bool fresh;
+        const long long slot = find_or_insert(A.keys, A.cap_log2, key, &fresh);
+        if (slot < 0) continue;
+        A.slot_of[r] = static_cast<int32_t>(slot);
+        if (fresh) {
+            A.first[slot] = static_cast<unsigned long long>(r);
+            A.acc_xy[2 * r] = 0;
+            A.acc_xy[2 * r + 1] = 0;
+            A.acc_zc[2 * r] = 0;
+            A.acc_zc[2 * r + 1] = 0;
+            A.best[r] = kEmptyVal;
+        }
+    }
+}
+
+__global__ void repr_accumulate(ReprArgs A) {
+    if (!repr_usable(A)) return;
+    ReprGrid R;
+    if (!repr_setup(A, &R)) return;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < A.n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float p3[3] = {A.pts[3 * i], A.pts[3 * i + 1], A.pts[3 * i + 2]};
+        unsigned long long key;
+        float f[3];
+        if (!cell_key(p3, R.G, &key, f)) continue;
+        const long long slot = lookup(A.keys, A.cap_log2, key);
+        if (slot < 0) continue;  // a voxel nobody selected
+        const long long r0 = static_cast<long long>(A.first[slot]);
+        const unsigned long long packed =
+            (static_cast<unsigned long long>(__float_as_uint(centre_d2(p3, R.G, f))) << 32) |
+            static_cast<unsigned>(i);
+        atomicMin(&A.best[r0], packed);
+        if (A.select == HAV_SELECT_MEAN) {
+            long long X[3];
+            for (int a = 0; a < 3; ++a) X[a] = __double2ll_rn(__dmul_rn(static_cast<double>(p3[a]), R.to_fixed));
+            atomicAdd(reinterpret_cast<unsigned long long*>(&A.acc_xy[2 * r0]), static_cast<unsigned long long>(X[0]));
+            atomicAdd(reinterpret_cast<unsigned long long*>(&A.acc_xy[2 * r0 + 1]),
+                      static_cast<unsigned long long>(X[1]));
+            atomicAdd(reinterpret_cast<unsigned long long*>(&A.acc_zc[2 * r0]), static_cast<unsigned long long>(X[2]));
+            atomicAdd(reinterpret_cast<unsigned long long*>(&A.acc_zc[2 * r0 + 1]), 1ull);
+        }
+    }
+}
+
+__global__ void repr_write(ReprArgs A, int use_table) {
+    ReprGrid R;
+    const bool ok = use_table && repr_setup(A, &R);  // slots exist only if the table was usable
+    for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r < A.m;
+         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int32_t i = A.idx[r];
+        const float* p = A.pts + 3ll * i;
+        float out[3] = {p[0], p[1], p[2]};
+        const int32_t slot = ok ? A.slot_of[r] : -1;
+        if (slot >= 0) {
+            const long long r0 = static_cast<long long>(A.first[slot]);
+            if (static_cast<int32_t>(A.best[r0] & 0xffffffffull) == i) {  // the voxel's representative
+                unsigned long long key;
+                float f[3];
+                const float p3[3] = {p[0], p[1], p[2]};
+                cell_key(p3, R.G, &key, f);
+                if (A.select == HAV_SELECT_CENTRE) {
+                    for (int a = 0; a < 3; ++a) out[a] = __fmul_rn(R.G.v[a], __fadd_rn(f[a], 0.5f));
+                } else {
+                    const double cnt = static_cast<double>(A.acc_zc[2 * r0 + 1]);
+                    const long long sum[3] = {A.acc_xy[2 * r0], A.acc_xy[2 * r0 + 1], A.acc_zc[2 * r0]};
+                    for (int a = 0; a < 3; ++a)
+                        out[a] = __double2float_rn(
+                            __dmul_rn(__ddiv_rn(__ll2double_rn(sum[a]), cnt), R.from_fixed));
+                }
+            }
+        }
+        A.xyz[3 * r] = out[0];
+        A.xyz[3 * r + 1] = out[1];
+        A.xyz[3 * r + 2] = out[2];
+    }
+}
+
+__global__ void repr_clear(ReprArgs A) {
+    for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r < A.m;
+         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int32_t slot = A.slot_of[r];
+        if (slot < 0) continue;
+        A.keys[slot] = kEmptyKey;
+        A.first[slot] = kEmptyVal;
+    }
+}
+
+}  // namespace
+
+int launch_repr(const float* points, long long n, long long m, const int32_t* idx, float* xyz, int select,
+                const float aspect[3], unsigned char* ws, const Layout& lay, cudaStream_t stream) {
+    ReprArgs A;
+    A.pts = points;
+    A.n = n;
+    A.m = m;
+    A.idx = idx;
+    A.xyz = xyz;
+    A.select = select;
+    for (int a = 0; a < 3; ++a) A.aspect[a] = aspect[a];
+    int lg = kMinCapLog2;
+    while ((1ll << lg) < 2 * m) ++lg;
+    A.cap_log2 = lg;
+    // scratch: one key-table array and the value table (left empty again),
+    // the first fresh-insert log, both staged-point arrays, the candidate area
+    A.keys = reinterpret_cast<unsigned long long*>(ws + lay.tabk[0]);
+    A.first = reinterpret_cast<unsigned long long*>(ws + lay.tabv);
+    A.slot_of = reinterpret_cast<int32_t*>(ws + lay.dirty[0]);
+    A.acc_xy = reinterpret_cast<long long*>(ws + lay.ord[0]);
+    A.acc_zc = reinterpret_cast<long long*>(ws + lay.ord[1]);
+    A.best = reinterpret_cast<unsigned long long*>(ws + lay.cand);
+    A.tr = reinterpret_cast<const hav_layer_trace*>(ws + lay.trace);
+    A.sh = reinterpret_cast<const SegHdr*>(ws + lay.seghdr);
+    A.gh = reinterpret_cast<const GlobalHdr*>(ws + lay.ghdr);
+    A.clean = reinterpret_cast<const unsigned*>(ws + lay.clean);
+    if ((1ll << lg) > lay.tab_slots || m > lay.dirty_slots || 16 * m > 16 * lay.max_points ||
+        8 * m > static_cast<long long>(sizeof(Cand)) * lay.cand_slots)
+        return -1;
+    const int threads = 256;
+    auto blocks = [&](long long work) {
+        long long b = (work + threads - 1) / threads;
+        if (b > 4096) b = 4096;
+        return static_cast<unsigned>(b < 1 ? 1 : b);
+    };
+    const bool table = (select == HAV_SELECT_MEAN || select == HAV_SELECT_CENTRE);
+    if (table) {
+        repr_insert<<<blocks(m), threads, 0, stream>>>(A);
+        repr_accumulate<<<blocks(n), threads, 0, stream>>>(A);
+    }
+    repr_write<<<blocks(m), threads, 0, stream>>>(A, table ? 1 : 0);
+    if (table) repr_clear<<<blocks(m), threads, 0, stream>>>(A);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace havk

@@ -564,10 +564,12 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 st.sel_cand[tid] = 0;
                 st.iters[tid] = 0;
                 st.kstar[tid] = 0;
+                // a fixed voxel size (Table 6 "Fix") skips the search
+                const bool fixed = P.fixed_s > 0.0f;
                 int fl = active ? F_ACTIVE : 0;
-                if (active && P.t_max > 0) fl |= F_SEARCH;
-                if (active && P.t_max == 0) {
-                    st.s_star[tid] = st.s_hi[tid];
+                if (active && P.t_max > 0 && !fixed) fl |= F_SEARCH;
+                if (active && (P.t_max == 0 || fixed)) {
+                    st.s_star[tid] = fixed ? P.fixed_s : st.s_hi[tid];
                     if (!make_grid(st.s_star[tid], P.aspect, st.mn[tid], &st.grid[tid])) {
                         seg_error(d, tid, HAV_ERR_RANGE);
                         st.err[tid] = HAV_ERR_RANGE;
@@ -873,9 +875,15 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                                 const float p3[3] = {q4[u].x, q4[u].y, q4[u].z};
                                 float f[3];
                                 if (cell_key(p3, G, &key, f)) {
-                                    const float d2 = centre_d2(p3, G, f);
-                                    packed = (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) |
-                                             static_cast<unsigned>(g);
+                                    // the voxel keeps the smallest (word, index): the squared
+                                    // distance to the centre, or a random draw (Table 6 "RA")
+                                    const unsigned word =
+                                        (P.select == HAV_SELECT_RANDOM)
+                                            ? static_cast<unsigned>(random_draw(P.seed, static_cast<unsigned long long>(
+                                                                                            g - st.off[s])) >>
+                                                                    32)
+                                            : __float_as_uint(centre_d2(p3, G, f));
+                                    packed = (static_cast<unsigned long long>(word) << 32) | static_cast<unsigned>(g);
                                 } else {
                                     bad = HAV_ERR_RANGE;
                                     ok = false;

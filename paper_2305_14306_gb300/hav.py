@@ -32,7 +32,15 @@ class hav_params(C.Structure):
         ("layer_ratio", C.c_int32),
         ("aspect", C.c_float * 3),
         ("flags", C.c_uint32),
+        ("select", C.c_int32),
+        ("seed", C.c_uint32),
+        ("fixed_s", C.c_float),
     ]
+
+
+# voxel representatives (Table 6): the method's centre-closest point, a random
+# point, the voxel mean, the voxel centre
+SELECT = {"centre-closest": 0, "random": 1, "mean": 2, "centre": 3}
 
 
 class hav_layer_trace(C.Structure):
@@ -72,7 +80,7 @@ EXPORTS = [
     "hav_params_default", "hav_context_create", "hav_context_destroy", "hav_workspace_bytes",
     "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
     "hav_count", "hav_status_string", "hav_sample_noalloc", "hav_phase_times_get", "hav_fps",
-    "hav_context_set_blocks", "hav_context_get_tuning", "hav_context_set_tuning",
+    "hav_context_set_blocks", "hav_context_get_tuning", "hav_context_set_tuning", "hav_sample_xyz",
 ]
 HAV_FLAG_PHASE_TIMES = 1
 
@@ -102,6 +110,8 @@ def load(path: str = LIB_PATH):
         L.hav_workspace_bytes.restype = C.c_size_t
         L.hav_sample.argtypes = [vp, vp, i64, i64, P(hav_params), vp, vp]
         L.hav_sample.restype = C.c_int
+        L.hav_sample_xyz.argtypes = [vp, vp, i64, i64, P(hav_params), vp, vp, vp]
+        L.hav_sample_xyz.restype = C.c_int
         L.hav_sample_levels.argtypes = [vp, vp, i64, P(C.c_int64), i32, P(hav_params), P(vp), vp]
         L.hav_sample_levels.restype = C.c_int
         L.hav_sample_batched.argtypes = [vp, vp, P(C.c_int64), P(C.c_int64), i32, i32, P(hav_params),
@@ -132,7 +142,7 @@ def load(path: str = LIB_PATH):
 
 
 def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 1.0),
-           flags=0) -> hav_params:
+           flags=0, select="centre-closest", seed=0, fixed_s=0.0) -> hav_params:
     p = hav_params()
     load().hav_params_default(C.byref(p))
     p.sigma_num, p.sigma_den = sigma
@@ -140,6 +150,9 @@ def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 
     for a in range(3):
         p.aspect[a] = aspect[a]
     p.flags = flags
+    p.select = SELECT[select] if isinstance(select, str) else int(select)
+    p.seed = int(seed)
+    p.fixed_s = float(fixed_s)
     return p
 
 
@@ -218,6 +231,22 @@ def hav_sample(ctx: Context, points, m: int, p: hav_params | None = None, out=No
                            C.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(st, "hav_sample")
     return out
+
+
+def hav_sample_xyz(ctx: Context, points, m: int, p: hav_params | None = None, out=None, xyz=None, stream=None):
+    """One cloud, one layer: (m ascending int32 indices, (m, 3) float32 coordinates
+    standing for them: the point, the voxel centre or the voxel mean, by p.select)."""
+    import torch
+    points = _points(points)
+    p = p or params(layers=1)
+    if out is None:
+        out = torch.empty(int(m), dtype=torch.int32, device=points.device)
+    if xyz is None:
+        xyz = torch.empty((int(m), 3), dtype=torch.float32, device=points.device)
+    st = load().hav_sample_xyz(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0], int(m), C.byref(p),
+                               C.c_void_p(out.data_ptr()), C.c_void_p(xyz.data_ptr()), _stream_handle(stream))
+    _check(st, "hav_sample_xyz")
+    return out, xyz
 
 
 def hav_sample_levels(ctx: Context, points, m_levels, p: hav_params | None = None, outs=None, stream=None):

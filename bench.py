@@ -48,6 +48,9 @@ WORKLOADS = {
     "compare": {"desc": "HAV vs the plain GPU FPS comparator (Eq. 1): C1 16,384 -> 4,096; C2 LiDAR returns -> 16,384; "
                         "C4 64 LiDAR clouds -> N/4 each; C3 1,048,576 -> 262,144 (level 1); time and coverage",
                 "n": None, "levels": None},
+    "variants": {"desc": "Table 6 strategies, one layer: centre-closest / random / mean / centre representatives, "
+                         "adaptive and fixed voxel size, on C1 16,384 -> 4,096 and C3 1,048,576 -> 262,144",
+                 "n": None, "levels": None},
     "batch64": {"desc": "64 LiDAR clouds, N log-uniform in [20k, 200k], per cloud M = N/4 then N/16, "
                         "one persistent segmented launch (also replayed from a CUDA graph) vs 64 per-cloud calls",
                 "n": None, "levels": None},
@@ -463,6 +466,60 @@ def run_compare(args, world, rank, local):
     return 0
 
 
+# ----------------------------------------------------------------- Table 6 variants
+def run_variants(args, world, rank, local):
+    import torch
+    from paper_2305_14306_gb300 import hav
+
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    steps = max(5, min(args.steps, 100))
+    rows = []
+    for case, pts_np, m in (("C1 uniform 16,384 -> 4,096", scenes.uniform_box(16384, seed=0), 4096),
+                            ("C3 indoor 1,048,576 -> 262,144", scenes.room_scene(1 << 20, seed=0), 1 << 18)):
+        n = pts_np.shape[0]
+        ctx = hav.Context(n, 1)
+        d = torch.from_numpy(pts_np).cuda()
+        base = hav.params(layers=1)
+        _ = hav.hav_sample_levels(ctx, d, [m], base)
+        s_star = float(hav.hav_trace_get(ctx, 1)[0]["s_star"])
+        idx = torch.empty(m, dtype=torch.int32, device="cuda")
+        xyz = torch.empty((m, 3), dtype=torch.float32, device="cuda")
+        for sel in ("centre-closest", "random", "mean", "centre"):
+            for fixed in (0.0, s_star):
+                p = hav.params(layers=1, select=sel, seed=1, fixed_s=fixed)
+                for _ in range(3):
+                    hav.hav_sample_xyz(ctx, d, m, p, out=idx, xyz=xyz)
+                ev = []
+                for _ in range(steps):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    hav.hav_sample_xyz(ctx, d, m, p, out=idx, xyz=xyz)
+                    b.record()
+                    ev.append((a, b))
+                torch.cuda.synchronize()
+                ms = sorted(a.elapsed_time(b) for a, b in ev)
+                st, _ = hav.hav_status_get(ctx, 1)
+                tr = hav.hav_trace_get(ctx, 1)[0]
+                rows.append({"case": case, "select": sel, "voxel": "fixed" if fixed else "adaptive",
+                             "fixed_s": fixed or None, "ms_p50": ms[len(ms) // 2], "k_star": int(tr["k_star"]),
+                             "iters": int(tr["iters"]), "status": st})
+        ctx.close()
+    if rank == 0:
+        main_rows = [r for r in rows if r["select"] == "centre-closest" and r["voxel"] == "adaptive"]
+        tot_n = 16384 + (1 << 20)
+        tot_ms = sum(r["ms_p50"] for r in main_rows)
+        line = {"metric": "input Mpoints/s", "value": tot_n / tot_ms / 1e3, "unit": "Mpoints/s", "n_gpus": world,
+                "steps": steps, "warmup": 3, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "variants", "desc": WORKLOADS["variants"]["desc"],
+                           "l2": "flushed before every step (256 MB write)",
+                           "fixed_s": "the adaptive search's s* of the same cloud"},
+                "rows": rows}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------- serving arm
 def run_serving(args, world, rank, local):
     """C5: closed-loop capacity and open-loop latency (Poisson arrivals at 0.5, 0.8
@@ -574,9 +631,9 @@ def main():
     if world > 1:
         dist.barrier()
     hav.load()
-    if args.workload in ("batch64", "serving", "compare"):
-        rc = {"batch64": run_batched, "serving": run_serving, "compare": run_compare}[args.workload](
-            args, world, rank, local)
+    if args.workload in ("batch64", "serving", "compare", "variants"):
+        rc = {"batch64": run_batched, "serving": run_serving, "compare": run_compare,
+              "variants": run_variants}[args.workload](args, world, rank, local)
         if world > 1:
             dist.destroy_process_group()
         return rc

@@ -116,6 +116,8 @@ def lib():
             L.hor_s_hi.restype = C.c_float
             L.hor_fps.argtypes = [fp, i64, i64, C.POINTER(C.c_int32)]
             L.hor_fps.restype = C.c_int
+            L.hor_spacing.argtypes = [fp, i64, C.POINTER(C.c_int32), i64, fp]
+            L.hor_spacing.restype = C.c_int
             L.hor_random.argtypes = [C.c_uint32, C.c_uint64]
             L.hor_random.restype = C.c_uint64
             L.hor_sample_xyz.argtypes = [fp, i64, i64, C.POINTER(Params), C.POINTER(C.c_int32), fp,
@@ -223,6 +225,17 @@ def select(points, s, aspect=(1.0, 1.0, 1.0)):
 
 def priority(key: int) -> int:
     return int(lib().hor_priority(C.c_uint64(int(key))))
+
+
+def spacing(points, idx):
+    """Squared nearest-neighbour distance of every subset point within the subset (Fig. 3)."""
+    a = _pts(points)
+    ix = np.ascontiguousarray(idx, dtype=np.int32)
+    out = np.zeros(max(len(ix), 1), dtype=np.float32)
+    st = lib().hor_spacing(_fp(a), a.shape[0], ix.ctypes.data_as(C.POINTER(C.c_int32)), len(ix), _fp(out))
+    if st != OK:
+        raise OracleError(st)
+    return out[: len(ix)]
 
 
 def random_draw(seed: int, counter: int) -> int:

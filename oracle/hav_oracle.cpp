@@ -586,6 +586,30 @@ float hor_s_hi(const float* pts, int64_t n, const float aspect[3]) {
     return c.s_hi;
 }
 
+// Point spacing of a sampled subset (the distributions of Fig. 3, Section
+// 3.1): for each subset point, the smallest squared distance to any other
+// subset point, binary32 (dx*dx + dy*dy) + dz*dz without fusion; +inf for a
+// subset of one point.  Brute force over all pairs.
+int hor_spacing(const float* pts, int64_t n, const int32_t* idx, int64_t m, float* out_d2) {
+    if (!pts || !idx || !out_d2 || m < 0 || n < 0) return OR_ERR_INVALID;
+    for (int64_t r = 0; r < m; ++r)
+        if (idx[r] < 0 || idx[r] >= n) return OR_ERR_INVALID;
+    for (int64_t r = 0; r < m; ++r) {
+        const float* a = pts + 3 * int64_t(idx[r]);
+        float best = INFINITY;
+        for (int64_t q = 0; q < m; ++q) {
+            if (q == r) continue;
+            const float* b = pts + 3 * int64_t(idx[q]);
+            float dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+            float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+            float d2 = (xx + yy) + zz;
+            if (d2 < best) best = d2;
+        }
+        out_d2[r] = best;
+    }
+    return OR_OK;
+}
+
 // Farthest point sampling (Eq. 1), the paper's comparator: start at index 0,
 // squared distances in binary32 without fusion, argmax ties to the lowest
 // index, selected points never chosen again.

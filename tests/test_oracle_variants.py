@@ -119,3 +119,35 @@ def test_variants_reject_several_layers(oracle_mod):
             oracle_mod.sample(pts, 100, oracle_mod.params(layers=2, **kw))
     with pytest.raises(oracle_mod.OracleError):
         oracle_mod.sample(pts, 100, oracle_mod.params(layers=1, select=4))
+
+
+# ------------------------------------------------------------ Fig. 3 spacing
+def test_spacing_hand_case(oracle_mod):
+    # a line 0, 1, 3, 7 and a duplicate of 7: spacings 1, 1, 2, 0, 0 (squared)
+    pts = np.array([[0, 0, 0], [1, 0, 0], [3, 0, 0], [7, 0, 0], [7, 0, 0], [50, 50, 50]], dtype=np.float32)
+    d2 = oracle_mod.spacing(pts, [0, 1, 2, 3, 4])
+    assert d2.tolist() == [1.0, 1.0, 4.0, 0.0, 0.0]
+    assert np.isinf(oracle_mod.spacing(pts, [5])[0])
+    assert oracle_mod.spacing(pts, []).shape == (0,)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_spacing_matches_kdtree(oracle_mod, seed):
+    spatial = pytest.importorskip("scipy.spatial")
+    pts = scenes.uniform_box(4000, seed=seed)
+    idx = np.sort(np.random.default_rng(seed).choice(4000, size=1500, replace=False)).astype(np.int32)
+    d2 = oracle_mod.spacing(pts, idx)
+    sub = pts[idx].astype(np.float64)
+    dist, _ = spatial.cKDTree(sub).query(sub, k=2)
+    assert np.allclose(np.sqrt(d2.astype(np.float64)), dist[:, 1], rtol=2e-6, atol=1e-6)
+
+
+def test_fps_spacing_lower_bound(oracle_mod):
+    # the FPS property behind Fig. 3's red line: every spacing is at least the
+    # distance at which the last point was added
+    pts = scenes.uniform_box(3000, seed=4)
+    idx = oracle_mod.fps(pts, 400)
+    d2 = oracle_mod.spacing(pts, idx)
+    last = pts[idx[-1]]
+    reach = min(float(np.sum((pts[i].astype(np.float64) - last) ** 2)) for i in idx[:-1])
+    assert d2.min() >= np.float32(reach) * (1 - 1e-5)

@@ -51,6 +51,9 @@ WORKLOADS = {
     "variants": {"desc": "Table 6 strategies, one layer: centre-closest / random / mean / centre representatives, "
                          "adaptive and fixed voxel size, on C1 16,384 -> 4,096 and C3 1,048,576 -> 262,144",
                  "n": None, "levels": None},
+    "spacing": {"desc": "Fig. 3 point spacing of HAV, random-voxel (RA + fixed size), FPS and random subsets: "
+                        "C1 16,384 -> 4,096; C2 LiDAR returns -> 16,384; C3 1,048,576 -> 262,144",
+                "n": None, "levels": None},
     "batch64": {"desc": "64 LiDAR clouds, N log-uniform in [20k, 200k], per cloud M = N/4 then N/16, "
                         "one persistent segmented launch (also replayed from a CUDA graph) vs 64 per-cloud calls",
                 "n": None, "levels": None},
@@ -520,6 +523,60 @@ def run_variants(args, world, rank, local):
     return 0
 
 
+# ----------------------------------------------------------------- Fig. 3 spacing
+def run_spacing(args, world, rank, local):
+    import torch
+    from paper_2305_14306_gb300 import hav
+
+    rng = np.random.default_rng(21)
+    cases = []
+    for case, pts_np, m in (("C1 uniform 16,384 -> 4,096", scenes.uniform_box(16384, seed=0), 4096),
+                            ("C2 LiDAR returns -> 16,384", scenes.lidar_min(16384, seed=0)[0], 16384),
+                            ("C3 indoor 1,048,576 -> 262,144", scenes.room_scene(1 << 20, seed=0), 1 << 18)):
+        n = pts_np.shape[0]
+        ctx = hav.Context(n, 1)
+        d = torch.from_numpy(pts_np).cuda()
+        subsets = {}
+        subsets["HAV"] = hav.hav_sample_levels(ctx, d, [m], hav.params())[0]
+        hav.hav_sample_levels(ctx, d, [m], hav.params(layers=1))
+        s1 = float(hav.hav_trace_get(ctx, 1)[0]["s_star"])  # the one-layer search's size
+        subsets["RVS (random voxel point, fixed size)"] = hav.hav_sample_levels(
+            ctx, d, [m], hav.params(layers=1, select="random", seed=1, fixed_s=s1))[0]
+        subsets["FPS"] = hav.hav_fps(ctx, d, m)
+        subsets["RPS"] = torch.from_numpy(rng.choice(n, size=m, replace=False).astype(np.int32)).cuda()
+        res = {}
+        fps_min = None
+        for name in ("FPS", "HAV", "RVS (random voxel point, fixed size)", "RPS"):
+            idx = subsets[name]
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            d2 = hav.hav_spacing(ctx, d, idx)
+            b.record()
+            torch.cuda.synchronize()
+            sp = np.sqrt(d2.cpu().numpy().astype(np.float64))
+            if fps_min is None:
+                fps_min = float(sp.min())
+            edges = np.linspace(0.0, 3.0, 25) * fps_min  # bins in units of FPS's minimum spacing
+            hist, _ = np.histogram(np.minimum(sp, edges[-1]), bins=edges)
+            res[name] = {"min": float(sp.min()), "p10": float(np.percentile(sp, 10)),
+                         "median": float(np.median(sp)), "mean": float(sp.mean()),
+                         "below_fps_min": float((sp < fps_min).mean()),
+                         "hist_fps_min_units_0_to_3": hist.tolist(), "spacing_ms": a.elapsed_time(b)}
+        st, _ = hav.hav_status_get(ctx, 1)
+        ctx.close()
+        cases.append({"case": case, "n": n, "m": m, "fps_min_spacing": fps_min, "samplers": res, "status": st})
+    if rank == 0:
+        tot = sum(c["m"] for c in cases)
+        tms = sum(c["samplers"]["HAV"]["spacing_ms"] for c in cases)
+        line = {"metric": "subset points/s (spacing)", "value": tot / tms * 1e3, "unit": "points/s", "n_gpus": world,
+                "steps": 1, "warmup": 0, "ms_per_step": tms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "spacing", "desc": WORKLOADS["spacing"]["desc"]}, "cases": cases}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------- serving arm
 def run_serving(args, world, rank, local):
     """C5: closed-loop capacity and open-loop latency (Poisson arrivals at 0.5, 0.8
@@ -631,9 +688,9 @@ def main():
     if world > 1:
         dist.barrier()
     hav.load()
-    if args.workload in ("batch64", "serving", "compare", "variants"):
+    if args.workload in ("batch64", "serving", "compare", "variants", "spacing"):
         rc = {"batch64": run_batched, "serving": run_serving, "compare": run_compare,
-              "variants": run_variants}[args.workload](args, world, rank, local)
+              "variants": run_variants, "spacing": run_spacing}[args.workload](args, world, rank, local)
         if world > 1:
             dist.destroy_process_group()
         return rc

@@ -248,6 +248,18 @@ hav_status hav_count(hav_ctx* ctx, const float* points, int64_t n, float s,
 hav_status hav_fps(hav_ctx* ctx, const float* points, int64_t n, int64_t m, int32_t* out_idx,
                    hav_stream stream);
 
+/* Point spacing of a sampled subset, the quantity whose distributions Fig. 3
+ * (Section 3.1) compares across samplers: out_d2[r] = the smallest squared
+ * distance from subset point r to any other subset point, binary32
+ * (dx*dx + dy*dy) + dz*dz without fusion (+inf when m == 1).  points: device,
+ * n*3 floats; idx: device, m int32 indices into points (any order, repeats
+ * allowed: a repeated point has spacing 0); out_d2: device, m floats.  An
+ * index outside [0, n) is skipped and reported as HAV_ERR_INVALID by
+ * hav_status_get.  Exact all-pairs search (O(m^2) work, about 16 ms for
+ * m = 262,144 on GB300); a measurement, not part of the sampler. */
+hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32_t* idx, int64_t m,
+                       float* out_d2, hav_stream stream);
+
 /* Static description of a status code. */
 const char* hav_status_string(hav_status s);
 

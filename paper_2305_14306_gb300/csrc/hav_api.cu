@@ -271,6 +271,22 @@ hav_status hav_sample_xyz(hav_ctx* ctx, const float* points, int64_t n, int64_t 
     return HAV_OK;
 }
 
+hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32_t* idx, int64_t m,
+                       float* out_d2, hav_stream stream) {
+    if (!ctx || n < 0 || m < 0 || n >= (1ll << 31) || m >= (1ll << 31)) return HAV_ERR_INVALID;
+    if (m > 0 && (!points || !idx || !out_d2)) return HAV_ERR_INVALID;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return HAV_ERR_CUDA;
+    cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);
+    // the status words of this call start at zero
+    if (cudaMemsetAsync(ctx->ws + ctx->lay.barrier, 0, ctx->lay.zero_bytes, strm) != cudaSuccess) return HAV_ERR_CUDA;
+    ctx->last_S = 1;
+    if (m == 0) return HAV_OK;
+    havk::GlobalHdr* gh = reinterpret_cast<havk::GlobalHdr*>(ctx->ws + ctx->lay.ghdr);
+    if (havk::launch_spacing(points, n, idx, m, out_d2, &gh->status, ctx->max_blocks, strm) != 0)
+        return HAV_ERR_CUDA;
+    return HAV_OK;
+}
+
 hav_status hav_status_get(hav_ctx* ctx, hav_stream stream, int32_t* per_segment) {
     if (!ctx) return HAV_ERR_INVALID;
     cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);

@@ -182,6 +182,9 @@ int launch_chain(const Plan& plan, cudaStream_t stream);
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
                  unsigned char* ws, const Layout& lay, int64_t* K, cudaStream_t stream);
 int fps_coresident_blocks(int device);
+// Subset point spacing (hav_spacing.cu).
+int launch_spacing(const float* points, long long n, const int32_t* idx, long long m, float* out_d2,
+                   int32_t* status, int sms, cudaStream_t stream);
 // Representative coordinates after a one-layer call (hav_repr.cu).
 int launch_repr(const float* points, long long n, long long m, const int32_t* idx, float* xyz, int select,
                 const float aspect[3], unsigned char* ws, const Layout& lay, cudaStream_t stream);

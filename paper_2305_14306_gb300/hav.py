@@ -81,6 +81,7 @@ EXPORTS = [
     "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
     "hav_count", "hav_status_string", "hav_sample_noalloc", "hav_phase_times_get", "hav_fps",
     "hav_context_set_blocks", "hav_context_get_tuning", "hav_context_set_tuning", "hav_sample_xyz",
+    "hav_spacing",
 ]
 HAV_FLAG_PHASE_TIMES = 1
 
@@ -110,6 +111,8 @@ def load(path: str = LIB_PATH):
         L.hav_workspace_bytes.restype = C.c_size_t
         L.hav_sample.argtypes = [vp, vp, i64, i64, P(hav_params), vp, vp]
         L.hav_sample.restype = C.c_int
+        L.hav_spacing.argtypes = [vp, vp, i64, vp, i64, vp, vp]
+        L.hav_spacing.restype = C.c_int
         L.hav_sample_xyz.argtypes = [vp, vp, i64, i64, P(hav_params), vp, vp, vp]
         L.hav_sample_xyz.restype = C.c_int
         L.hav_sample_levels.argtypes = [vp, vp, i64, P(C.c_int64), i32, P(hav_params), P(vp), vp]
@@ -331,6 +334,20 @@ def hav_fps(ctx: Context, points, m: int, out=None, stream=None):
     st = load().hav_fps(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0], int(m),
                         C.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(st, "hav_fps")
+    return out
+
+
+def hav_spacing(ctx: Context, points, idx, out=None, stream=None):
+    """Squared distance from each subset point to its nearest other subset point (Fig. 3)."""
+    import torch
+    points = _points(points)
+    idx = idx.to(dtype=torch.int32, device=points.device).contiguous()
+    m = idx.shape[0]
+    if out is None:
+        out = torch.empty(m, dtype=torch.float32, device=points.device)
+    st = load().hav_spacing(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0],
+                            C.c_void_p(idx.data_ptr()), m, C.c_void_p(out.data_ptr()), _stream_handle(stream))
+    _check(st, "hav_spacing")
     return out
 
 

@@ -1,0 +1,88 @@
+"""GPU parity of the subset point spacing (Fig. 3, Section 3.1) through the C
+ABI: bit-identical squared nearest-neighbour distances to the oracle's."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+sys.path.insert(0, os.path.dirname(__file__))
+from paper_2305_14306_gb300 import scenes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_14306_gb300 import build, hav
+    build.build()
+    hav.load()
+    return hav
+
+
+@pytest.fixture(scope="module")
+def ctx(hv):
+    c = hv.Context(1 << 17, 4)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def check(hv, ctx, oracle_mod, pts, idx):
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    got = hv.hav_spacing(ctx, dev(pts), torch.from_numpy(idx).cuda()).cpu().numpy()
+    st, _ = hv.hav_status_get(ctx, 1)
+    assert st == 0
+    want = oracle_mod.spacing(pts, idx)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), np.nonzero(got != want)[0][:5]
+    return got
+
+
+def test_spacing_of_samplers(hv, ctx, oracle_mod):
+    pts = scenes.uniform_box(16384, seed=3)
+    d = dev(pts)
+    hav_idx = hv.hav_sample(ctx, d, 4096).cpu().numpy()
+    fps_idx = hv.hav_fps(ctx, d, 1500).cpu().numpy()
+    rnd_idx = np.random.default_rng(0).choice(16384, size=5000, replace=False)
+    for idx in (hav_idx, fps_idx, rnd_idx):
+        check(hv, ctx, oracle_mod, pts, idx)
+
+
+def test_spacing_lidar_subset_and_order(hv, ctx, oracle_mod):
+    pts = scenes.lidar_min(16384, seed=2)[0]
+    idx = hv.hav_sample(ctx, dev(pts), 8192).cpu().numpy()
+    a = check(hv, ctx, oracle_mod, pts, idx)
+    perm = np.random.default_rng(1).permutation(len(idx))
+    b = check(hv, ctx, oracle_mod, pts, idx[perm])
+    assert np.array_equal(a[perm], b)
+
+
+def test_spacing_edges(hv, ctx, oracle_mod):
+    pts = np.array([[0, 0, 0], [1, 0, 0], [3, 0, 0], [7, 0, 0], [7, 0, 0]], dtype=np.float32)
+    got = check(hv, ctx, oracle_mod, pts, [0, 1, 2, 3, 4])
+    assert got.tolist() == [1.0, 1.0, 4.0, 0.0, 0.0]
+    got = check(hv, ctx, oracle_mod, pts, [2, 2, 1])  # a repeated index is at distance 0
+    assert got.tolist() == [0.0, 0.0, 4.0]
+    assert np.isinf(check(hv, ctx, oracle_mod, pts, [3])[0])
+    out = hv.hav_spacing(ctx, dev(pts), torch.zeros(0, dtype=torch.int32, device="cuda"))
+    assert out.shape == (0,)
+    # ragged sizes around the tile and block sizes
+    big = scenes.uniform_box(9000, seed=5)
+    for m in (1023, 1024, 1025, 4097, 8999):
+        check(hv, ctx, oracle_mod, big, np.arange(m))
+
+
+def test_spacing_rejects_bad_indices(hv, ctx):
+    pts = dev(scenes.uniform_box(100, seed=1))
+    hv.hav_spacing(ctx, pts, torch.tensor([0, 5, 100, 7], dtype=torch.int32, device="cuda"))
+    st, _ = hv.hav_status_get(ctx, 1)
+    assert st == hv.HAV_ERR_INVALID
+    hv.hav_spacing(ctx, pts, torch.tensor([0, 5, 7], dtype=torch.int32, device="cuda"))
+    st, _ = hv.hav_status_get(ctx, 1)
+    assert st == 0

@@ -116,6 +116,9 @@ def lib():
             L.hor_s_hi.restype = C.c_float
             L.hor_fps.argtypes = [fp, i64, i64, C.POINTER(C.c_int32)]
             L.hor_fps.restype = C.c_int
+            L.hor_ball_query.argtypes = [fp, i64, C.POINTER(C.c_int32), i64, C.c_float, C.c_int32,
+                                         C.POINTER(C.c_int32), fp]
+            L.hor_ball_query.restype = C.c_int
             L.hor_spacing.argtypes = [fp, i64, C.POINTER(C.c_int32), i64, fp]
             L.hor_spacing.restype = C.c_int
             L.hor_random.argtypes = [C.c_uint32, C.c_uint64]
@@ -225,6 +228,22 @@ def select(points, s, aspect=(1.0, 1.0, 1.0)):
 
 def priority(key: int) -> int:
     return int(lib().hor_priority(C.c_uint64(int(key))))
+
+
+def ball_query(points, centres, radius, nsample):
+    """Grouping around centres (indices into points): (m, nsample) int32 indices and
+    (m, nsample, 3) float32 offsets p_k - c_j."""
+    a = _pts(points)
+    c = np.ascontiguousarray(centres, dtype=np.int32)
+    m = len(c)
+    idx = np.zeros((max(m, 1), nsample), dtype=np.int32)
+    xyz = np.zeros((max(m, 1), nsample, 3), dtype=np.float32)
+    st = lib().hor_ball_query(_fp(a), a.shape[0], c.ctypes.data_as(C.POINTER(C.c_int32)), m,
+                              float(np.float32(radius)), int(nsample), idx.ctypes.data_as(C.POINTER(C.c_int32)),
+                              _fp(xyz))
+    if st != OK:
+        raise OracleError(st)
+    return idx[:m], xyz[:m]
 
 
 def spacing(points, idx):

@@ -610,6 +610,38 @@ int hor_spacing(const float* pts, int64_t n, const int32_t* idx, int64_t m, floa
     return OR_OK;
 }
 
+// Grouping around sampled centres, the step that follows sampling in the
+// sample-group-aggregate block (Section 3.1; the ball query of PointNet++):
+// for centre j (the point centres[j]), the nsample smallest indices k with
+// (dx*dx + dy*dy) + dz*dz < radius*radius in binary32, ascending; if fewer
+// qualify, the remaining slots repeat the smallest.  The centre itself always
+// qualifies.  out_xyz (optional) receives p_k - c_j per slot.
+int hor_ball_query(const float* pts, int64_t n, const int32_t* centres, int64_t m, float radius,
+                   int32_t nsample, int32_t* out_idx, float* out_xyz) {
+    if (!pts || (m > 0 && (!centres || !out_idx)) || n < 0 || m < 0 || nsample < 1) return OR_ERR_INVALID;
+    if (!(radius > 0.0f) || !std::isfinite(radius)) return OR_ERR_INVALID;
+    const float r2 = radius * radius;
+    for (int64_t j = 0; j < m; ++j) {
+        if (centres[j] < 0 || centres[j] >= n) return OR_ERR_INVALID;
+        const float* c = pts + 3 * int64_t(centres[j]);
+        int32_t cnt = 0;
+        int32_t* row = out_idx + j * int64_t(nsample);
+        for (int64_t k = 0; k < n && cnt < nsample; ++k) {
+            const float* q = pts + 3 * k;
+            float dx = q[0] - c[0], dy = q[1] - c[1], dz = q[2] - c[2];
+            float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+            float d2 = (xx + yy) + zz;
+            if (d2 < r2) row[cnt++] = static_cast<int32_t>(k);
+        }
+        for (int32_t s = cnt; s < nsample; ++s) row[s] = row[0];
+        if (out_xyz)
+            for (int32_t s = 0; s < nsample; ++s)
+                for (int a = 0; a < 3; ++a)
+                    out_xyz[(j * int64_t(nsample) + s) * 3 + a] = pts[3 * int64_t(row[s]) + a] - c[a];
+    }
+    return OR_OK;
+}
+
 // Farthest point sampling (Eq. 1), the paper's comparator: start at index 0,
 // squared distances in binary32 without fusion, argmax ties to the lowest
 // index, selected points never chosen again.

@@ -151,3 +151,35 @@ def test_fps_spacing_lower_bound(oracle_mod):
     last = pts[idx[-1]]
     reach = min(float(np.sum((pts[i].astype(np.float64) - last) ** 2)) for i in idx[:-1])
     assert d2.min() >= np.float32(reach) * (1 - 1e-5)
+
+
+# --------------------------------------------------- grouping (ball query)
+def test_ball_query_hand_case(oracle_mod):
+    # a line at x = 0, 1, 2, 5, 5.5; radius 1.5: strict inequality, index order, padding
+    pts = np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0], [5, 0, 0], [5.5, 0, 0]], dtype=np.float32)
+    idx, xyz = oracle_mod.ball_query(pts, [1, 3, 0], 1.5, 4)
+    assert idx.tolist() == [[0, 1, 2, 0], [3, 4, 3, 3], [0, 1, 0, 0]]
+    assert xyz[0, :, 0].tolist() == [-1.0, 0.0, 1.0, -1.0]
+    assert xyz[1, :, 0].tolist() == [0.0, 0.5, 0.0, 0.0]
+    # a point exactly at the radius is outside (d^2 < r^2)
+    idx, _ = oracle_mod.ball_query(pts, [0], 1.0, 3)
+    assert idx.tolist() == [[0, 0, 0]]
+
+
+@pytest.mark.parametrize("radius,nsample", [(2.0, 16), (4.5, 64), (0.5, 8)])
+def test_ball_query_matches_kdtree(oracle_mod, radius, nsample):
+    spatial = pytest.importorskip("scipy.spatial")
+    pts = scenes.uniform_box(6000, seed=2)
+    centres = oracle_mod.sample(pts, 500, oracle_mod.params(layers=1))
+    idx, xyz = oracle_mod.ball_query(pts, centres, radius, nsample)
+    tree = spatial.cKDTree(pts.astype(np.float64))
+    r2 = np.float32(radius) * np.float32(radius)
+    for j, c in enumerate(centres):
+        near = sorted(tree.query_ball_point(pts[c].astype(np.float64), radius * (1 + 1e-5)))
+        # drop the points whose binary32 distance is not strictly inside
+        d = pts[near] - pts[c]
+        d2 = ((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]).astype(np.float32) + d[:, 2] * d[:, 2]).astype(np.float32)
+        inside = [k for k, q in zip(near, d2) if q < r2]
+        want = inside[:nsample] + [inside[0]] * max(0, nsample - len(inside))
+        assert idx[j].tolist() == want
+        assert np.array_equal(xyz[j], (pts[idx[j]] - pts[c]).astype(np.float32))

@@ -54,6 +54,9 @@ WORKLOADS = {
     "spacing": {"desc": "Fig. 3 point spacing of HAV, random-voxel (RA + fixed size), FPS and random subsets: "
                         "C1 16,384 -> 4,096; C2 LiDAR returns -> 16,384; C3 1,048,576 -> 262,144",
                 "n": None, "levels": None},
+    "grouping": {"desc": "grouping after sampling (ball query, fused offset gather): C2 LiDAR 4,096 centres r = 0.8 m, "
+                         "C3 262,144 centres of 1,048,576 r = 0.1 m and 65,536 centres r = 0.2 m, 32 samples",
+                 "n": None, "levels": None},
     "batch64": {"desc": "64 LiDAR clouds, N log-uniform in [20k, 200k], per cloud M = N/4 then N/16, "
                         "one persistent segmented launch (also replayed from a CUDA graph) vs 64 per-cloud calls",
                 "n": None, "levels": None},
@@ -577,6 +580,52 @@ def run_spacing(args, world, rank, local):
     return 0
 
 
+# ----------------------------------------------------------------- grouping
+def run_grouping(args, world, rank, local):
+    import torch
+    from paper_2305_14306_gb300 import hav
+
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    steps = max(5, min(args.steps, 50))
+    rows = []
+    for case, pts_np, m, radius, ns in (
+            ("C2 LiDAR, 4,096 centres, r 0.8 m", scenes.lidar_min(16384, seed=0)[0], 4096, 0.8, 32),
+            ("C3 indoor, 262,144 centres, r 0.1 m", scenes.room_scene(1 << 20, seed=0), 1 << 18, 0.1, 32),
+            ("C3 indoor, 65,536 centres, r 0.2 m", scenes.room_scene(1 << 20, seed=0), 1 << 16, 0.2, 32)):
+        n = pts_np.shape[0]
+        ctx = hav.Context(n, 1)
+        d = torch.from_numpy(pts_np).cuda()
+        centres = hav.hav_sample(ctx, d, m)
+        out = torch.empty((m, ns), dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            hav.hav_ball_query(ctx, d, centres, radius, ns, out=out)
+        ev = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            hav.hav_ball_query(ctx, d, centres, radius, ns, out=out)
+            b.record()
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        st, _ = hav.hav_status_get(ctx, 1)
+        filled = float((out[:, 1:] != out[:, :1]).any(dim=1).float().mean())
+        rows.append({"case": case, "n": n, "m": m, "radius": radius, "nsample": ns, "ms_p50": ms[len(ms) // 2],
+                     "centres_per_s": m / ms[len(ms) // 2] * 1e3, "share_with_neighbours": filled, "status": st})
+        ctx.close()
+    if rank == 0:
+        tot_m = sum(r["m"] for r in rows)
+        tot_ms = sum(r["ms_p50"] for r in rows)
+        line = {"metric": "centres/s (grouping)", "value": tot_m / tot_ms * 1e3, "unit": "centres/s",
+                "n_gpus": world, "steps": steps, "warmup": 3, "ms_per_step": tot_ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "grouping", "desc": WORKLOADS["grouping"]["desc"],
+                           "l2": "flushed before every step (256 MB write)"}, "rows": rows}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------- serving arm
 def run_serving(args, world, rank, local):
     """C5: closed-loop capacity and open-loop latency (Poisson arrivals at 0.5, 0.8
@@ -688,9 +737,10 @@ def main():
     if world > 1:
         dist.barrier()
     hav.load()
-    if args.workload in ("batch64", "serving", "compare", "variants", "spacing"):
-        rc = {"batch64": run_batched, "serving": run_serving, "compare": run_compare,
-              "variants": run_variants, "spacing": run_spacing}[args.workload](args, world, rank, local)
+    arms = {"batch64": run_batched, "serving": run_serving, "compare": run_compare,
+            "variants": run_variants, "spacing": run_spacing, "grouping": run_grouping}
+    if args.workload in arms:
+        rc = arms[args.workload](args, world, rank, local)
         if world > 1:
             dist.destroy_process_group()
         return rc

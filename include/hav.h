@@ -260,6 +260,22 @@ hav_status hav_fps(hav_ctx* ctx, const float* points, int64_t n, int64_t m, int3
 hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32_t* idx, int64_t m,
                        float* out_d2, hav_stream stream);
 
+/* Grouping around sampled centres, the step that follows sampling in the
+ * sample-group-aggregate block of point networks (Section 3.1; the ball query
+ * of PointNet++): for centre j (the point centres[j]), the nsample smallest
+ * point indices k with (dx*dx + dy*dy) + dz*dz < radius*radius (binary32, no
+ * fusion), ascending; if fewer qualify, the remaining slots repeat the
+ * smallest (the centre itself always qualifies).  out_xyz, when not NULL,
+ * receives p_k - c_j for every slot (the block's gather, fused).
+ * points: device, n*3 floats, n <= the context's max_points; centres: device,
+ * m int32 (e.g. the indices hav_sample returned); out_idx: device,
+ * m*nsample int32; out_xyz: device, m*nsample*3 floats or NULL.
+ * radius finite and > 0; 1 <= nsample <= 256.  A centre outside [0, n) gets
+ * zeros and HAV_ERR_INVALID in hav_status_get.  Uses the context's workspace
+ * (the phase-timer records of an earlier call are overwritten). */
+hav_status hav_ball_query(hav_ctx* ctx, const float* points, int64_t n, const int32_t* centres, int64_t m,
+                          float radius, int32_t nsample, int32_t* out_idx, float* out_xyz, hav_stream stream);
+
 /* Static description of a status code. */
 const char* hav_status_string(hav_status s);
 

@@ -287,6 +287,23 @@ hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32
     return HAV_OK;
 }
 
+hav_status hav_ball_query(hav_ctx* ctx, const float* points, int64_t n, const int32_t* centres, int64_t m,
+                          float radius, int32_t nsample, int32_t* out_idx, float* out_xyz, hav_stream stream) {
+    if (!ctx || n < 0 || m < 0 || n > ctx->lay.max_points || m >= (1ll << 31)) return HAV_ERR_INVALID;
+    if (nsample < 1 || nsample > 256 || !(radius > 0.0f) || !std::isfinite(radius)) return HAV_ERR_INVALID;
+    if (m > 0 && (!points || !centres || !out_idx)) return HAV_ERR_INVALID;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return HAV_ERR_CUDA;
+    cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ctx->ws + ctx->lay.barrier, 0, ctx->lay.zero_bytes, strm) != cudaSuccess) return HAV_ERR_CUDA;
+    ctx->last_S = 1;
+    if (m == 0) return HAV_OK;
+    havk::GlobalHdr* gh = reinterpret_cast<havk::GlobalHdr*>(ctx->ws + ctx->lay.ghdr);
+    if (havk::launch_ball_query(points, n, centres, m, radius, nsample, out_idx, out_xyz, ctx->ws, ctx->lay,
+                                &gh->status, strm) != 0)
+        return HAV_ERR_CUDA;
+    return HAV_OK;
+}
+
 hav_status hav_status_get(hav_ctx* ctx, hav_stream stream, int32_t* per_segment) {
     if (!ctx) return HAV_ERR_INVALID;
     cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);

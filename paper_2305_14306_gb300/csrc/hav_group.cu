@@ -1,0 +1,275 @@
+// Grouping around sampled centres: the step after sampling in the
+// sample-group-aggregate block (Section 3.1), the ball query of PointNet++.
+// For centre j (point centres[j]) the nsample smallest indices k with
+// (dx*dx + dy*dy) + dz*dz < radius*radius (binary32, no fusion), ascending;
+// missing slots repeat the smallest.  The offsets p_k - c_j of every slot are
+// written beside them (the gather of the block, fused).
+//
+// A uniform grid with cells of at least the radius (so every ball lies in the
+// 3 x 3 x 3 cells around its centre's cell) is built by a counting sort of the
+// points by cell; one thread per centre then scans those cells and keeps the
+// nsample smallest qualifying indices in a sorted array.  The result does not
+// depend on the grid, only the work does.  Kernels, on the caller's stream:
+// bounding box, grid set-up, cell counts, a three-stage exclusive scan,
+// scatter, query.
+
+#include <cuda_runtime.h>
+
+#include "hav.h"
+#include "hav_device.cuh"
+#include "hav_internal.h"
+
+namespace havk {
+namespace {
+
+constexpr int kGrpMaxSample = 256;
+constexpr int kScanItems = 4;                        // cells per thread in the scan
+constexpr int kScanBlock = 1024 * kScanItems;       // cells per scan block
+constexpr long long kMaxCells = 1ll << 24;
+
+struct GroupGrid {
+    uint32_t box[6];  // ~enc(min xyz), enc(max xyz), atomicMax'ed
+    float mn[3];
+    float inv_h;
+    int dims[3];
+    int pad;
+    long long cells;
+};
+
+__device__ __forceinline__ int axis_cell(float x, float mn, float inv_h, int dim) {
+    const float t = __fmul_rn(__fsub_rn(x, mn), inv_h);
+    int c = (t > 0.0f) ? static_cast<int>(t) : 0;
+    return c < dim ? c : dim - 1;
+}
+
+__device__ __forceinline__ long long cell_of(const float* p, const GroupGrid& g, int c[3]) {
+    for (int a = 0; a < 3; ++a) c[a] = axis_cell(p[a], g.mn[a], g.inv_h, g.dims[a]);
+    return (static_cast<long long>(c[2]) * g.dims[1] + c[1]) * g.dims[0] + c[0];
+}
+
+__global__ void grp_bbox(const float* pts, long long n, GroupGrid* g) {
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            const float x = pts[3 * i + a];
+            if (isfinite(x)) {
+                mn[a] = fminf(mn[a], x);
+                mx[a] = fmaxf(mx[a], x);
+            }
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 3; ++a) {
+            if (isfinite(mn[a])) atomicMax(&g->box[a], ~enc_f(mn[a]));
+            if (isfinite(mx[a])) atomicMax(&g->box[3 + a], enc_f(mx[a]));
+        }
+}
+
+// Cell size h >= radius (1 + 2^-10) and at least 1/256 of the largest
+// extent, grown by 2^(1/3) until the grid has at most `budget` cells.  With
+// at most 257 cells per axis the cell map t = (x - mn) * RN(1/h) is off by
+// under 2^-12 cells, so two points closer than the radius (under 1 - 2^-10
+// cells apart) never land more than one cell apart.
+__global__ void grp_setup(GroupGrid* g, float radius, long long budget) {
+    float ext = 0.0f, e[3];
+    for (int a = 0; a < 3; ++a) {
+        g->mn[a] = dec_f(~g->box[a]);
+        const float mx = dec_f(g->box[3 + a]);
+        e[a] = (mx >= g->mn[a]) ? __fsub_rn(mx, g->mn[a]) : 0.0f;
+        ext = fmaxf(ext, e[a]);
+        if (!(mx >= g->mn[a])) g->mn[a] = 0.0f;  // no finite point
+    }
+    float h = fmaxf(__fmul_rn(radius, 1.0009765625f), __fmul_rn(ext, 0.00390625f));
+    long long cells = 0;
+    for (int guard = 0; guard < 200; ++guard) {
+        cells = 1;
+        for (int a = 0; a < 3; ++a) {
+            const long long d = static_cast<long long>(__fdiv_rn(e[a], h)) + 1;
+            g->dims[a] = static_cast<int>(d);
+            cells *= d;
+        }
+        if (cells <= budget) break;
+        h = __fmul_rn(h, 1.2599210739135742f);
+    }
+    g->inv_h = __fdiv_rn(1.0f, h);
+    g->cells = cells;
+}
+
+__global__ void grp_count(const float* pts, long long n, const GroupGrid* g, uint32_t* counts) {
+    const GroupGrid G = *g;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        int c[3];
+        atomicAdd(&counts[cell_of(pts + 3 * i, G, c)], 1u);
+    }
+}
+
+// exclusive scan of counts[0..cells): block sums, a scan of those, then the offsets
+__global__ void grp_scan_local(uint32_t* v, const GroupGrid* g, uint32_t* block_sums) {
+    __shared__ uint32_t scratch[32];
+    const long long cells = g->cells;
+    const long long base = static_cast<long long>(blockIdx.x) * kScanBlock;
+    if (base >= cells) return;
+    uint32_t x[kScanItems], sum = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        const long long i = base + threadIdx.x * kScanItems + k;
+        x[k] = (i < cells) ? v[i] : 0u;
+        sum += x[k];
+    }
+    uint32_t tot;
+    uint32_t before = block_excl_scan<uint32_t>(sum, &tot, scratch);
+    for (int k = 0; k < kScanItems; ++k) {
+        const long long i = base + threadIdx.x * kScanItems + k;
+        if (i < cells) v[i] = before;
+        before += x[k];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void grp_scan_sums(uint32_t* block_sums, const GroupGrid* g) {
+    __shared__ uint32_t scratch[32];
+    const long long nb = (g->cells + kScanBlock - 1) / kScanBlock;  // <= kMaxCells / kScanBlock = 4096
+    uint32_t x[kScanItems], sum = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        const long long i = threadIdx.x * kScanItems + k;
+        x[k] = (i < nb) ? block_sums[i] : 0u;
+        sum += x[k];
+    }
+    uint32_t tot;
+    uint32_t before = block_excl_scan<uint32_t>(sum, &tot, scratch);
+    for (int k = 0; k < kScanItems; ++k) {
+        const long long i = threadIdx.x * kScanItems + k;
+        if (i < nb) block_sums[i] = before;
+        before += x[k];
+    }
+}
+
+__global__ void grp_scan_add(uint32_t* v, const GroupGrid* g, const uint32_t* block_sums) {
+    const long long cells = g->cells;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < cells;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        v[i] += block_sums[i / kScanBlock];
+}
+
+// after this, start[c] holds the end of cell c (its start is end[c - 1])
+__global__ void grp_scatter(const float* pts, long long n, const GroupGrid* g, uint32_t* start, int32_t* list) {
+    const GroupGrid G = *g;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        int c[3];
+        const uint32_t pos = atomicAdd(&start[cell_of(pts + 3 * i, G, c)], 1u);
+        if (pos < static_cast<uint32_t>(n)) list[pos] = static_cast<int32_t>(i);
+    }
+}
+
+__global__ void grp_query(const float* pts, long long n, const int32_t* centres, long long m, float radius,
+                          int nsample, const GroupGrid* g, const uint32_t* end, const int32_t* list,
+                          int32_t* out_idx, float* out_xyz, int32_t* status) {
+    const GroupGrid G = *g;
+    const float r2 = __fmul_rn(radius, radius);
+    int32_t best[kGrpMaxSample];
+    for (long long j = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; j < m;
+         j += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int32_t ci = centres[j];
+        int32_t* row = out_idx + j * nsample;
+        if (ci < 0 || ci >= n) {
+            atomicCAS(status, 0, static_cast<int>(HAV_ERR_INVALID));
+            for (int s = 0; s < nsample; ++s) row[s] = 0;
+            if (out_xyz)
+                for (int s = 0; s < 3 * nsample; ++s) out_xyz[j * 3 * nsample + s] = 0.0f;
+            continue;
+        }
+        const float cx = pts[3ll * ci], cy = pts[3ll * ci + 1], cz = pts[3ll * ci + 2];
+        int c[3];
+        const float cp[3] = {cx, cy, cz};
+        cell_of(cp, G, c);
+        int cnt = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int z = c[2] + dz;
+            if (z < 0 || z >= G.dims[2]) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y = c[1] + dy;
+                if (y < 0 || y >= G.dims[1]) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x = c[0] + dx;
+                    if (x < 0 || x >= G.dims[0]) continue;
+                    const long long cell = (static_cast<long long>(z) * G.dims[1] + y) * G.dims[0] + x;
+                    const uint32_t a = (cell > 0) ? end[cell - 1] : 0u;
+                    const uint32_t b = end[cell];
+                    for (uint32_t q = a; q < b && q < static_cast<uint32_t>(n); ++q) {
+                        const int32_t k = list[q];
+                        if (cnt == nsample && k >= best[nsample - 1]) continue;
+                        const float ex = __fsub_rn(pts[3ll * k], cx), ey = __fsub_rn(pts[3ll * k + 1], cy),
+                                    ez = __fsub_rn(pts[3ll * k + 2], cz);
+                        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+                        if (!(d2 < r2)) continue;
+                        // insert k into the sorted best[0..cnt), keeping at most nsample
+                        int at = (cnt < nsample) ? cnt : nsample - 1;
+                        while (at > 0 && best[at - 1] > k) {
+                            best[at] = best[at - 1];
+                            --at;
+                        }
+                        best[at] = k;
+                        if (cnt < nsample) ++cnt;
+                    }
+                }
+            }
+        }
+        if (cnt == 0) best[cnt++] = ci;  // unreachable: the centre is at distance 0
+        for (int s = 0; s < nsample; ++s) {
+            const int32_t k = (s < cnt) ? best[s] : best[0];
+            row[s] = k;
+            if (out_xyz) {
+                float* o = out_xyz + (j * nsample + s) * 3;
+                o[0] = __fsub_rn(pts[3ll * k], cx);
+                o[1] = __fsub_rn(pts[3ll * k + 1], cy);
+                o[2] = __fsub_rn(pts[3ll * k + 2], cz);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int launch_ball_query(const float* points, long long n, const int32_t* centres, long long m, float radius,
+                      int nsample, int32_t* out_idx, float* out_xyz, unsigned char* ws, const Layout& lay,
+                      int32_t* status, cudaStream_t stream) {
+    if (nsample < 1 || nsample > kGrpMaxSample) return -1;
+    // scratch: grid parameters and scan block sums in the phase-timer area,
+    // cell counts in the candidate area, the sorted point list in staged points
+    GroupGrid* g = reinterpret_cast<GroupGrid*>(ws + lay.ptimes);
+    uint32_t* block_sums = reinterpret_cast<uint32_t*>(ws + lay.ptimes + 256);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(ws + lay.cand);
+    int32_t* list = reinterpret_cast<int32_t*>(ws + lay.ord[0]);
+    long long budget = static_cast<long long>(sizeof(Cand)) * lay.cand_slots / 4;
+    if (budget > kMaxCells) budget = kMaxCells;
+    if (n > lay.max_points) return -1;
+    static_assert(256 + 4 * (kMaxCells / kScanBlock) <= 2 * 8 * kPhaseTimes, "scan scratch fits");
+    const int t = 256;
+    auto blocks = [&](long long work) {
+        long long b = (work + t - 1) / t;
+        if (b > 4096) b = 4096;
+        return static_cast<unsigned>(b < 1 ? 1 : b);
+    };
+    if (cudaMemsetAsync(g, 0, sizeof(GroupGrid), stream) != cudaSuccess) return -1;
+    grp_bbox<<<blocks(n), t, 0, stream>>>(points, n, g);
+    grp_setup<<<1, 1, 0, stream>>>(g, radius, budget);
+    // the grid size is known on the device only: size the cell work by the budget
+    if (cudaMemsetAsync(counts, 0, 4 * budget, stream) != cudaSuccess) return -1;
+    grp_count<<<blocks(n), t, 0, stream>>>(points, n, g, counts);
+    grp_scan_local<<<static_cast<unsigned>((budget + kScanBlock - 1) / kScanBlock), 1024, 0, stream>>>(counts, g,
+                                                                                                       block_sums);
+    grp_scan_sums<<<1, 1024, 0, stream>>>(block_sums, g);
+    grp_scan_add<<<blocks(budget), t, 0, stream>>>(counts, g, block_sums);
+    grp_scatter<<<blocks(n), t, 0, stream>>>(points, n, g, counts, list);
+    grp_query<<<blocks(m), 128, 0, stream>>>(points, n, centres, m, radius, nsample, g, counts, list, out_idx,
+                                             out_xyz, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace havk

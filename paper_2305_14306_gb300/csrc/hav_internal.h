@@ -182,6 +182,10 @@ int launch_chain(const Plan& plan, cudaStream_t stream);
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
                  unsigned char* ws, const Layout& lay, int64_t* K, cudaStream_t stream);
 int fps_coresident_blocks(int device);
+// Grouping around centres (hav_group.cu).
+int launch_ball_query(const float* points, long long n, const int32_t* centres, long long m, float radius,
+                      int nsample, int32_t* out_idx, float* out_xyz, unsigned char* ws, const Layout& lay,
+                      int32_t* status, cudaStream_t stream);
 // Subset point spacing (hav_spacing.cu).
 int launch_spacing(const float* points, long long n, const int32_t* idx, long long m, float* out_d2,
                    int32_t* status, int sms, cudaStream_t stream);

@@ -81,7 +81,7 @@ EXPORTS = [
     "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
     "hav_count", "hav_status_string", "hav_sample_noalloc", "hav_phase_times_get", "hav_fps",
     "hav_context_set_blocks", "hav_context_get_tuning", "hav_context_set_tuning", "hav_sample_xyz",
-    "hav_spacing",
+    "hav_spacing", "hav_ball_query",
 ]
 HAV_FLAG_PHASE_TIMES = 1
 
@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH):
         L.hav_workspace_bytes.restype = C.c_size_t
         L.hav_sample.argtypes = [vp, vp, i64, i64, P(hav_params), vp, vp]
         L.hav_sample.restype = C.c_int
+        L.hav_ball_query.argtypes = [vp, vp, i64, vp, i64, C.c_float, i32, vp, vp, vp]
+        L.hav_ball_query.restype = C.c_int
         L.hav_spacing.argtypes = [vp, vp, i64, vp, i64, vp, vp]
         L.hav_spacing.restype = C.c_int
         L.hav_sample_xyz.argtypes = [vp, vp, i64, i64, P(hav_params), vp, vp, vp]
@@ -349,6 +351,24 @@ def hav_spacing(ctx: Context, points, idx, out=None, stream=None):
                             C.c_void_p(idx.data_ptr()), m, C.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(st, "hav_spacing")
     return out
+
+
+def hav_ball_query(ctx: Context, points, centres, radius: float, nsample: int, out=None, xyz=True, stream=None):
+    """Grouping around centres (indices into points): (m, nsample) int32 indices and,
+    if xyz, (m, nsample, 3) float32 offsets p_k - c_j (else None)."""
+    import torch
+    points = _points(points)
+    centres = centres.to(dtype=torch.int32, device=points.device).contiguous()
+    m = centres.shape[0]
+    if out is None:
+        out = torch.empty((m, int(nsample)), dtype=torch.int32, device=points.device)
+    offs = torch.empty((m, int(nsample), 3), dtype=torch.float32, device=points.device) if xyz else None
+    st = load().hav_ball_query(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0],
+                               C.c_void_p(centres.data_ptr()), m, float(np.float32(radius)), int(nsample),
+                               C.c_void_p(out.data_ptr()), C.c_void_p(offs.data_ptr() if xyz else None),
+                               _stream_handle(stream))
+    _check(st, "hav_ball_query")
+    return out, offs
 
 
 def coverage(points, idx, chunk: int = 8192) -> float:

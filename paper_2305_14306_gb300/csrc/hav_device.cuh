@@ -358,6 +358,55 @@ __device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* scratch /* >
 // e * nblocks, so no block has to act as the last arriver.  Returns false
 // (for the whole block) when this or another block gave up; the caller then
 // leaves the kernel.
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier that also sums one count over the blocks.  Each block adds
+// 2^48 + add to `word`; the barrier is complete when the arrival field (bits
+// 48..63, mod 2^16) reaches uses * nblocks.  Between two uses of the same
+// word every block has passed a barrier on the other word, so no block adds
+// to it again before all have read it: the change of the low 48 bits since
+// this block's last reading is exactly this barrier's sum.  The caller keeps
+// the low field below 2^48.  Bounded like grid_sync_impl.
+__device__ inline bool fused_sync_impl(unsigned long long* word, GlobalHdr* gh, unsigned nblocks, unsigned* uses,
+                                       unsigned long long* last, unsigned long long add,
+                                       unsigned long long* delta, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        *uses += 1u;
+        const unsigned target = (*uses * nblocks) & 0xffffu;
+        const unsigned long long inc = (1ull << 48) | add;
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(word), "l"(inc) : "memory");
+        const unsigned long long t0 = globaltimer();
+        unsigned long long v = 0;
+        for (unsigned it = 0;; ++it) {
+            v = ld_acquire64(word);
+            if ((static_cast<unsigned>(v >> 48) & 0xffffu) == target) break;
+            if ((it & 31) == 31) {
+                if (ld_volatile(&gh->abort) || it > kSpinIters || globaltimer() - t0 > kSpinNs) {
+                    fail = 1;
+                    break;
+                }
+            }
+            if (it > 64) __nanosleep(32);
+        }
+        if (fail) {
+            atomicExch(&gh->abort, 1);
+            atomicCAS(&gh->status, 0, static_cast<int>(HAV_ERR_TIMEOUT));
+        }
+        const unsigned long long c = v & ((1ull << 48) - 1ull);
+        *delta = c - *last;
+        *last = c;
+        *s_flag = fail | ld_volatile(&gh->abort);
+    }
+    __syncthreads();
+    return *s_flag == 0;
+}
+
 __device__ inline bool grid_sync_impl(Barrier* bar, GlobalHdr* gh, unsigned nblocks, unsigned* epoch,
                                       int* s_flag) {
     __syncthreads();

@@ -44,6 +44,10 @@ struct alignas(128) Barrier {
     unsigned int pad0[31];
     unsigned int gen;
     unsigned int pad1[31];
+    // counting barriers of single-cloud passes, alternating by pass parity:
+    // arrivals (mod 2^16) in bits 48..63, summed counts in bits 0..47
+    unsigned long long fused[2];
+    unsigned long long pad2[14];
 };
 
 struct GlobalHdr {

@@ -111,6 +111,12 @@ struct Smem {
     int any;
     int items_total;
     int chunk;
+    // counting barrier of single-cloud passes
+    unsigned fused_uses[2];
+    unsigned long long fused_last[2];
+    unsigned long long fused_delta;
+    unsigned long long pass_cnt;
+    int pass_err;
     long long n_level;
     long long m_total;
 };
@@ -141,6 +147,25 @@ struct Dev {
 };
 
 // Barrier plus, when phase timing is on, a (time, tag) record from block 0.
+// A pass of one cloud with one candidate: the pass count travels with the
+// barrier (fused_sync_impl).  A block that met an out-of-range key adds
+// kFusedErr, which no count reaches (counts stay below 2^31); it happens at
+// most once per call, as the search of the cloud stops there, so the low
+// field stays below 2^48 (at most 640 passes per word, each below 2^31).
+constexpr unsigned long long kFusedErr = 1ull << 36;
+
+__device__ __forceinline__ bool fused_sync(Dev& d, unsigned nblocks, Smem& st, int par, unsigned long long add,
+                                           unsigned tag) {
+    const bool ok = fused_sync_impl(&d.bar->fused[par], d.gh, nblocks, &st.fused_uses[par], &st.fused_last[par],
+                                    add, &st.fused_delta, &st.flag);
+    if (d.ptimes && blockIdx.x == 0 && threadIdx.x == 0 && st.ntimes < d.ptimes_cap) {
+        d.ptimes[2 * st.ntimes] = globaltimer();
+        d.ptimes[2 * st.ntimes + 1] = tag;
+        st.ntimes += 1;
+    }
+    return ok;
+}
+
 __device__ __forceinline__ bool grid_sync(Dev& d, unsigned nblocks, Smem& st, unsigned tag) {
     const bool ok = grid_sync_impl(d.bar, d.gh, nblocks, &st.epoch, &st.flag);
     if (d.ptimes && blockIdx.x == 0 && threadIdx.x == 0 && st.ntimes < d.ptimes_cap) {
@@ -362,6 +387,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
     d.ptimes = P.ptimes;
     d.ptimes_cap = P.ptimes_cap;
     if (tid == 0) {
+        st.fused_uses[0] = st.fused_uses[1] = 0u;
+        st.fused_last[0] = st.fused_last[1] = 0ull;
         st.epoch = 0u;
         st.set_clean = 0;
         st.ntimes = 0;
@@ -599,8 +626,14 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             // subtree exactly as the sequential search does, so the sizes
             // evaluated on the path, their counts and the outcome are those of the
             // plain bisection; D = 1 is the plain bisection.
+            // one cloud, one candidate per pass: the count rides on the barrier
+            const bool fused = (S == 1 && ncand == 1);
             for (int p = 0; p < P.t_max; ++p) {
                 const int searching = (tid < S && (st.flags[tid] & F_SEARCH)) ? 1 : 0;
+                if (tid == 0) {
+                    st.pass_cnt = 0ull;
+                    st.pass_err = 0;
+                }
                 if (!__syncthreads_or(searching)) break;
                 const int X = p & 1, Y = X ^ 1;
 
@@ -749,24 +782,37 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     if (rbits) atomicOr(&st.rbits, rbits);
                     if (bad) seg_error(d, s, bad);
                     __syncthreads();
-                    if (tid < ncand && st.dcnt[X][li][tid])
-                        atomicAdd(&ls[s].count[p % 3][tid], static_cast<unsigned>(st.dcnt[X][li][tid]));
-                    if (tid == 0 && st.rbits) atomicOr(&ls[s].cerr[p % 3], st.rbits);
-                }
-                if (p >= 1 && blockIdx.x == 0)
-                    for (int k = tid; k < S * (kMaxCand + 1); k += kThreads) {
-                        const int s = k / (kMaxCand + 1), c = k % (kMaxCand + 1);
-                        if (c < kMaxCand) ls[s].count[(p + 1) % 3][c] = 0u;
-                        else ls[s].cerr[(p + 1) % 3] = 0u;
+                    if (fused) {
+                        if (tid == 0) {
+                            st.pass_cnt += static_cast<unsigned long long>(st.dcnt[X][li][0]);
+                            if (st.rbits) st.pass_err = 1;
+                        }
+                    } else {
+                        if (tid < ncand && st.dcnt[X][li][tid])
+                            atomicAdd(&ls[s].count[p % 3][tid], static_cast<unsigned>(st.dcnt[X][li][tid]));
+                        if (tid == 0 && st.rbits) atomicOr(&ls[s].cerr[p % 3], st.rbits);
                     }
-                if (!grid_sync(d, nb, st, TAG(2, j, l, p))) return;
+                }
+                if (fused) {
+                    const unsigned long long add = st.pass_cnt + (st.pass_err ? kFusedErr : 0ull);
+                    if (!fused_sync(d, nb, st, X, add, TAG(2, j, l, p))) return;
+                } else {
+                    if (p >= 1 && blockIdx.x == 0)
+                        for (int k = tid; k < S * (kMaxCand + 1); k += kThreads) {
+                            const int s = k / (kMaxCand + 1), c = k % (kMaxCand + 1);
+                            if (c < kMaxCand) ls[s].count[(p + 1) % 3][c] = 0u;
+                            else ls[s].cerr[(p + 1) % 3] = 0u;
+                        }
+                    if (!grid_sync(d, nb, st, TAG(2, j, l, p))) return;
+                }
 
                 // decide (identically in every block): walk the evaluated subtree
                 if (searching) {
                     float lo = st.lo[tid], hi = st.hi[tid];
                     int node = 0;
                     int t = st.iters[tid];
-                    const unsigned cerr = ld_volatile_u(&ls[tid].cerr[p % 3]);
+                    const unsigned cerr = fused ? (st.fused_delta >= kFusedErr ? 1u : 0u)
+                                                : ld_volatile_u(&ls[tid].cerr[p % 3]);
                     hav_layer_trace* tr = d.tr + (static_cast<long long>(j) * S + tid) * kMaxLayers + l;
                     while (node < ncand && t < P.t_max) {
                         const float sv = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
@@ -777,7 +823,9 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             st.flags[tid] = 0;
                             break;
                         }
-                        const long long K = ld_volatile(reinterpret_cast<const int*>(&ls[tid].count[p % 3][node]));
+                        const long long K =
+                            fused ? static_cast<long long>(st.fused_delta)
+                                  : ld_volatile(reinterpret_cast<const int*>(&ls[tid].count[p % 3][node]));
                         if (blockIdx.x == 0) {
                             tr->s[t] = sv;
                             tr->K[t] = K;

@@ -148,10 +148,16 @@ typedef struct {
                                 <= [2] <= 2^31 */
     int32_t chunk_min;       /* smallest work item in points, 1..65536 */
     int32_t nblocks;         /* as in hav_context_set_blocks (0: all co-resident) */
+    int32_t small_points;    /* levels whose every segment has at most this many
+                                points (0..32768; 0: none, the default) run on
+                                thread-block clusters, one cluster of 8 SMs per
+                                segment, the voxel table in distributed shared
+                                memory (same results; plain bisection) */
+    int32_t reserved;        /* 0 */
 } hav_tuning;
 
 /* Copy the context's tuning into *out (the defaults after creation:
- * {0, 16384, 262144}, 64, the co-resident maximum). */
+ * {0, 16384, 262144}, 64, the co-resident maximum, 0, 0). */
 hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out);
 
 /* Replace the context's tuning.  HAV_ERR_INVALID (and no change) on a value

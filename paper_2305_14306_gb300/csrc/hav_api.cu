@@ -17,6 +17,8 @@ struct hav_ctx {
     int max_blocks;
     int chunk_min;
     int64_t spec_n[3];
+    int small_nc;      // clusters of the small-level kernel that fit at once (0: none)
+    int small_points;  // largest level run on clusters (0: never)
     int fps_nblocks;
     havk::Layout lay;
     unsigned char* ws;
@@ -105,6 +107,12 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
     c->max_blocks = nb;
     c->fps_nblocks = fnb;
     c->chunk_min = havk::kChunkMin;
+    {
+        const int snc = havk::small_clusters(dev);
+        cudaGetLastError();
+        c->small_nc = snc > 0 ? snc : 0;
+        c->small_points = 0;  // measured no faster than the grid kernel on GB300: opt-in
+    }
     c->spec_n[0] = havk::kSpecN4;
     c->spec_n[1] = havk::kSpecN3;
     c->spec_n[2] = havk::kSpecN2;
@@ -134,6 +142,8 @@ hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out) {
     for (int k = 0; k < 3; ++k) out->spec_points[k] = ctx->spec_n[k];
     out->chunk_min = ctx->chunk_min;
     out->nblocks = ctx->nblocks;
+    out->small_points = ctx->small_points;
+    out->reserved = 0;
     return HAV_OK;
 }
 
@@ -144,6 +154,9 @@ hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t) {
     if (t->spec_points[0] > t->spec_points[1] || t->spec_points[1] > t->spec_points[2]) return HAV_ERR_INVALID;
     if (t->chunk_min < 1 || t->chunk_min > 65536) return HAV_ERR_INVALID;
     if (t->nblocks < 0 || t->nblocks > ctx->max_blocks) return HAV_ERR_INVALID;
+    if (t->small_points < 0 || t->small_points > havk::kSmallMax || t->reserved != 0) return HAV_ERR_INVALID;
+    if (t->small_points > 0 && ctx->small_nc == 0) return HAV_ERR_INVALID;  // no cluster launch on this device
+    ctx->small_points = t->small_points;
     for (int k = 0; k < 3; ++k) ctx->spec_n[k] = t->spec_points[k];
     ctx->chunk_min = t->chunk_min;
     ctx->nblocks = t->nblocks == 0 ? ctx->max_blocks : t->nblocks;
@@ -235,8 +248,34 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
                cudaMemsetAsync(plan->ptimes, 0, sizeof(unsigned long long) * 2 * havk::kPhaseTimes, strm) !=
                    cudaSuccess) {
         ret = HAV_ERR_CUDA;
-    } else if (any_m > 0 && havk::launch_chain(*plan, strm) != 0) {
-        ret = HAV_ERR_CUDA;
+    } else if (any_m > 0) {
+        // levels from j0 on, where every segment has at most small_points points,
+        // run on thread-block clusters; the phase timer stays with the grid kernel
+        int j0 = num_levels;
+        if (ctx->small_points > 0 && !(params->flags & HAV_FLAG_PHASE_TIMES)) {
+            for (int j = 0; j < num_levels && j0 == num_levels; ++j) {
+                int64_t mx = 0;
+                for (int s = 0; s < num_segments; ++s) {
+                    const int64_t nj = (j == 0) ? seg_offsets[s + 1] - seg_offsets[s]
+                                                : seg_m[static_cast<int64_t>(j - 1) * num_segments + s];
+                    if (nj > mx) mx = nj;
+                }
+                if (mx <= ctx->small_points) j0 = j;
+            }
+        }
+        if (j0 > 0) {
+            plan->L = j0;
+            plan->keep_orig = (j0 < num_levels) ? 1 : 0;
+            if (havk::launch_chain(*plan, strm) != 0) ret = HAV_ERR_CUDA;
+            plan->L = num_levels;
+            plan->keep_orig = 0;
+        }
+        if (ret == HAV_OK && j0 < num_levels) {
+            int nc = plan->nblocks / 8;
+            if (nc > ctx->small_nc) nc = ctx->small_nc;
+            if (nc < 1) nc = 1;
+            if (havk::launch_small(*plan, j0, nc, strm) != 0) ret = HAV_ERR_CUDA;
+        }
     }
     delete plan;
     return ret;

@@ -33,6 +33,7 @@ constexpr int64_t kSpecN4 = 0;
 constexpr int64_t kSpecN3 = 16384;
 constexpr int64_t kSpecN2 = 262144;
 constexpr int kChunkMin = 64;              // default smallest work item (points)
+constexpr int kSmallMax = 32768;           // largest level the cluster kernel takes (points)
 constexpr int kLocalItems = 8;             // work items one block can own in a level
 
 constexpr unsigned long long kEmptyKey = ~0ull;  // valid keys use 63 bits
@@ -165,6 +166,8 @@ struct Plan {
     int32_t select;              // HAV_SELECT_*
     uint32_t seed;               // draws of HAV_SELECT_RANDOM
     float fixed_s;               // > 0: fixed voxel size, no search
+    int32_t keep_orig;           // write the last level's original indices (a cluster launch follows)
+    int32_t pad3;
     int64_t off0[kMaxSegments + 1];       // level-0 segment offsets
     int32_t m[kMaxLevels][kMaxSegments];  // budgets per level and segment
 };
@@ -186,6 +189,10 @@ int launch_chain(const Plan& plan, cudaStream_t stream);
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
                  unsigned char* ws, const Layout& lay, int64_t* K, cudaStream_t stream);
 int fps_coresident_blocks(int device);
+// Small levels on thread-block clusters (hav_small.cu): clusters that fit at
+// once (<= 0: none), and a launch of levels [first_level, plan.L).
+int small_clusters(int device);
+int launch_small(const Plan& plan, int first_level, int nclusters, cudaStream_t stream);
 // Grouping around centres (hav_group.cu).
 int launch_ball_query(const float* points, long long n, const int32_t* centres, long long m, float radius,
                       int nsample, int32_t* out_idx, float* out_xyz, unsigned char* ws, const Layout& lay,

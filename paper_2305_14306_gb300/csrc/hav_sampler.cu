@@ -1279,7 +1279,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     const int s = find_seg(st.off, S, g);
                     const int32_t oi = orig_in ? orig_in[g] : static_cast<int32_t>(g - st.off[s]);
                     out[pos] = oi;
-                    if (!last_level) orig_out[pos] = oi;
+                    if (!last_level || P.keep_orig) orig_out[pos] = oi;
                     ++pos;
                 }
             }

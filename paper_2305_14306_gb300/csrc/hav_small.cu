@@ -1,0 +1,544 @@
+// Small levels on thread-block clusters.
+//
+// The same sampler as hav_chain_kernel (Sections 3.2-3.4 and Eq. 3, with the
+// same readings), for levels of at most kSmallMax points: one cluster of kQ
+// CTAs per segment, the voxel table spread over the CTAs' shared memory and
+// reached through distributed shared memory, phases separated by the cluster
+// barrier.  An exchange between SMs then costs a few hundred cycles instead
+// of an L2 round trip across the chip, and a phase ends with a hardware
+// cluster barrier instead of a grid barrier: on levels of tens of thousands
+// of points the grid-wide kernel pays for that latency, not for work.  The
+// search is the plain bisection (one size per pass), so every evaluated size
+// and count is the paper's.
+//
+// Inside a cluster, CTA r holds the level's points [n r / kQ, n (r + 1) / kQ)
+// (level indices, ascending) in shared memory with their taken flags.  The
+// voxel table has max(nextpow2(2 n), 64 kQ) slots: key k lives in CTA
+// owner(k) (the top bits of slot_mix(k)), at the next bits inside that CTA's
+// part, with linear probing inside the part.  A level's points are read from
+// the original cloud through the ascending original indices of the level
+// (orig), so a chain can start here at any level.
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "hav.h"
+#include "hav_device.cuh"
+#include "hav_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace havk {
+namespace {
+
+constexpr int kQ = 8;  // CTAs per cluster
+constexpr int kQLog2 = 3;
+constexpr int kST = 1024;  // threads per CTA
+constexpr int kPtsPerCta = kSmallMax / kQ;
+constexpr int kPartMax = 2 * kSmallMax / kQ;  // table slots per CTA at most
+constexpr size_t kSmallDyn = static_cast<size_t>(kPartMax) * 16 + static_cast<size_t>(kPtsPerCta) * 16 +
+                             static_cast<size_t>(kPtsPerCta) + 4 * kHistBins;
+static_assert(kHistBins == kST, "one histogram bin per thread");
+
+struct SmallSmem {
+    // CTA 0's copy is the cluster's: written by every CTA through distributed shared memory
+    unsigned long long cnt[3];  // pass counts, three-way rotation
+    unsigned perr[3];           // pass errors (1: range, 2: table full), same rotation
+    unsigned long long kstar;   // occupied voxels at s*
+    unsigned errbits;           // selection errors
+    unsigned ncand;             // boundary-bin candidates appended
+    uint32_t box[6];            // bounding box codes of the level
+    int nonfinite;
+    int part_cnt[kQ];  // per-CTA counts for prefixes (shortfall, compaction)
+    // this CTA's
+    float mn[3], s_hi;
+    int cut_bin, cut_below;
+    unsigned long long red_u[32];
+    int red_i[32];
+    float redf[6][32];
+    int flag;
+};
+
+__device__ __forceinline__ int part_start(long long n, int r) { return static_cast<int>((n * r) / kQ); }
+
+__device__ __forceinline__ int point_owner(long long n, int g) {
+    int r = (n > 0) ? static_cast<int>((static_cast<long long>(g) * kQ) / n) : 0;
+    if (r > kQ - 1) r = kQ - 1;
+    while (r > 0 && part_start(n, r) > g) --r;
+    while (r + 1 < kQ && part_start(n, r + 1) <= g) ++r;
+    return r;
+}
+
+// Insert `key` into the cluster table: the slot inside the owner's part, or
+// -1 when the part is full; *fresh when this call inserted it.
+__device__ __forceinline__ int dsm_insert(cg::cluster_group& cl, unsigned long long* keys_local, int part_log2,
+                                          unsigned long long key, int* owner_out, bool* fresh) {
+    const unsigned long long h = slot_mix(key);
+    const int owner = static_cast<int>(h >> (64 - kQLog2));
+    unsigned long long* part = cl.map_shared_rank(keys_local, owner);
+    const unsigned mask = (1u << part_log2) - 1u;
+    unsigned slot = static_cast<unsigned>(h >> (64 - kQLog2 - part_log2)) & mask;
+    *owner_out = owner;
+    *fresh = false;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        const unsigned long long prev = atomicCAS(part + slot, kEmptyKey, key);
+        if (prev == kEmptyKey) {
+            *fresh = true;
+            return static_cast<int>(slot);
+        }
+        if (prev == key) return static_cast<int>(slot);
+        slot = (slot + 1) & mask;
+    }
+    return -1;
+}
+
+// 64-bit minimum in another CTA's shared memory with compare-and-swap (the
+// operation the table inserts use): every failed attempt saw a smaller
+// value, so the loop ends after at most as many attempts as writers.
+__device__ __forceinline__ void dsm_min(unsigned long long* p, unsigned long long v) {
+    unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(p);
+    while (v < cur) {
+        const unsigned long long prev = atomicCAS(p, cur, v);
+        if (prev == cur) break;
+        cur = prev;
+    }
+}
+
+__device__ __forceinline__ unsigned long long block_sum_ull(unsigned long long v, unsigned long long* scratch) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    for (int k = 0; k < kST / 32; ++k) t += scratch[k];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ void seg_fail(SegHdr* sh, GlobalHdr* gh, int seg, int code) {
+    atomicCAS(&sh[seg].status, 0, code);
+    atomicCAS(&gh->status, 0, code);
+}
+
+// Levels [first_level, P.L) of every segment; level first_level > 0 reads its
+// input through orig[(first_level - 1) & 1].
+__global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
+    hav_small_kernel(const __grid_constant__ Plan P, int first_level) {
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ SmallSmem sm;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(dyn);
+    unsigned long long* vals = keys + kPartMax;
+    float4* pts = reinterpret_cast<float4*>(vals + kPartMax);  // x, y, z, original index
+    unsigned char* taken = reinterpret_cast<unsigned char*>(pts + kPtsPerCta);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(taken + kPtsPerCta);
+
+    const int tid = threadIdx.x;
+    const int rank = static_cast<int>(cl.block_rank());
+    const int cluster_id = blockIdx.x / kQ;
+    const int nclusters = gridDim.x / kQ;
+    SmallSmem* sm0 = cl.map_shared_rank(&sm, 0);
+    unsigned char* ws = P.ws;
+    SegHdr* sh = reinterpret_cast<SegHdr*>(ws + P.lay.seghdr);
+    GlobalHdr* gh = reinterpret_cast<GlobalHdr*>(ws + P.lay.ghdr);
+    hav_layer_trace* trace = reinterpret_cast<hav_layer_trace*>(ws + P.lay.trace);
+    int32_t* orig[2] = {reinterpret_cast<int32_t*>(ws + P.lay.orig[0]), reinterpret_cast<int32_t*>(ws + P.lay.orig[1])};
+    Cand* cand_all = reinterpret_cast<Cand*>(ws + P.lay.cand);
+    const int S = P.S;
+    const bool write_tr = (rank == 0 && tid == 0);
+
+    for (int seg = cluster_id; seg < S; seg += nclusters) {
+        // an error from earlier levels (another kernel) carries on: first m points
+        int err = ld_volatile(&sh[seg].status);
+        for (int j = first_level; j < P.L; ++j) {
+            const long long n = (j == 0) ? (P.off0[seg + 1] - P.off0[seg]) : P.m[j - 1][seg];
+            const long long m = P.m[j][seg];
+            long long obase = 0, ibase = 0;  // this segment's first output / input position in the level arrays
+            for (int s2 = 0; s2 < seg; ++s2) {
+                obase += P.m[j][s2];
+                ibase += (j == 0) ? 0 : P.m[j - 1][s2];
+            }
+            const int a = part_start(n, rank), b = part_start(n, rank + 1);
+            const int L = b - a;
+
+            // --------------------------------------------- points and bbox
+            if (tid == 0) {
+                for (int k = 0; k < 3; ++k) {
+                    sm.box[k] = 0u;
+                    sm.box[3 + k] = 0u;
+                }
+                sm.nonfinite = 0;
+            }
+            cl.sync();
+            float mnv[3] = {INFINITY, INFINITY, INFINITY}, mxv[3] = {-INFINITY, -INFINITY, -INFINITY};
+            int bad = 0;
+            for (int i = tid; i < L; i += kST) {
+                const int o = (j == 0) ? (a + i) : orig[(j - 1) & 1][ibase + a + i];
+                const float* p = P.points + 3 * (P.off0[seg] + o);
+                const float4 q = make_float4(p[0], p[1], p[2], __int_as_float(o));
+                pts[i] = q;
+                taken[i] = 0;
+                const float c3[3] = {q.x, q.y, q.z};
+                for (int k = 0; k < 3; ++k) {
+                    if (!isfinite(c3[k])) bad = 1;
+                    mnv[k] = fminf(mnv[k], c3[k]);
+                    mxv[k] = fmaxf(mxv[k], c3[k]);
+                }
+            }
+            for (int k = 0; k < 3; ++k)
+                for (int o = 16; o > 0; o >>= 1) {
+                    mnv[k] = fminf(mnv[k], __shfl_xor_sync(0xffffffffu, mnv[k], o));
+                    mxv[k] = fmaxf(mxv[k], __shfl_xor_sync(0xffffffffu, mxv[k], o));
+                }
+            if ((tid & 31) == 0)
+                for (int k = 0; k < 3; ++k) {
+                    sm.redf[k][tid >> 5] = mnv[k];
+                    sm.redf[3 + k][tid >> 5] = mxv[k];
+                }
+            bad = __syncthreads_or(bad);
+            if (tid < 6) {
+                float r = sm.redf[tid][0];
+                for (int w = 1; w < kST / 32; ++w) r = (tid < 3) ? fminf(r, sm.redf[tid][w]) : fmaxf(r, sm.redf[tid][w]);
+                if (isfinite(r)) atomicMax(&sm0->box[tid], (tid < 3) ? ~enc_f(r) : enc_f(r));
+            }
+            if (tid == 0 && bad) atomicExch(&sm0->nonfinite, 1);
+            cl.sync();
+            // the bracket (0, s_hi] of Section 3.3 from CTA 0's box, in every CTA
+            if (tid == 0) {
+                const int nf = sm0->nonfinite;
+                float s_hi = 0.0f;
+                for (int k = 0; k < 3; ++k) {
+                    float lo = dec_f(~sm0->box[k]), hi = dec_f(sm0->box[3 + k]);
+                    if (n == 0 || nf || err) lo = hi = 0.0f;
+                    sm.mn[k] = lo;
+                    if (j == 0 && rank == 0) {
+                        sh[seg].bbox[0][k] = sm0->box[k];
+                        sh[seg].bbox[0][3 + k] = sm0->box[3 + k];
+                    }
+                    s_hi = fmaxf(s_hi, __fdiv_rn(__fsub_rn(hi, lo), P.aspect[k]));
+                }
+                if (s_hi == 0.0f) s_hi = 1.0f;
+                sm.s_hi = s_hi;
+                sm.flag = nf;
+            }
+            __syncthreads();
+            if (!err && sm.flag) {
+                err = HAV_ERR_NONFINITE;
+                if (write_tr) seg_fail(sh, gh, seg, err);
+            }
+            if (!err && !isfinite(sm.s_hi)) {
+                err = HAV_ERR_RANGE;
+                if (write_tr) seg_fail(sh, gh, seg, err);
+            }
+
+            int part_log2 = kMinCapLog2;
+            while ((1ll << part_log2) < 2 * n) ++part_log2;
+            part_log2 -= kQLog2;
+            if (part_log2 < kMinCapLog2) part_log2 = kMinCapLog2;
+            const int part = 1 << part_log2;
+
+            // ----------------------------------------------------- layers
+            long long taken_before = 0;
+            unsigned pass_no = 0;
+            for (int l = 0; l < P.layers; ++l) {
+                const long long ml = layer_budget(m, P.layers, P.ratio, l);
+                const long long kmax = ml + ml * P.sigma_num / P.sigma_den;
+                hav_layer_trace* tr = trace + (static_cast<long long>(j) * S + seg) * kMaxLayers + l;
+                if (write_tr) {
+                    tr->m_l = ml;
+                    tr->k_max = kmax;
+                    tr->k_star = 0;
+                    tr->n_in = n - taken_before;
+                    tr->iters = 0;
+                    tr->accepted = 0;
+                    tr->s_hi = sm.s_hi;
+                    tr->s_star = 0.0f;
+                }
+                taken_before += ml;
+                if (ml == 0 || err) continue;
+                const bool fixed = P.fixed_s > 0.0f;
+                float lo = 0.0f, hi = sm.s_hi;
+                float s_star = fixed ? P.fixed_s : sm.s_hi;
+                bool accepted = false;
+                const int steps = fixed ? 0 : P.t_max;
+
+                // Section 3.3 bisection, one size per pass
+                for (int t = 0; t < steps; ++t) {
+                    const float sv = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+                    Grid G;
+                    const bool gok = make_grid(sv, P.aspect, sm.mn, &G);
+                    for (int k = tid; k < part; k += kST) keys[k] = kEmptyKey;
+                    // slot pass_no % 3 was last read three passes ago
+                    if (rank == 0 && tid == 0) {
+                        sm.cnt[pass_no % 3] = 0ull;
+                        sm.perr[pass_no % 3] = 0u;
+                    }
+                    cl.sync();
+                    unsigned long long local = 0;
+                    unsigned ebits = gok ? 0u : 1u;
+                    if (gok) {
+                        for (int i = tid; i < L; i += kST) {
+                            if (taken[i]) continue;
+                            const float4 q = pts[i];
+                            const float p3[3] = {q.x, q.y, q.z};
+                            unsigned long long key;
+                            float f[3];
+                            if (!cell_key(p3, G, &key, f)) {
+                                ebits |= 1u;
+                                continue;
+                            }
+                            int owner;
+                            bool fr;
+                            if (dsm_insert(cl, keys, part_log2, key, &owner, &fr) < 0) ebits |= 2u;
+                            else if (fr) ++local;
+                        }
+                    }
+                    const unsigned long long tot = block_sum_ull(local, sm.red_u);
+                    const unsigned e1 = __syncthreads_or(ebits & 1u) ? 1u : 0u;
+                    const unsigned e2 = __syncthreads_or(ebits & 2u) ? 2u : 0u;
+                    if (tid == 0) {
+                        if (tot) atomicAdd(&sm0->cnt[pass_no % 3], tot);
+                        if (e1 | e2) atomicOr(&sm0->perr[pass_no % 3], e1 | e2);
+                    }
+                    cl.sync();
+                    const long long K = static_cast<long long>(sm0->cnt[pass_no % 3]);
+                    const unsigned eb = sm0->perr[pass_no % 3];
+                    ++pass_no;
+                    if (write_tr) {
+                        tr->s[t] = sv;
+                        tr->K[t] = K;
+                        tr->iters = t + 1;
+                    }
+                    if (eb) {
+                        err = (eb & 1u) ? HAV_ERR_RANGE : HAV_ERR_TABLE_FULL;
+                        if (write_tr) seg_fail(sh, gh, seg, err);
+                        break;
+                    }
+                    if (K > kmax) {
+                        lo = sv;
+                    } else if (K < ml) {
+                        hi = sv;
+                    } else {
+                        s_star = sv;
+                        accepted = true;
+                        break;
+                    }
+                }
+                if (err) continue;
+                if (!accepted && !fixed && P.t_max > 0) s_star = (lo > 0.0f) ? lo : hi;
+                Grid G;
+                if (!make_grid(s_star, P.aspect, sm.mn, &G)) {
+                    err = HAV_ERR_RANGE;
+                    if (write_tr) seg_fail(sh, gh, seg, err);
+                    continue;
+                }
+
+                // ------------------------------ Section 3.2 selection at s*
+                for (int k = tid; k < part; k += kST) {
+                    keys[k] = kEmptyKey;
+                    vals[k] = kEmptyVal;
+                }
+                hist[tid] = 0u;
+                if (rank == 0 && tid == 0) {
+                    sm.kstar = 0ull;
+                    sm.errbits = 0u;
+                    sm.ncand = 0u;
+                }
+                cl.sync();
+                {
+                    unsigned long long local = 0;
+                    unsigned ebits = 0;
+                    uint32_t* hist0 = cl.map_shared_rank(hist, 0);
+                    for (int i = tid; i < L; i += kST) {
+                        if (taken[i]) continue;
+                        const float4 q = pts[i];
+                        const float p3[3] = {q.x, q.y, q.z};
+                        unsigned long long key;
+                        float f[3];
+                        if (!cell_key(p3, G, &key, f)) {
+                            ebits |= 1u;
+                            continue;
+                        }
+                        const int g = a + i;  // the point's level index
+                        const unsigned word =
+                            (P.select == HAV_SELECT_RANDOM)
+                                ? static_cast<unsigned>(random_draw(P.seed, static_cast<unsigned long long>(g)) >> 32)
+                                : __float_as_uint(centre_d2(p3, G, f));
+                        const unsigned long long packed =
+                            (static_cast<unsigned long long>(word) << 32) | static_cast<unsigned>(g);
+                        int owner;
+                        bool fr;
+                        const int slot = dsm_insert(cl, keys, part_log2, key, &owner, &fr);
+                        if (slot < 0) {
+                            ebits |= 2u;
+                            continue;
+                        }
+                        dsm_min(cl.map_shared_rank(vals, owner) + slot, packed);
+                        if (fr) {
+                            ++local;
+                            atomicAdd(hist0 + static_cast<int>(priority(key) >> (64 - kHistBits)), 1u);
+                        }
+                    }
+                    const unsigned long long tot = block_sum_ull(local, sm.red_u);
+                    const unsigned e1 = __syncthreads_or(ebits & 1u) ? 1u : 0u;
+                    const unsigned e2 = __syncthreads_or(ebits & 2u) ? 2u : 0u;
+                    if (tid == 0) {
+                        if (tot) atomicAdd(&sm0->kstar, tot);
+                        if (e1 | e2) atomicOr(&sm0->errbits, e1 | e2);
+                    }
+                }
+                cl.sync();
+                const long long kstar = static_cast<long long>(sm0->kstar);
+                {
+                    const unsigned eb = sm0->errbits;
+                    if (write_tr) {
+                        tr->k_star = kstar;
+                        tr->accepted = accepted ? 1 : 0;
+                        tr->s_star = s_star;
+                    }
+                    if (eb) {
+                        err = (eb & 1u) ? HAV_ERR_RANGE : HAV_ERR_TABLE_FULL;
+                        if (write_tr) seg_fail(sh, gh, seg, err);
+                        continue;
+                    }
+                }
+
+                // ----------------------------------- cut-off and taken marks
+                const bool cut = kstar > ml;
+                Cand* cand = cand_all + 2 * P.off0[seg];  // room for 2 n entries of this segment
+                if (cut) {
+                    // boundary bin: smallest b with (voxels in bins <= b) >= m_l
+                    const int v = static_cast<int>(cl.map_shared_rank(hist, 0)[tid]);
+                    int total;
+                    const int before = block_excl_scan<int>(v, &total, sm.red_i);
+                    if (before < ml && before + v >= ml) {
+                        sm.cut_bin = tid;
+                        sm.cut_below = before;
+                    }
+                    __syncthreads();
+                }
+                for (int k = tid; k < part; k += kST) {
+                    const unsigned long long key = keys[k];
+                    if (key == kEmptyKey) continue;
+                    const int g = static_cast<int>(vals[k] & 0xffffffffull);
+                    bool take = !cut;
+                    if (cut) {
+                        const unsigned long long h = priority(key);
+                        const int hb = static_cast<int>(h >> (64 - kHistBits));
+                        if (hb < sm.cut_bin) {
+                            take = true;
+                        } else if (hb == sm.cut_bin) {
+                            const unsigned ci = atomicAdd(&sm0->ncand, 1u);
+                            if (ci < static_cast<unsigned>(2 * n)) {
+                                cand[ci].h = h;
+                                cand[ci].g = static_cast<uint32_t>(g);
+                            }
+                        }
+                    }
+                    if (take) {
+                        const int r = point_owner(n, g);
+                        cl.map_shared_rank(taken, r)[g - part_start(n, r)] = 1;
+                    }
+                }
+                cl.sync();
+                if (cut) {
+                    // the boundary bin's candidates ranked exactly; the r smallest priorities are taken
+                    const int c = static_cast<int>(sm0->ncand);
+                    const int r = static_cast<int>(ml) - sm.cut_below;
+                    for (int f = rank * kST + tid; f < c; f += kQ * kST) {
+                        const unsigned long long hf = cand[f].h;
+                        int rk = 0;
+                        for (int k = 0; k < c; ++k) rk += (cand[k].h < hf) ? 1 : 0;
+                        if (rk < r) {
+                            const int g = static_cast<int>(cand[f].g);
+                            const int owner = point_owner(n, g);
+                            cl.map_shared_rank(taken, owner)[g - part_start(n, owner)] = 1;
+                        }
+                    }
+                    cl.sync();
+                } else if (kstar < ml) {
+                    // shortfall: untaken points in ascending level index until m_l
+                    int cnt = 0;
+                    for (int i = tid; i < L; i += kST) cnt += taken[i] ? 0 : 1;
+                    int tot;
+                    block_excl_scan<int>(cnt, &tot, sm.red_i);
+                    if (tid == 0) sm0->part_cnt[rank] = tot;
+                    cl.sync();
+                    long long before = 0;
+                    for (int r2 = 0; r2 < rank; ++r2) before += sm0->part_cnt[r2];
+                    long long budget = (ml - kstar) - before;
+                    for (int i0 = 0; i0 < L && budget > 0; i0 += kST) {
+                        const int i = i0 + tid;
+                        const int free_pt = (i < L && !taken[i]) ? 1 : 0;
+                        int chunk;
+                        const int rk = block_excl_scan<int>(free_pt, &chunk, sm.red_i);
+                        if (free_pt && rk < budget) taken[i] = 1;
+                        budget -= chunk;
+                    }
+                    cl.sync();
+                }
+            }
+
+            // ----------------------------------------------------- compaction
+            // Segments in error take their first m points, as in the grid kernel.
+            {
+                int cnt = 0;
+                for (int i = tid; i < L; i += kST) cnt += (err ? (a + i < m) : (taken[i] != 0)) ? 1 : 0;
+                int tot;
+                block_excl_scan<int>(cnt, &tot, sm.red_i);
+                if (tid == 0) sm0->part_cnt[rank] = tot;
+                cl.sync();
+                long long pos = obase;
+                for (int r2 = 0; r2 < rank; ++r2) pos += sm0->part_cnt[r2];
+                int32_t* out = P.out[j];
+                int32_t* orig_out = orig[j & 1];
+                const bool more = (j + 1 < P.L) || P.keep_orig;
+                for (int i0 = 0; i0 < L; i0 += kST) {
+                    const int i = i0 + tid;
+                    const int keep = (i < L && (err ? (a + i < m) : (taken[i] != 0))) ? 1 : 0;
+                    int chunk;
+                    const int rk = block_excl_scan<int>(keep, &chunk, sm.red_i);
+                    if (keep) {
+                        if (pos + rk < obase + m) {
+                            const int o = __float_as_int(pts[i].w);
+                            out[pos + rk] = o;
+                            if (more) orig_out[pos + rk] = o;
+                        } else {
+                            seg_fail(sh, gh, seg, HAV_ERR_TABLE_FULL);  // cannot happen: every layer takes m_l
+                        }
+                    }
+                    pos += chunk;
+                }
+                cl.sync();  // the next level reads orig_out; part_cnt is reused
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int small_clusters(int device) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kQ * 64);
+    cfg.blockDim = dim3(kST);
+    cfg.dynamicSmemBytes = kSmallDyn;
+    if (cudaFuncSetAttribute(hav_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmallDyn)) != cudaSuccess)
+        return -1;
+    int nc = 0;
+    (void)device;
+    if (cudaOccupancyMaxActiveClusters(&nc, hav_small_kernel, &cfg) != cudaSuccess) return -1;
+    return nc;
+}
+
+int launch_small(const Plan& plan, int first_level, int nclusters, cudaStream_t stream) {
+    int nc = nclusters < plan.S ? nclusters : plan.S;
+    if (nc < 1) nc = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(kQ * nc));
+    cfg.blockDim = dim3(kST);
+    cfg.dynamicSmemBytes = kSmallDyn;
+    cfg.stream = stream;
+    return cudaLaunchKernelEx(&cfg, hav_small_kernel, plan, first_level) == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace havk

@@ -63,6 +63,8 @@ class hav_tuning(C.Structure):
         ("spec_points", C.c_int64 * 3),
         ("chunk_min", C.c_int32),
         ("nblocks", C.c_int32),
+        ("small_points", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 
@@ -200,9 +202,10 @@ class Context:
         """The context's launch-shape knobs (no knob changes a result)."""
         t = hav_tuning()
         _check(load().hav_context_get_tuning(self.handle, C.byref(t)), "hav_context_get_tuning")
-        return {"spec_points": list(t.spec_points), "chunk_min": t.chunk_min, "nblocks": t.nblocks}
+        return {"spec_points": list(t.spec_points), "chunk_min": t.chunk_min, "nblocks": t.nblocks,
+                "small_points": t.small_points}
 
-    def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None):
+    def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None, small_points=None):
         """Change some of the knobs; the others keep their values."""
         cur = self.get_tuning()
         t = hav_tuning()
@@ -211,6 +214,8 @@ class Context:
             t.spec_points[k] = int(sp[k])
         t.chunk_min = int(cur["chunk_min"] if chunk_min is None else chunk_min)
         t.nblocks = int(cur["nblocks"] if nblocks is None else nblocks)
+        t.small_points = int(cur["small_points"] if small_points is None else small_points)
+        t.reserved = 0
         _check(load().hav_context_set_tuning(self.handle, C.byref(t)), "hav_context_set_tuning")
 
     def close(self):

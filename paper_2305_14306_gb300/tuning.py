@@ -7,7 +7,8 @@ A context has three knobs (``hav_tuning`` in include/hav.h):
   is mostly fixed latency, so evaluating several sizes per pass means fewer
   grid-wide passes, until the work per candidate catches up);
 * the smallest work item, in points;
-* the number of blocks (one per SM).
+* the number of blocks (one per SM);
+* the level size up to which levels run on thread-block clusters (0: never).
 
 No knob changes a result.  The tuner therefore times the caller's own
 workload under a short list of settings (a coordinate search: first the
@@ -32,6 +33,7 @@ SPEC_CHOICES = (
     (0, 32768, 262144), (0, 65536, 524288), (8192, 16384, 262144), (32768, 131072, 262144),
 )
 CHUNK_MINS = (32, 64, 128, 256, 512, 1024)
+SMALL_POINTS = (0, 32768)
 
 
 def signature(seg_sizes, levels: int) -> str:
@@ -93,7 +95,8 @@ def autotune(ctx, run, key: str, gpu: str, cache: str | None = DEFAULT_CACHE, fo
     data = load_cache(cache) if cache else {}
     if not force and entry_key in data:
         t = data[entry_key]["tuning"]
-        ctx.set_tuning(spec_points=t["spec_points"], chunk_min=t["chunk_min"])
+        ctx.set_tuning(spec_points=t["spec_points"], chunk_min=t["chunk_min"],
+                       small_points=t.get("small_points", 0))
         return t, {"cached": True, **data[entry_key].get("report", {})}
 
     start = ctx.get_tuning()
@@ -120,8 +123,21 @@ def autotune(ctx, run, key: str, gpu: str, cache: str | None = DEFAULT_CACHE, fo
         ms = measure(best[1], ch)
         if ms < best[0]:
             best = (ms, best[1], ch)
-    tuning = {"spec_points": best[1], "chunk_min": best[2]}
-    ctx.set_tuning(spec_points=tuning["spec_points"], chunk_min=tuning["chunk_min"])
+    small = int(start.get("small_points", 0))
+    for sp in SMALL_POINTS:  # stage 3: small levels on clusters or not
+        if sp == small:
+            continue
+        try:
+            ctx.set_tuning(spec_points=best[1], chunk_min=best[2], small_points=sp)
+        except Exception:  # no cluster launch on this device
+            continue
+        ms = float(timer())
+        tried.append({"spec_points": list(best[1]), "chunk_min": int(best[2]), "small_points": sp, "ms": ms})
+        if ms < best[0]:
+            best = (ms, best[1], best[2])
+            small = sp
+    tuning = {"spec_points": best[1], "chunk_min": best[2], "small_points": small}
+    ctx.set_tuning(spec_points=tuning["spec_points"], chunk_min=tuning["chunk_min"], small_points=small)
     report = {"cached": False, "default_ms": default_ms, "tuned_ms": best[0], "tried": len(tried)}
     if cache:
         data = load_cache(cache)  # re-read: another process may have added entries

@@ -49,9 +49,9 @@ def test_struct_layouts_match_header(libhav, tmp_path):
     src = tmp_path / "s.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "hav.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(hav_params), sizeof(hav_layer_trace),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hav_params), sizeof(hav_layer_trace),'
         ' offsetof(hav_layer_trace, s), offsetof(hav_layer_trace, K), sizeof(hav_tuning),'
-        ' offsetof(hav_tuning, chunk_min)); return 0;}\n')
+        ' offsetof(hav_tuning, chunk_min), offsetof(hav_tuning, small_points)); return 0;}\n')
     exe = tmp_path / "s"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
@@ -63,6 +63,7 @@ def test_struct_layouts_match_header(libhav, tmp_path):
     assert int(out[3]) == hav.hav_layer_trace.K.offset
     assert int(out[4]) == ctypes.sizeof(hav.hav_tuning)
     assert int(out[5]) == hav.hav_tuning.chunk_min.offset
+    assert int(out[6]) == hav.hav_tuning.small_points.offset
 
 
 def test_params_default_and_status_strings(libhav):

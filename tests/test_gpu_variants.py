@@ -145,3 +145,39 @@ def test_variant_parameters_rejected(hv, ctx):
             hv.hav_sample(ctx, pts, 100, hv.params(**kw))
     with pytest.raises(hv.HavError):
         hv.hav_sample_xyz(ctx, pts, 100, hv.params(layers=2))
+
+
+# ------------------------------------------- small levels on thread-block clusters
+def test_cluster_levels_match_the_oracle(hv, oracle_mod):
+    # the same sampler on clusters (opt-in): identical indices and traces
+    c = hv.Context(1 << 20, 16)
+    try:
+        c.set_tuning(small_points=32768)
+        check_levels(hv, c, scenes.uniform_box(16384, seed=0), [4096])
+        check_levels(hv, c, scenes.uniform_box(16384, seed=1), [4096], layers=1, select=RA, seed=4)
+        check_levels(hv, c, scenes.lidar_min(16384, seed=2)[0], [16384, 4096, 1024, 512])
+        check_levels(hv, c, scenes.room_scene(1 << 18, seed=1), [1 << 16, 1 << 14, 1 << 12])  # split launch
+        check_levels(hv, c, scenes.uniform_box(16384, seed=3), [4096], layers=1, fixed_s=3.0)
+        for n, m in ((1, 1), (7, 3), (513, 100), (1000, 1000), (2049, 1)):
+            check_levels(hv, c, scenes.uniform_box(n, seed=n), [m])
+        sizes = [20000, 1, 0, 513, 7000, 4096]
+        clouds = [scenes.lidar_exact(n, 90 + i) if n >= 20000 else scenes.uniform_box(n, 90 + i)
+                  for i, n in enumerate(sizes)]
+        pts, offs = scenes.concat(clouds)
+        seg_m = np.array([[n // 4 for n in sizes], [n // 16 for n in sizes]], dtype=np.int64)
+        outs = hv.hav_sample_batched(c, dev(pts), offs, seg_m, hv.params())
+        st, _ = hv.hav_status_get(c, len(sizes))
+        assert st == 0
+        ora = G.oracle_many(clouds, [seg_m[:, s] for s in range(len(sizes))])
+        for j in range(2):
+            cut = np.concatenate([[0], np.cumsum(seg_m[j])])
+            got = outs[j].cpu().numpy()
+            for s in range(len(sizes)):
+                assert np.array_equal(got[cut[s]:cut[s + 1]], ora[s][0][j]), (j, s)
+        bad = scenes.uniform_box(3000, seed=1)
+        bad[5, 2] = np.nan
+        outs = hv.hav_sample_levels(c, dev(bad), [700], hv.params())
+        st, _ = hv.hav_status_get(c, 1)
+        assert st == hv.HAV_ERR_NONFINITE and outs[0].cpu().numpy().tolist() == list(range(700))
+    finally:
+        c.close()

@@ -6,18 +6,20 @@ from paper_2305_14306_gb300 import tuning
 
 class FakeCtx:
     def __init__(self):
-        self.t = {"spec_points": list(tuning.BASE_SPEC), "chunk_min": 64, "nblocks": 152}
+        self.t = {"spec_points": list(tuning.BASE_SPEC), "chunk_min": 64, "nblocks": 152, "small_points": 0}
         self.sets = 0
 
     def get_tuning(self):
         return dict(self.t, spec_points=list(self.t["spec_points"]))
 
-    def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None):
+    def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None, small_points=None):
         self.sets += 1
         if spec_points is not None:
             self.t["spec_points"] = list(spec_points)
         if chunk_min is not None:
             self.t["chunk_min"] = int(chunk_min)
+        if small_points is not None:
+            self.t["small_points"] = int(small_points)
 
 
 BEST_SPEC = [0, 8192, 131072]
@@ -33,7 +35,7 @@ def test_search_finds_the_minimum_and_caches(tmp_path):
     path = str(tmp_path / "c.json")
     ctx = FakeCtx()
     t, rep = tuning.autotune(ctx, None, "S64-N8388608-L2", "GB300", cache=path, timer=lambda: cost_of(ctx))
-    assert t == {"spec_points": BEST_SPEC, "chunk_min": 256}
+    assert t == {"spec_points": BEST_SPEC, "chunk_min": 256, "small_points": 0}
     assert ctx.t["spec_points"] == t["spec_points"] and ctx.t["chunk_min"] == 256
     assert rep["tuned_ms"] <= rep["default_ms"] and not rep["cached"]
     data = json.load(open(path))
@@ -52,8 +54,9 @@ def test_search_finds_the_minimum_and_caches(tmp_path):
 def test_default_kept_when_nothing_is_faster():
     ctx = FakeCtx()
     t, rep = tuning.autotune(ctx, None, "k", "g", cache=None, timer=lambda: 1.0)
-    assert t == {"spec_points": list(tuning.BASE_SPEC), "chunk_min": 64}
-    assert rep["tried"] == 1 + (len(tuning.SPEC_CHOICES) - 1) + (len(tuning.CHUNK_MINS) - 1)
+    assert t == {"spec_points": list(tuning.BASE_SPEC), "chunk_min": 64, "small_points": 0}
+    assert rep["tried"] == (1 + (len(tuning.SPEC_CHOICES) - 1) + (len(tuning.CHUNK_MINS) - 1)
+                            + (len(tuning.SMALL_POINTS) - 1))
 
 
 def test_signature_and_corrupt_cache(tmp_path):

@@ -292,7 +292,7 @@ const char* hav_status_string(hav_status s);
  * where an allocation and the synchronisation it can imply are not allowed).
  * It computes exactly what hav_sample computes for one cloud, one level.
  *
- * Scratch: a static __device__ array of 6 MiB inside libhav.so, enough for
+ * Scratch: a static __device__ array of 8 MiB inside libhav.so, enough for
  * one cloud of at most 32,768 points; every GPU that loads the library holds
  * it until the process exits.  n > 32,768 returns HAV_ERR_NOMEM and enqueues
  * nothing.  The first call on a device looks up the array's device address

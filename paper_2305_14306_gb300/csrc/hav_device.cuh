@@ -370,24 +370,35 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
 // word every block has passed a barrier on the other word, so no block adds
 // to it again before all have read it: the change of the low 48 bits since
 // this block's last reading is exactly this barrier's sum.  The caller keeps
-// the low field below 2^48.  Bounded like grid_sync_impl.
-__device__ inline bool fused_sync_impl(unsigned long long* word, GlobalHdr* gh, unsigned nblocks, unsigned* uses,
-                                       unsigned long long* last, unsigned long long add,
-                                       unsigned long long* delta, int* s_flag) {
+// the low field below 2^48.  Bounded like grid_wait_impl.
+//
+// Both barriers come in two halves.  The arrival orders every write the block
+// made before it; work between the arrival and the wait (writes that only the
+// block's next arrival has to publish) overlaps the wait for the other blocks.
+__device__ inline void fused_arrive_impl(unsigned long long* word, unsigned* uses, unsigned long long add) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        int fail = 0;
         *uses += 1u;
-        const unsigned target = (*uses * nblocks) & 0xffffu;
         const unsigned long long inc = (1ull << 48) | add;
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(word), "l"(inc) : "memory");
+    }
+}
+
+__device__ inline bool fused_wait_impl(unsigned long long* word, GlobalHdr* gh, unsigned nblocks,
+                                       const unsigned* uses, unsigned long long* last,
+                                       unsigned long long* delta, int* s_flag) {
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        const unsigned target = (*uses * nblocks) & 0xffffu;
         const unsigned long long t0 = globaltimer();
         unsigned long long v = 0;
+        int ab = 0;
         for (unsigned it = 0;; ++it) {
+            ab = ld_volatile(&gh->abort);  // in flight together with the poll
             v = ld_acquire64(word);
             if ((static_cast<unsigned>(v >> 48) & 0xffffu) == target) break;
             if ((it & 31) == 31) {
-                if (ld_volatile(&gh->abort) || it > kSpinIters || globaltimer() - t0 > kSpinNs) {
+                if (ab || it > kSpinIters || globaltimer() - t0 > kSpinNs) {
                     fail = 1;
                     break;
                 }
@@ -401,28 +412,38 @@ __device__ inline bool fused_sync_impl(unsigned long long* word, GlobalHdr* gh, 
         const unsigned long long c = v & ((1ull << 48) - 1ull);
         *delta = c - *last;
         *last = c;
-        *s_flag = fail | ld_volatile(&gh->abort);
+        *s_flag = fail | ab;
     }
     __syncthreads();
     return *s_flag == 0;
 }
 
-__device__ inline bool grid_sync_impl(Barrier* bar, GlobalHdr* gh, unsigned nblocks, unsigned* epoch,
-                                      int* s_flag) {
+__device__ inline void grid_arrive_impl(Barrier* bar, unsigned* epoch) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        int fail = 0;
-        const unsigned target = (*epoch + 1u) * nblocks;
         *epoch += 1u;
         // The block barrier above orders every thread's writes before this
-        // release; the acquire load below orders them before every thread's
-        // reads after the closing block barrier.  No further fence is needed.
+        // release; the acquire load in the wait orders them before every
+        // thread's reads after its closing block barrier.  No further fence
+        // is needed.
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+    }
+}
+
+__device__ inline bool grid_wait_impl(Barrier* bar, GlobalHdr* gh, unsigned nblocks, const unsigned* epoch,
+                                      int* s_flag) {
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        const unsigned target = *epoch * nblocks;
         const unsigned long long t0 = globaltimer();
+        int ab = 0;
         for (unsigned it = 0;; ++it) {
+            // the abort flag is read in the same round trip as the poll (a
+            // relaxed load ahead of the acquire), not after the barrier
+            ab = ld_volatile(&gh->abort);
             if (ld_acquire(&bar->count) >= target) break;
             if ((it & 31) == 31) {
-                if (ld_volatile(&gh->abort) || it > kSpinIters || globaltimer() - t0 > kSpinNs) {
+                if (ab || it > kSpinIters || globaltimer() - t0 > kSpinNs) {
                     fail = 1;
                     break;
                 }
@@ -433,10 +454,16 @@ __device__ inline bool grid_sync_impl(Barrier* bar, GlobalHdr* gh, unsigned nblo
             atomicExch(&gh->abort, 1);
             atomicCAS(&gh->status, 0, static_cast<int>(HAV_ERR_TIMEOUT));
         }
-        *s_flag = fail | ld_volatile(&gh->abort);
+        *s_flag = fail | ab;
     }
     __syncthreads();
     return *s_flag == 0;
+}
+
+__device__ inline bool grid_sync_impl(Barrier* bar, GlobalHdr* gh, unsigned nblocks, unsigned* epoch,
+                                      int* s_flag) {
+    grid_arrive_impl(bar, epoch);
+    return grid_wait_impl(bar, gh, nblocks, epoch, s_flag);
 }
 
 }  // namespace havk

@@ -26,6 +26,10 @@ constexpr int kMinCapLog2 = 6;             // smallest per-segment table: 64 slo
 constexpr int kPhaseTimes = 4096;          // (time, tag) records of the phase timer
 constexpr int kMaxSpecDepth = 4;           // bisection steps one pass may evaluate ahead
 constexpr int kMaxCand = (1 << kMaxSpecDepth) - 1;  // candidate sizes per pass (a full subtree)
+// Key-table sets of the bisection passes, used in rotation: pass p inserts
+// into set p % 3 and, once it has arrived at its closing grid barrier, empties
+// set (p - 1) % 3 while it waits, ready for pass p + 2.
+constexpr int kTableSets = 3;
 // default level sizes (points) up to which a pass evaluates 4, 3 or 2 steps
 // ahead (measured on GB300: 15 candidates per pass never paid off; 7 pay up
 // to about 16k points, 3 up to 256k)
@@ -93,8 +97,8 @@ struct Layout {
     size_t barrier, ghdr, seghdr, zero_bytes;  // [barrier, barrier+zero_bytes) zeroed per call
     size_t clean;          // 1 when every hash-table slot is empty (kept across calls)
     size_t lstate, hist, partial_sf, partial_cmp, pitem, trace, ptimes;
-    size_t ord[2], orig[2], taken[2], wpre, posof, dirty[2], bkt;
-    size_t tabk[2], tabv, cand;
+    size_t ord[2], orig[2], taken[2], wpre, posof, dirty[kTableSets], bkt;
+    size_t tabk[kTableSets], tabv, cand;
     size_t total;
 };
 
@@ -137,13 +141,12 @@ inline Layout make_layout(int64_t N, int32_t S, bool spec_room = true) {
         L.ord[b] = take(16 * static_cast<size_t>(N) + 16);
         L.orig[b] = take(sizeof(int32_t) * N + 16);
         L.taken[b] = take(sizeof(uint32_t) * L.taken_words);
-        L.dirty[b] = take(sizeof(uint32_t) * L.dirty_slots + 16);
     }
+    for (int b = 0; b < kTableSets; ++b) L.dirty[b] = take(sizeof(uint32_t) * L.dirty_slots + 16);
     L.wpre = take(sizeof(uint32_t) * L.taken_words);
     L.posof = take(sizeof(int32_t) * N + 16);
     L.bkt = take(sizeof(uint32_t) * 2 * 4096);
-    L.tabk[0] = take(sizeof(unsigned long long) * L.tab_slots);
-    L.tabk[1] = take(sizeof(unsigned long long) * L.tab_slots);
+    for (int b = 0; b < kTableSets; ++b) L.tabk[b] = take(sizeof(unsigned long long) * L.tab_slots);
     L.tabv = take(sizeof(unsigned long long) * L.tab_slots);
     L.cand = take(sizeof(Cand) * L.cand_slots);
     L.total = align_up(o, 256);

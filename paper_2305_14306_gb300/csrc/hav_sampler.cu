@@ -86,7 +86,7 @@ struct Smem {
     int kstar[kMaxSegments];
     int cprefix[kMaxSegments + 1];
     // per-block logs of fresh global inserts, one per (table set, owned item, candidate)
-    int dcnt[2][kLocalItems][kMaxCand];
+    int dcnt[kTableSets][kLocalItems][kMaxCand];
     // candidate grids of a speculative pass, per owned item
     Grid cgrid[kLocalItems][kMaxCand];
     int cvalid[kLocalItems][kMaxCand];
@@ -137,9 +137,9 @@ struct Dev {
     int32_t* posof;        // staged position by level index (current level)
     uint32_t* taken[2];    // by level index
     uint32_t* wpre;        // block-local prefix of taken bits per mask word
-    uint32_t* dirty[2];    // fresh-insert logs, item-owned ranges of the level index space
+    uint32_t* dirty[kTableSets];  // fresh-insert logs, item-owned ranges of the level index space
     uint32_t* bkt;         // [2][4096] bucket counts, bucket cursors
-    unsigned long long* tk[2];
+    unsigned long long* tk[kTableSets];
     unsigned long long* tv;
     Cand* cand;
     unsigned long long* ptimes;
@@ -154,25 +154,36 @@ struct Dev {
 // field stays below 2^48 (at most 640 passes per word, each below 2^31).
 constexpr unsigned long long kFusedErr = 1ull << 36;
 
-__device__ __forceinline__ bool fused_sync(Dev& d, unsigned nblocks, Smem& st, int par, unsigned long long add,
-                                           unsigned tag) {
-    const bool ok = fused_sync_impl(&d.bar->fused[par], d.gh, nblocks, &st.fused_uses[par], &st.fused_last[par],
-                                    add, &st.fused_delta, &st.flag);
+__device__ __forceinline__ void phase_record(Dev& d, Smem& st, unsigned tag) {
     if (d.ptimes && blockIdx.x == 0 && threadIdx.x == 0 && st.ntimes < d.ptimes_cap) {
         d.ptimes[2 * st.ntimes] = globaltimer();
         d.ptimes[2 * st.ntimes + 1] = tag;
         st.ntimes += 1;
     }
+}
+
+__device__ __forceinline__ void fused_arrive(Dev& d, Smem& st, int par, unsigned long long add) {
+    fused_arrive_impl(&d.bar->fused[par], &st.fused_uses[par], add);
+}
+
+__device__ __forceinline__ bool fused_wait(Dev& d, unsigned nblocks, Smem& st, int par, unsigned tag) {
+    const bool ok = fused_wait_impl(&d.bar->fused[par], d.gh, nblocks, &st.fused_uses[par], &st.fused_last[par],
+                                    &st.fused_delta, &st.flag);
+    phase_record(d, st, tag);
+    return ok;
+}
+
+__device__ __forceinline__ void grid_arrive(Dev& d, Smem& st) { grid_arrive_impl(d.bar, &st.epoch); }
+
+__device__ __forceinline__ bool grid_wait(Dev& d, unsigned nblocks, Smem& st, unsigned tag) {
+    const bool ok = grid_wait_impl(d.bar, d.gh, nblocks, &st.epoch, &st.flag);
+    phase_record(d, st, tag);
     return ok;
 }
 
 __device__ __forceinline__ bool grid_sync(Dev& d, unsigned nblocks, Smem& st, unsigned tag) {
     const bool ok = grid_sync_impl(d.bar, d.gh, nblocks, &st.epoch, &st.flag);
-    if (d.ptimes && blockIdx.x == 0 && threadIdx.x == 0 && st.ntimes < d.ptimes_cap) {
-        d.ptimes[2 * st.ntimes] = globaltimer();
-        d.ptimes[2 * st.ntimes + 1] = tag;
-        st.ntimes += 1;
-    }
+    phase_record(d, st, tag);
     return ok;
 }
 
@@ -298,7 +309,7 @@ __device__ void level_setup(const Plan& P, int j, Smem& st) {
         st.tab_off[s] = o;
         st.cand_off[s] = o / 2;
     }
-    for (int k = s; k < 2 * kLocalItems * kMaxCand; k += kThreads) (&st.dcnt[0][0][0])[k] = 0;
+    for (int k = s; k < kTableSets * kLocalItems * kMaxCand; k += kThreads) (&st.dcnt[0][0][0])[k] = 0;
     __syncthreads();
     const long long stride = st.tab_off[S - 1] + (1ll << st.cap_log2[S - 1]);
     // speculation depth: deeper on small levels, where a pass is latency-bound;
@@ -377,6 +388,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
         d.orig[b] = reinterpret_cast<int32_t*>(ws + P.lay.orig[b]);
     d.posof = reinterpret_cast<int32_t*>(ws + P.lay.posof);
         d.taken[b] = reinterpret_cast<uint32_t*>(ws + P.lay.taken[b]);
+    }
+    for (int b = 0; b < kTableSets; ++b) {
         d.dirty[b] = reinterpret_cast<uint32_t*>(ws + P.lay.dirty[b]);
         d.tk[b] = reinterpret_cast<unsigned long long*>(ws + P.lay.tabk[b]);
     }
@@ -476,8 +489,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             clear_layer_state(d, S, 1, gtid, gstride);
             if (j == 0 && !st.was_clean) {
                 // first call on this workspace, or the previous call was cut short
-                fill<unsigned long long>(d.tk[0], P.lay.tab_slots, kEmptyKey, gtid, gstride);
-                fill<unsigned long long>(d.tk[1], P.lay.tab_slots, kEmptyKey, gtid, gstride);
+                for (int b = 0; b < kTableSets; ++b)
+                    fill<unsigned long long>(d.tk[b], P.lay.tab_slots, kEmptyKey, gtid, gstride);
                 fill<unsigned long long>(d.tv, P.lay.tab_slots, kEmptyVal, gtid, gstride);
             }
             if (bucketing) fill<uint32_t>(d.bkt, 2 * 4096, 0u, gtid, gstride);
@@ -635,7 +648,11 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     st.pass_err = 0;
                 }
                 if (!__syncthreads_or(searching)) break;
-                const int X = p & 1, Y = X ^ 1;
+                // table sets: X this pass, Z the previous pass (emptied after this
+                // pass's arrival), F the next pass (empty since the last barrier)
+                const int X = p % kTableSets;
+                const int Z = (p + kTableSets - 1) % kTableSets;
+                const int F = (p + 1) % kTableSets;
 
                 // candidate grids of the owned items' segments
                 {
@@ -646,26 +663,6 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             const float sc = cand_size(st.lo[s], st.hi[s], tid);
                             st.cvalid[li][tid] = make_grid(sc, P.aspect, st.mn[s], &st.cgrid[li][tid]) ? 1 : 0;
                         }
-                    }
-                }
-                // clean the other table set, slot by slot, from this block's logs
-                if (p >= 1) {
-                    int li = 0;
-                    for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
-                        int a, b;
-                        const int s = item_range(st, S, it, &a, &b);
-                        if (!(st.flags[s] & F_SEARCH)) continue;
-                        for (int c = 0; c < ncand; ++c) {
-                            const int cnt = st.dcnt[Y][li][c];
-                            const uint32_t* lg = d.dirty[Y] + c * dstride + a;
-                            for (int k = tid; k < cnt; k += kThreads) d.tk[Y][lg[k]] = kEmptyKey;
-                        }
-                    }
-                    __syncthreads();
-                    li = 0;
-                    for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
-                        const int s = find_seg(st.item0, S, it);
-                        if (tid < ncand && (st.flags[s] & F_SEARCH)) st.dcnt[Y][li][tid] = 0;
                     }
                 }
                 __syncthreads();
@@ -795,7 +792,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 }
                 if (fused) {
                     const unsigned long long add = st.pass_cnt + (st.pass_err ? kFusedErr : 0ull);
-                    if (!fused_sync(d, nb, st, X, add, TAG(2, j, l, p))) return;
+                    fused_arrive(d, st, p & 1, add);
                 } else {
                     if (p >= 1 && blockIdx.x == 0)
                         for (int k = tid; k < S * (kMaxCand + 1); k += kThreads) {
@@ -803,7 +800,35 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             if (c < kMaxCand) ls[s].count[(p + 1) % 3][c] = 0u;
                             else ls[s].cerr[(p + 1) % 3] = 0u;
                         }
-                    if (!grid_sync(d, nb, st, TAG(2, j, l, p))) return;
+                    grid_arrive(d, st);
+                }
+                // while the other blocks arrive: empty set Z, slot by slot, from this
+                // block's logs (segments still searching only: an accepted segment's
+                // tables stay for its selection).  This block's next arrival
+                // publishes the stores, before pass p + 2 inserts into set Z.
+                if (p >= 1) {
+                    int li = 0;
+                    for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
+                        int a, b;
+                        const int s = item_range(st, S, it, &a, &b);
+                        if (!(st.flags[s] & F_SEARCH)) continue;
+                        for (int c = 0; c < ncand; ++c) {
+                            const int cnt = st.dcnt[Z][li][c];
+                            const uint32_t* lg = d.dirty[Z] + c * dstride + a;
+                            for (int k = tid; k < cnt; k += kThreads) d.tk[Z][lg[k]] = kEmptyKey;
+                        }
+                    }
+                    __syncthreads();
+                    li = 0;
+                    for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
+                        const int s = find_seg(st.item0, S, it);
+                        if (tid < ncand && (st.flags[s] & F_SEARCH)) st.dcnt[Z][li][tid] = 0;
+                    }
+                }
+                if (fused) {
+                    if (!fused_wait(d, nb, st, p & 1, TAG(2, j, l, p))) return;
+                } else {
+                    if (!grid_wait(d, nb, st, TAG(2, j, l, p))) return;
                 }
 
                 // decide (identically in every block): walk the evaluated subtree
@@ -813,6 +838,11 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     int t = st.iters[tid];
                     const unsigned cerr = fused ? (st.fused_delta >= kFusedErr ? 1u : 0u)
                                                 : ld_volatile_u(&ls[tid].cerr[p % 3]);
+                    // every candidate's count in one round trip, before the walk
+                    unsigned cnt[kMaxCand];
+#pragma unroll
+                    for (int c = 0; c < kMaxCand; ++c)
+                        cnt[c] = (!fused && c < ncand) ? ld_volatile_u(&ls[tid].count[p % 3][c]) : 0u;
                     hav_layer_trace* tr = d.tr + (static_cast<long long>(j) * S + tid) * kMaxLayers + l;
                     while (node < ncand && t < P.t_max) {
                         const float sv = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
@@ -823,9 +853,11 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             st.flags[tid] = 0;
                             break;
                         }
-                        const long long K =
-                            fused ? static_cast<long long>(st.fused_delta)
-                                  : ld_volatile(reinterpret_cast<const int*>(&ls[tid].count[p % 3][node]));
+                        unsigned kn = cnt[0];
+#pragma unroll
+                        for (int c = 1; c < kMaxCand; ++c)
+                            if (c == node) kn = cnt[c];
+                        const long long K = fused ? static_cast<long long>(st.fused_delta) : static_cast<long long>(kn);
                         if (blockIdx.x == 0) {
                             tr->s[t] = sv;
                             tr->K[t] = K;
@@ -851,10 +883,11 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     st.hi[tid] = hi;
                     st.iters[tid] = t;
                     if ((st.flags[tid] & F_SEARCH) && t >= P.t_max) {
-                        // no acceptance within t_max steps: the set cleaned in this pass is free
+                        // no acceptance within t_max steps: set F is empty for this
+                        // segment (emptied before this pass's arrival, or unused)
                         const float sv = (lo > 0.0f) ? lo : hi;
                         st.s_star[tid] = sv;
-                        st.sel[tid] = Y;
+                        st.sel[tid] = F;
                         st.sel_cand[tid] = 0;
                         st.flags[tid] = F_ACTIVE;
                         if (!make_grid(sv, P.aspect, st.mn[tid], &st.grid[tid])) {
@@ -1110,14 +1143,14 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         if (tid == 0) d.psf[static_cast<long long>(s) * kMaxBlocks + blockIdx.x] = tot;
                     }
                 }
-                // every candidate table of both sets, and the value table, back to
+                // every candidate table of every set, and the value table, back to
                 // empty, slot by slot
                 int li = 0;
                 for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
                     int a, b;
                     const int s = item_range(st, S, it, &a, &b);
                     const bool act = (st.flags[s] & F_ACTIVE) != 0;
-                    for (int t = 0; t < 2; ++t) {
+                    for (int t = 0; t < kTableSets; ++t) {
                         for (int cd = 0; cd < ncand; ++cd) {
                             const int c2 = st.dcnt[t][li][cd];
                             const bool v_too = act && st.sel[s] == t && st.sel_cand[s] == cd;
@@ -1132,7 +1165,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     }
                 }
                 __syncthreads();
-                for (int k = tid; k < 2 * kLocalItems * kMaxCand; k += kThreads)
+                for (int k = tid; k < kTableSets * kLocalItems * kMaxCand; k += kThreads)
                     (&st.dcnt[0][0][0])[k] = 0;
                 if (l + 1 < P.layers) clear_layer_state(d, S, q ^ 1, gtid, gstride);
                 if (!grid_sync(d, nb, st, TAG(5, j, l, 0))) return;

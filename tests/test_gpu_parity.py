@@ -155,6 +155,25 @@ def test_duplicates_and_lattice(hv, ctx):
         assert_parity(res, tr, K, ora, tr_o)
 
 
+@pytest.mark.parametrize("shift,aspect", [(0.0, (1.0, 1.0, 1.0)), (-8.0, (1.0, 1.0, 0.88))])
+def test_bucketed_lattice_on_cell_boundaries(hv, ctx, shift, aspect):
+    # a cloud large enough for the Morton bucketing whose box is [shift, shift + 16]
+    # on every axis: a 16^3 cell is one unit, and a quarter of the lattice planes
+    # lie exactly on cell faces, where voxels counted without the global table
+    # would first go wrong
+    g = np.arange(65, dtype=np.float32) * np.float32(0.25)
+    zz = np.arange(33, dtype=np.float32) * np.float32(0.5)
+    x, y, z = np.meshgrid(g, g, zz, indexing="ij")
+    pts = np.stack([x.ravel(), y.ravel(), z.ravel()], 1).astype(np.float32) + np.float32(shift)
+    pts = np.concatenate([pts, pts[::7]])
+    assert pts.shape[0] >= 1 << 17
+    ml = [40000, 10000, 2500]
+    res, st, tr, K = run_levels(hv, ctx, pts, ml, {"aspect": aspect})
+    assert st == 0
+    (ora, tr_o), = G.oracle_many([pts], [ml], {"aspect": aspect})
+    assert_parity(res, tr, K, ora, tr_o)
+
+
 def test_nonfinite_reports_status(hv, ctx):
     pts = scenes.uniform_box(5000, 2)
     pts[1234, 2] = np.inf

@@ -78,6 +78,7 @@ typedef struct {
     uint32_t seed;        /* draws of HAV_SELECT_RANDOM */
     float fixed_s;        /* 0: adaptive voxel (Section 3.3); > 0: fixed voxel
                              v = fixed_s * aspect, no search (Table 6 "Fix") */
+    int32_t search;       /* HAV_SEARCH_BISECT (default) or HAV_SEARCH_GUIDED */
 } hav_params;
 
 /* Voxel representatives (hav_params.select).  CENTRE_CLOSEST keeps the point
@@ -93,6 +94,21 @@ typedef struct {
 #define HAV_SELECT_RANDOM 1
 #define HAV_SELECT_MEAN 2
 #define HAV_SELECT_CENTRE 3
+
+/* Start of the Section 3.3 search (hav_params.search).  BISECT bisects over
+ * (0, s_hi], s_hi the largest bounding-box extent over the aspect.  GUIDED
+ * starts each search at a guess g and doubles up from it while the counts
+ * stay above (1 + sigma) m_l; after the first count below m_l, or once
+ * 2 * lo would reach hi, it bisects as BISECT does.  g = s_hi / sqrt(m_l) for
+ * a cloud's first search in the call; then g = s_prev * sqrt(m_prev / m_l)
+ * from the cloud's previous search (layers and levels of one call; s_prev
+ * its chosen size, m_prev its budget), the surface law K ~ s^-2.  Products,
+ * quotients and square roots are binary32, rounded to nearest; g >= s_hi
+ * gives the plain bisection.  The paper bounds the search by
+ * ceil(log 1/sigma) steps, which needs a start near s*; it does not say how
+ * to start, and both modes stop by its rule. */
+#define HAV_SEARCH_BISECT 0
+#define HAV_SEARCH_GUIDED 1
 
 /* Record a device timestamp after every grid-wide phase of the call (for
  * profiling; read back with hav_phase_times_get). */

@@ -41,10 +41,12 @@ class Params(C.Structure):
         ("select", C.c_int32),
         ("seed", C.c_uint32),
         ("fixed_s", C.c_float),
+        ("search", C.c_int32),
     ]
 
 
 SELECT = {"cc": 0, "random": 1, "mean": 2, "centre": 3}
+SEARCH = {"bisect": 0, "guided": 1}
 
 
 class LayerTrace(C.Structure):
@@ -63,9 +65,10 @@ class LayerTrace(C.Structure):
 
 
 def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 1.0),
-           select="cc", seed=0, fixed_s=0.0):
+           select="cc", seed=0, fixed_s=0.0, search="bisect"):
     """Paper defaults (Section 4.1): sigma = 0.05, t_max = 20, k = 2, centre-closest
-    selection, adaptive voxel.  select / fixed_s: the Table 6 variants."""
+    selection, adaptive voxel.  select / fixed_s: the Table 6 variants.
+    search: "bisect" (over (0, s_hi]) or "guided" (from the previous search)."""
     p = Params()
     p.sigma_num, p.sigma_den = sigma
     p.t_max, p.layers, p.layer_ratio = t_max, layers, layer_ratio
@@ -75,6 +78,7 @@ def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 
     p.select = SELECT[select] if isinstance(select, str) else int(select)
     p.seed = int(seed)
     p.fixed_s = float(fixed_s)
+    p.search = SEARCH[search] if isinstance(search, str) else int(search)
     return p
 
 

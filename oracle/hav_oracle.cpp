@@ -27,6 +27,16 @@
 //   * Eq. 3 layer budgets with ratio 4: m_l = floor(m * 4^(l-1) / S) for the
 //     first k-1 layers, the last layer takes the remainder, S = sum 4^(l-1).
 //   * Output is every taken index in ascending order.
+//   * Section 3.3 search, "guided" mode (search = 1; the default search = 0 is
+//     the bisection above): the paper bounds the search by ceil(log 1/sigma)
+//     steps, which needs a starting bracket near s*.  After the first search
+//     of a call (per cloud, across layers and levels) the next search starts
+//     from g = s_prev * sqrt(m_prev / m_l): the previous search's s* and budget
+//     under the surface law K ~ s^-2.  While every count so far exceeded
+//     k_max, the next size is 2 * lo (doubling up from g) as long as that stays
+//     below hi; otherwise, and after the first count below m_l, it is the
+//     bisection midpoint.  g >= s_hi, or no previous search, gives the plain
+//     bisection.
 //   * Table 6 variants (Section 4.5): RA keeps, per voxel, the point with the
 //     smallest counter-based SplitMix64 draw (seed, index); ME and CE keep the
 //     centre-closest index and report the voxel's mean (fixed-point sums, see
@@ -81,6 +91,7 @@ typedef struct {
     int32_t select;       // 0 centre-closest, 1 random, 2 mean, 3 centre (Table 6)
     uint32_t seed;        // draws of the random selection
     float fixed_s;        // > 0: fixed voxel size s (no search); 0: adaptive
+    int32_t search;       // 0 bisection over (0, s_hi]; 1 guided by the previous search
 } hor_params;
 
 // Per-layer record of one call: what the bisection evaluated and decided.
@@ -105,6 +116,13 @@ struct Ctx {
     float mn[3];
     float s_hi;
     float r[3];
+};
+
+// The previous search of this cloud within one call (guided search mode).
+struct Guide {
+    bool valid = false;
+    float s = 0.0f;     // its chosen s*
+    int64_t m = 0;      // its budget m_l
 };
 
 // Eq. 2: g_a = floor(x_a / v_a), then made relative to the cell of the
@@ -238,6 +256,7 @@ int check_params(const hor_params* p) {
         if (!(p->aspect[a] > 0.0f) || !std::isfinite(p->aspect[a])) return OR_ERR_INVALID;
     if (p->flags != 0) return OR_ERR_INVALID;
     if (p->select < OR_SEL_CC || p->select > OR_SEL_CE) return OR_ERR_INVALID;
+    if (p->search != 0 && p->search != 1) return OR_ERR_INVALID;
     if (!(p->fixed_s >= 0.0f) || !std::isfinite(p->fixed_s)) return OR_ERR_INVALID;
     // the ablation variants run one layer, as in Table 6
     if ((p->fixed_s > 0.0f || p->select == OR_SEL_ME || p->select == OR_SEL_CE) && p->layers != 1)
@@ -260,9 +279,10 @@ std::vector<int64_t> layer_budgets(int64_t m, int layers, int ratio) {
     return ml;
 }
 
-// One HAVSampler call on pts[0..n): fills taken[] and the trace.
+// One HAVSampler call on pts[0..n): fills taken[] and the trace; `guide`
+// carries the previous search of the cloud (guided search mode).
 int sample_one(const float* pts, int64_t n, int64_t m, const hor_params* p,
-               std::vector<uint8_t>& taken, hor_layer_trace* tr) {
+               std::vector<uint8_t>& taken, hor_layer_trace* tr, Guide* guide) {
     Ctx c;
     int st = bounding_box(pts, n, p->aspect, &c);
     if (st != OR_OK) return st;
@@ -291,8 +311,27 @@ int sample_one(const float* pts, int64_t n, int64_t m, const hor_params* p,
         float lo = 0.0f, hi = c.s_hi, s_star = 0.0f;
         bool accepted = false;
         const bool fixed = p->fixed_s > 0.0f;
+        // guided mode: start at g and double while the counts stay above k_max
+        float first = 0.0f;
+        bool up = false;
+        if (p->search == 1) {
+            float g;
+            if (guide->valid) {
+                const float ratio = static_cast<float>(guide->m) / static_cast<float>(m_l);
+                g = guide->s * std::sqrt(ratio);
+            } else {
+                g = c.s_hi / std::sqrt(static_cast<float>(m_l));
+            }
+            if (g > 0.0f && g < hi) {
+                first = g;
+                up = true;
+            }
+        }
         for (int t = 0; t < (fixed ? 0 : p->t_max); ++t) {
-            float s = (lo + hi) * 0.5f;
+            float s;
+            if (t == 0 && first > 0.0f) s = first;
+            else if (up && lo * 2.0f < hi) s = lo * 2.0f;
+            else s = (lo + hi) * 0.5f;
             int64_t K;
             st = count_voxels(pts, active, c, s, &K);
             if (st != OR_OK) return st;
@@ -303,6 +342,7 @@ int sample_one(const float* pts, int64_t n, int64_t m, const hor_params* p,
                 lo = s;
             } else if (K < m_l) {
                 hi = s;
+                up = false;
             } else {
                 s_star = s;
                 accepted = true;
@@ -311,6 +351,11 @@ int sample_one(const float* pts, int64_t n, int64_t m, const hor_params* p,
         }
         if (!accepted) s_star = (lo > 0.0f) ? lo : hi;
         if (fixed) s_star = p->fixed_s;
+        if (!fixed && p->t_max > 0) {
+            guide->valid = true;
+            guide->s = s_star;
+            guide->m = m_l;
+        }
         rec.accepted = accepted ? 1 : 0;
         rec.s_star = s_star;
 
@@ -368,24 +413,30 @@ int sample_one(const float* pts, int64_t n, int64_t m, const hor_params* p,
     return OR_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int hor_sample(const float* pts, int64_t n, int64_t m, const hor_params* p,
-               int32_t* out, hor_layer_trace* tr) {
+int sample_guided(const float* pts, int64_t n, int64_t m, const hor_params* p, int32_t* out,
+                  hor_layer_trace* tr, Guide* guide) {
     int st = check_params(p);
     if (st != OR_OK) return st;
     if (n < 0 || m < 0 || m > n || n >= (int64_t(1) << 31)) return OR_ERR_INVALID;
     if (m == 0) return OR_OK;
     if (!pts || !out) return OR_ERR_INVALID;
     std::vector<uint8_t> taken;
-    st = sample_one(pts, n, m, p, taken, tr);
+    st = sample_one(pts, n, m, p, taken, tr, guide);
     if (st != OR_OK) return st;
     int64_t j = 0;
     for (int64_t i = 0; i < n; ++i)
         if (taken[i]) out[j++] = static_cast<int32_t>(i);
     return (j == m) ? OR_OK : OR_ERR_INVALID;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hor_sample(const float* pts, int64_t n, int64_t m, const hor_params* p,
+               int32_t* out, hor_layer_trace* tr) {
+    Guide guide;
+    return sample_guided(pts, n, m, p, out, tr, &guide);
 }
 
 // Level chain: level j+1 samples the points level j kept (in ascending
@@ -407,12 +458,13 @@ int hor_sample_levels(const float* pts, int64_t n, const int64_t* m_levels,
     std::vector<int32_t> orig(static_cast<size_t>(n));
     for (int64_t i = 0; i < n; ++i) orig[i] = static_cast<int32_t>(i);
     int64_t cur_n = n, off = 0;
+    Guide guide;  // the guided search carries over from level to level
     for (int32_t j = 0; j < num_levels; ++j) {
         const int64_t m = m_levels[j];
         std::vector<int32_t> idx(static_cast<size_t>(m));
         if (m > 0) {
-            st = hor_sample(cur.data(), cur_n, m, p, idx.data(),
-                            tr ? tr + int64_t(j) * p->layers : nullptr);
+            st = sample_guided(cur.data(), cur_n, m, p, idx.data(),
+                               tr ? tr + int64_t(j) * p->layers : nullptr, &guide);
             if (st != OR_OK) return st;
         }
         std::vector<float> nxt(static_cast<size_t>(3 * m));

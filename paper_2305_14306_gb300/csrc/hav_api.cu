@@ -65,6 +65,7 @@ void hav_params_default(hav_params* p) {
     p->select = HAV_SELECT_CENTRE_CLOSEST;
     p->seed = 0;
     p->fixed_s = 0.0f;
+    p->search = HAV_SEARCH_BISECT;
 }
 
 const char* hav_status_string(hav_status s) {
@@ -227,6 +228,7 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
     plan->select = params->select;
     plan->seed = params->seed;
     plan->fixed_s = params->fixed_s;
+    plan->search = params->search;
     for (int j = 0; j < num_levels; ++j) plan->out[j] = out_idx[j];
     if (params->flags & HAV_FLAG_PHASE_TIMES) {
         plan->ptimes = reinterpret_cast<unsigned long long*>(ctx->ws + ctx->lay.ptimes);
@@ -252,7 +254,8 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
         // levels from j0 on, where every segment has at most small_points points,
         // run on thread-block clusters; the phase timer stays with the grid kernel
         int j0 = num_levels;
-        if (ctx->small_points > 0 && !(params->flags & HAV_FLAG_PHASE_TIMES)) {
+        if (ctx->small_points > 0 && !(params->flags & HAV_FLAG_PHASE_TIMES) &&
+            params->search == HAV_SEARCH_BISECT) {
             for (int j = 0; j < num_levels && j0 == num_levels; ++j) {
                 int64_t mx = 0;
                 for (int s = 0; s < num_segments; ++s) {

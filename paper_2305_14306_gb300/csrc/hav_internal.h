@@ -170,7 +170,7 @@ struct Plan {
     uint32_t seed;               // draws of HAV_SELECT_RANDOM
     float fixed_s;               // > 0: fixed voxel size, no search
     int32_t keep_orig;           // write the last level's original indices (a cluster launch follows)
-    int32_t pad3;
+    int32_t search;              // HAV_SEARCH_*
     int64_t off0[kMaxSegments + 1];       // level-0 segment offsets
     int32_t m[kMaxLevels][kMaxSegments];  // budgets per level and segment
 };
@@ -180,6 +180,7 @@ struct Plan {
 // run one layer.
 inline hav_status check_variant_params(const hav_params* p) {
     if (p->select < HAV_SELECT_CENTRE_CLOSEST || p->select > HAV_SELECT_CENTRE) return HAV_ERR_INVALID;
+    if (p->search != HAV_SEARCH_BISECT && p->search != HAV_SEARCH_GUIDED) return HAV_ERR_INVALID;
     if (!(p->fixed_s >= 0.0f) || !std::isfinite(p->fixed_s)) return HAV_ERR_INVALID;
     if ((p->fixed_s > 0.0f || p->select == HAV_SELECT_MEAN || p->select == HAV_SELECT_CENTRE) && p->layers != 1)
         return HAV_ERR_INVALID;

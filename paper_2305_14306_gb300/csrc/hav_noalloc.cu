@@ -127,6 +127,7 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
         plan.select = params->select;
         plan.seed = params->seed;
         plan.fixed_s = params->fixed_s;
+        plan.search = params->search;
         plan.out[0] = out_idx;
         plan.off0[0] = 0;
         plan.off0[1] = n;

@@ -58,7 +58,7 @@ constexpr int kProbes = 2;         // global first probes issued together per th
 static_assert(kSetSlots % (kProbes * kThreads) == 0 && kSelSlots % (kProbes * kThreads) == 0,
               "flush loops take kProbes slots per thread per step");
 
-enum : int { F_ACTIVE = 1, F_SEARCH = 2, F_ACCEPT = 4 };
+enum : int { F_ACTIVE = 1, F_SEARCH = 2, F_ACCEPT = 4, F_UP = 8 };
 
 struct Smem {
     // level layout
@@ -76,6 +76,11 @@ struct Smem {
     float s_hi[kMaxSegments];
     // controller of the current layer
     float lo[kMaxSegments], hi[kMaxSegments], s_star[kMaxSegments];
+    // guided search: the pending first size of the current search, and the
+    // segment's previous search in this call (its s*, its budget; 0: none)
+    float first[kMaxSegments];
+    float gs[kMaxSegments];
+    int gm[kMaxSegments];
     Grid grid[kMaxSegments];
     int iters[kMaxSegments];
     int sel_cand[kMaxSegments];
@@ -266,14 +271,29 @@ __device__ __forceinline__ unsigned bucket_of(const float p[3], const float mn[3
 // (lo, hi): the path from the root follows the bits of c + 1 below its
 // leading one (0: too few voxels, hi = s; 1: too many, lo = s), with the
 // same binary32 midpoint as the sequential search.
-__device__ __forceinline__ float cand_size(float lo, float hi, int c) {
+// The next size of a search with bracket (lo, hi): a pending first guess,
+// 2 lo while doubling up (guided start, F_UP), else the bisection midpoint.
+__device__ __forceinline__ float next_size(float lo, float hi, bool up, float first) {
+    if (first > 0.0f) return first;
+    const float d = __fmul_rn(lo, 2.0f);
+    if (up && d < hi) return d;
+    return __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+}
+
+// Size at node c of the search subtree below the current state (heap order:
+// child 2c + 1 follows a count below m_l, 2c + 2 a count above k_max).
+__device__ __forceinline__ float cand_size(float lo, float hi, bool up, float first, int c) {
     const int x = c + 1;
     const int depth = 31 - __clz(x);
-    float s = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+    float s = next_size(lo, hi, up, first);
     for (int b = depth - 1; b >= 0; --b) {
-        if ((x >> b) & 1) lo = s;
-        else hi = s;
-        s = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+        if ((x >> b) & 1) {
+            lo = s;
+        } else {
+            hi = s;
+            up = false;
+        }
+        s = next_size(lo, hi, up, 0.0f);
     }
     return s;
 }
@@ -399,6 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
     d.cand = reinterpret_cast<Cand*>(ws + P.lay.cand);
     d.ptimes = P.ptimes;
     d.ptimes_cap = P.ptimes_cap;
+    for (int k = tid; k < P.S; k += kThreads) st.gm[k] = 0;  // no previous search yet
     if (tid == 0) {
         st.fused_uses[0] = st.fused_uses[1] = 0u;
         st.fused_last[0] = st.fused_last[1] = 0ull;
@@ -547,18 +568,20 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 if (h[b]) atomicAdd(&d.bkt[b], h[b]);
             if (!grid_sync(d, nb, st, TAG(9, j, 0, 0))) return;
             {
-                // exclusive prefix over the 4096 global counts (4 bins per thread)
-                uint32_t c4[4], sum = 0;
+                // exclusive prefix over the 4096 global counts (whole bins per thread)
+                constexpr int kPerT = 4096 / kThreads;
+                static_assert(4096 % kThreads == 0, "bucket bins per thread");
+                uint32_t c4[kPerT], sum = 0;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    c4[k] = d.bkt[4 * tid + k];
+                for (int k = 0; k < kPerT; ++k) {
+                    c4[k] = d.bkt[kPerT * tid + k];
                     sum += c4[k];
                 }
                 unsigned tot;
                 unsigned before = block_excl_scan<unsigned>(sum, &tot, st.scan_u);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    hb[4 * tid + k] = before;
+                for (int k = 0; k < kPerT; ++k) {
+                    hb[kPerT * tid + k] = before;
                     before += c4[k];
                 }
                 __syncthreads();
@@ -608,6 +631,19 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 const bool fixed = P.fixed_s > 0.0f;
                 int fl = active ? F_ACTIVE : 0;
                 if (active && P.t_max > 0 && !fixed) fl |= F_SEARCH;
+                // guided start: g from the previous search, or from s_hi for the
+                // first; doubling up from it while the counts stay too high
+                st.first[tid] = 0.0f;
+                if ((fl & F_SEARCH) && P.search == HAV_SEARCH_GUIDED) {
+                    const float g =
+                        (st.gm[tid] > 0)
+                            ? __fmul_rn(st.gs[tid], __fsqrt_rn(__fdiv_rn(__int2float_rn(st.gm[tid]), __ll2float_rn(ml))))
+                            : __fdiv_rn(st.s_hi[tid], __fsqrt_rn(__ll2float_rn(ml)));
+                    if (g > 0.0f && g < st.s_hi[tid]) {
+                        st.first[tid] = g;
+                        fl |= F_UP;
+                    }
+                }
                 if (active && (P.t_max == 0 || fixed)) {
                     st.s_star[tid] = fixed ? P.fixed_s : st.s_hi[tid];
                     if (!make_grid(st.s_star[tid], P.aspect, st.mn[tid], &st.grid[tid])) {
@@ -660,7 +696,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     for (int it = blockIdx.x; it < st.items_total; it += nb, ++li) {
                         const int s = find_seg(st.item0, S, it);
                         if (tid < ncand && (st.flags[s] & F_SEARCH)) {
-                            const float sc = cand_size(st.lo[s], st.hi[s], tid);
+                            const float sc = cand_size(st.lo[s], st.hi[s], (st.flags[s] & F_UP) != 0,
+                                                       st.first[s], tid);
                             st.cvalid[li][tid] = make_grid(sc, P.aspect, st.mn[s], &st.cgrid[li][tid]) ? 1 : 0;
                         }
                     }
@@ -834,6 +871,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 // decide (identically in every block): walk the evaluated subtree
                 if (searching) {
                     float lo = st.lo[tid], hi = st.hi[tid];
+                    bool up = (st.flags[tid] & F_UP) != 0;
+                    float first = st.first[tid];
                     int node = 0;
                     int t = st.iters[tid];
                     const unsigned cerr = fused ? (st.fused_delta >= kFusedErr ? 1u : 0u)
@@ -845,7 +884,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         cnt[c] = (!fused && c < ncand) ? ld_volatile_u(&ls[tid].count[p % 3][c]) : 0u;
                     hav_layer_trace* tr = d.tr + (static_cast<long long>(j) * S + tid) * kMaxLayers + l;
                     while (node < ncand && t < P.t_max) {
-                        const float sv = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+                        const float sv = next_size(lo, hi, up, first);
+                        first = 0.0f;
                         Grid gv;
                         if ((cerr >> node) & 1u || !make_grid(sv, P.aspect, st.mn[tid], &gv)) {
                             seg_error(d, tid, HAV_ERR_RANGE);
@@ -869,6 +909,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             node = 2 * node + 2;
                         } else if (K < st.ml[tid]) {
                             hi = sv;
+                            up = false;
                             node = 2 * node + 1;
                         } else {
                             st.s_star[tid] = sv;
@@ -882,6 +923,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     st.lo[tid] = lo;
                     st.hi[tid] = hi;
                     st.iters[tid] = t;
+                    st.first[tid] = first;
+                    if (st.flags[tid] & F_SEARCH) st.flags[tid] = up ? (st.flags[tid] | F_UP) : (st.flags[tid] & ~F_UP);
                     if ((st.flags[tid] & F_SEARCH) && t >= P.t_max) {
                         // no acceptance within t_max steps: set F is empty for this
                         // segment (emptied before this pass's arrival, or unused)
@@ -901,6 +944,12 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             }
             // (every searching segment takes at least one step per pass, so none is
             // still searching after t_max passes)
+            // the guided start of the segment's next search follows this one
+            if (P.search == HAV_SEARCH_GUIDED && tid < S && st.ml[tid] > 0 && P.t_max > 0 &&
+                !(P.fixed_s > 0.0f) && st.err[tid] == 0) {
+                st.gs[tid] = st.s_star[tid];
+                st.gm[tid] = st.ml[tid];
+            }
 
             // ------------------------------------- Section 3.2 selection at s*
             {

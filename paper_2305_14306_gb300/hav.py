@@ -35,8 +35,13 @@ class hav_params(C.Structure):
         ("select", C.c_int32),
         ("seed", C.c_uint32),
         ("fixed_s", C.c_float),
+        ("search", C.c_int32),
     ]
 
+
+# start of the Section 3.3 search: bisection over (0, s_hi], or guided by the
+# cloud's previous search (HAV_SEARCH_GUIDED in hav.h)
+SEARCH = {"bisect": 0, "guided": 1}
 
 # voxel representatives (Table 6): the method's centre-closest point, a random
 # point, the voxel mean, the voxel centre
@@ -149,7 +154,7 @@ def load(path: str = LIB_PATH):
 
 
 def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 1.0),
-           flags=0, select="centre-closest", seed=0, fixed_s=0.0) -> hav_params:
+           flags=0, select="centre-closest", seed=0, fixed_s=0.0, search="bisect") -> hav_params:
     p = hav_params()
     load().hav_params_default(C.byref(p))
     p.sigma_num, p.sigma_den = sigma
@@ -160,6 +165,7 @@ def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 
     p.select = SELECT[select] if isinstance(select, str) else int(select)
     p.seed = int(seed)
     p.fixed_s = float(fixed_s)
+    p.search = SEARCH[search] if isinstance(search, str) else int(search)
     return p
 
 

@@ -128,44 +128,76 @@ def budgets(m: int, layers: int, ratio: int):
     return ml
 
 
-def bisection(p, m_l, s_hi, sigma=(5, 100), t_max=20, aspect=(1.0, 1.0, 1.0), active=None):
-    """Section 3.3 search with numpy counting; returns (trace [(s, K)], s*, accepted)."""
+def bisection(p, m_l, s_hi, sigma=(5, 100), t_max=20, aspect=(1.0, 1.0, 1.0), active=None, start=None):
+    """Section 3.3 search with numpy counting; returns (trace [(s, K)], s*, accepted).
+    start: the guided search's first size; from it the size doubles while every
+    count so far was above k_max and twice the lower end stays below the top,
+    and bisects otherwise."""
     k_max = m_l + (m_l * sigma[0]) // sigma[1]
     lo, hi = F32(0.0), F32(s_hi)
+    up = start is not None
     trace = []
-    for _ in range(t_max):
-        s = F32((lo + hi) * F32(0.5))
+    for t in range(t_max):
+        if t == 0 and start is not None:
+            s = F32(start)
+        elif up and F32(lo * F32(2.0)) < hi:
+            s = F32(lo * F32(2.0))
+        else:
+            s = F32((lo + hi) * F32(0.5))
         K = count_unique(p, s, aspect, active)
         trace.append((s, K))
         if K > k_max:
             lo = s
         elif K < m_l:
             hi = s
+            up = False
         else:
             return trace, s, True
     return trace, (lo if lo > 0 else hi), False
 
 
+def guided_start(s_hi, m_l, prev):
+    """First size of a guided search: s_hi / sqrt(m_l) without a previous search,
+    else s_prev * sqrt(m_prev / m_l); None when it is not below s_hi."""
+    if prev is None:
+        g = F32(F32(s_hi) / np.sqrt(F32(m_l)))
+    else:
+        g = F32(F32(prev[0]) * np.sqrt(F32(F32(prev[1]) / F32(m_l))))
+    return g if (g > 0 and g < F32(s_hi)) else None
+
+
 def hav_reference_small(p, m, layers=2, ratio=4, sigma=(5, 100), t_max=20, aspect=(1.0, 1.0, 1.0),
-                        select="cc", seed=0, fixed_s=0.0):
+                        select="cc", seed=0, fixed_s=0.0, search="bisect", guide=None, traces=None):
     """Whole sampler on a tiny cloud with numpy pieces (bisection + lexsort select +
     priority truncation + shortfall), for cross-checking the oracle end to end.
     select "random": per cell the smallest SplitMix64 draw (high 32 bits) wins;
-    fixed_s > 0: no search, s* = fixed_s."""
+    fixed_s > 0: no search, s* = fixed_s.  search "guided": each search starts at
+    guided_start(); `guide` (a one-element list) carries (s*, m_l) of the previous
+    search between calls; `traces` collects each layer's [(s, K)]."""
     n = p.shape[0]
     taken = np.zeros(n, dtype=bool)
     _, s_hi = bbox_s_hi(p, aspect)
+    if guide is None:
+        guide = [None]
     word = None
     if select == "random":
         word = np.array([splitmix64_draw(seed, i) >> 32 for i in range(n)], dtype=np.uint64)
     for m_l in budgets(m, layers, ratio):
         if m_l == 0:
+            if traces is not None:
+                traces.append([])
             continue
         active = np.nonzero(~taken)[0]
         if fixed_s > 0:
             s_star = F32(fixed_s)
+            tr = []
         else:
-            _, s_star, _ = bisection(p, m_l, s_hi, sigma, t_max, aspect, active)
+            start = guided_start(s_hi, m_l, guide[0]) if search == "guided" else None
+            tr, s_star, _ = bisection(p, m_l, s_hi, sigma, t_max, aspect, active, start)
+            if t_max > 0:
+                guide[0] = (s_star, m_l)
+        if traces is not None:
+            traces.append(tr)
         if word is None:
             reps = lexsort_select(p, s_star, aspect, active)
         else:
@@ -187,3 +219,21 @@ def hav_reference_small(p, m, layers=2, ratio=4, sigma=(5, 100), t_max=20, aspec
                     taken[i] = True
                     need -= 1
     return np.nonzero(taken)[0].astype(np.int32)
+
+
+def hav_reference_levels_small(p, m_levels, search="bisect", **kw):
+    """Level chain of hav_reference_small: level j + 1 samples level j's points in
+    ascending order; indices refer to the original cloud.  Returns (levels, traces),
+    traces[j][l] the [(s, K)] of level j, layer l."""
+    cur = np.asarray(p, dtype=F32)
+    orig = np.arange(cur.shape[0], dtype=np.int32)
+    guide = [None]
+    out, traces = [], []
+    for m in m_levels:
+        tr = []
+        idx = hav_reference_small(cur, m, search=search, guide=guide, traces=tr, **kw) if m > 0 else \
+            np.zeros(0, dtype=np.int32)
+        out.append(orig[idx])
+        traces.append(tr)
+        cur, orig = cur[idx], orig[idx]
+    return out, traces

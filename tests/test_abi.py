@@ -49,9 +49,10 @@ def test_struct_layouts_match_header(libhav, tmp_path):
     src = tmp_path / "s.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "hav.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hav_params), sizeof(hav_layer_trace),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hav_params), sizeof(hav_layer_trace),'
         ' offsetof(hav_layer_trace, s), offsetof(hav_layer_trace, K), sizeof(hav_tuning),'
-        ' offsetof(hav_tuning, chunk_min), offsetof(hav_tuning, small_points)); return 0;}\n')
+        ' offsetof(hav_tuning, chunk_min), offsetof(hav_tuning, small_points),'
+        ' offsetof(hav_params, search)); return 0;}\n')
     exe = tmp_path / "s"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
@@ -64,6 +65,7 @@ def test_struct_layouts_match_header(libhav, tmp_path):
     assert int(out[4]) == ctypes.sizeof(hav.hav_tuning)
     assert int(out[5]) == hav.hav_tuning.chunk_min.offset
     assert int(out[6]) == hav.hav_tuning.small_points.offset
+    assert int(out[7]) == hav.hav_params.search.offset
 
 
 def test_params_default_and_status_strings(libhav):
@@ -72,6 +74,7 @@ def test_params_default_and_status_strings(libhav):
     p = hav.params()
     assert (p.sigma_num, p.sigma_den, p.t_max, p.layers, p.layer_ratio) == (5, 100, 20, 2, 4)
     assert list(p.aspect) == [1.0, 1.0, 1.0]
+    assert (p.select, p.fixed_s, p.search) == (0, 0.0, 0)
     for code in range(8):
         assert hav.load().hav_status_string(code)
 

@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -194,6 +195,17 @@ def whole_job(local_seconds: float, points_per_rank: int, world: int, device=Non
     return t, points_per_rank * world / t / 1e6
 
 
+def host_cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -221,7 +233,8 @@ def run_reference(args, world, rank):
     # calibrate: per-point time on a 16k prefix (the scenes are shuffled or scan-ordered clouds)
     n_cal = min(16384, n_full)
     t0 = time.perf_counter()
-    oracle.sample_levels(pts[:n_cal], levels_for(n_cal))
+    op = oracle.params(search=args.search)
+    oracle.sample_levels(pts[:n_cal], levels_for(n_cal), op)
     per_pt = (time.perf_counter() - t0) / n_cal
     budget_s = 90.0
     n_s = int(budget_s / max(1, args.steps + args.warmup) / per_pt)
@@ -229,10 +242,10 @@ def run_reference(args, world, rank):
     sample = pts[:n_s]
     ml = levels_for(n_s)
     for _ in range(args.warmup):
-        oracle.sample_levels(sample, ml)
+        oracle.sample_levels(sample, ml, op)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.sample_levels(sample, ml)
+        oracle.sample_levels(sample, ml, op)
     dt = time.perf_counter() - t0
     value = n_s * args.steps / dt / 1e6
     desc = f"first {n_s} points of the {args.workload} scene, levels {ml}, per step"
@@ -241,8 +254,9 @@ def run_reference(args, world, rank):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": w["desc"], "sample": desc},
-        "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "config": {"workload": args.workload, "desc": w["desc"], "sample": desc, "search": args.search},
+        "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": 1, "kind": "oracle", "sample": desc,
+                         "cpu_model": host_cpu_model()},
         "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -262,7 +276,7 @@ def run_batched(args, world, rank, local):
     sizes = np.diff(offs)
     seg_m = np.stack([sizes // 4, sizes // 16]).astype(np.int64)
     total = int(offs[-1])
-    p = hav.params()
+    p = hav.params(search=args.search)
     ctx = hav.Context(total, 64)
     ctx1 = hav.Context(int(sizes.max()), 1)
     stream = torch.cuda.current_stream()
@@ -347,7 +361,8 @@ def run_batched(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "batch64", "desc": WORKLOADS["batch64"]["desc"], "points": total,
-                       "segments": 64, "levels": 2, "l2": "flushed before every step (256 MB write)"},
+                       "segments": 64, "levels": 2, "l2": "flushed before every step (256 MB write)",
+                       "search": args.search},
             "scenes_per_s": 64 * len(ms_b) / (sum(ms_b) / 1e3),
             "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
             "graph": {"value": v_graph, "ms_per_step": statistics.fmean(ms_g)},
@@ -395,7 +410,7 @@ def run_compare(args, world, rank, local):
         return out, a.elapsed_time(b)
 
     rng = np.random.default_rng(11)
-    p = hav.params()
+    p = hav.params(search=args.search)
     cases = []
 
     def single(name, pts_np, m, exact_cov, sample_q=None):
@@ -650,8 +665,9 @@ def run_serving(args, world, rank, local):
         return out
 
     slot_points = int(pool_n.max()) * 2
-    served = serving.Server(slots=args.serve_slots, slot_points=slot_points, max_segments=64)
-    plain = serving.Server(slots=1, slot_points=int(pool_n.max()), max_segments=1, share_sms=False)
+    sp = hav.params(search=args.search)
+    served = serving.Server(slots=args.serve_slots, slot_points=slot_points, max_segments=64, params=sp)
+    plain = serving.Server(slots=1, slot_points=int(pool_n.max()), max_segments=1, share_sms=False, params=sp)
     try:
         zero = np.zeros(R)
         plain.serve(make(zero[:min(R, 8)]))  # warm-up
@@ -691,7 +707,8 @@ def run_serving(args, world, rank, local):
             "n_gpus": world, "steps": R, "warmup": 8, "ms_per_step": 1e3 / cap_served,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving", "desc": WORKLOADS["serving"]["desc"], "requests": R,
-                       "slots": args.serve_slots, "slot_points": slot_points, "pool_scenes": len(pool)},
+                       "slots": args.serve_slots, "slot_points": slot_points, "pool_scenes": len(pool),
+                       "search": args.search},
             "scenes_per_s": cap_served,
             "plain": {"scenes_per_s": cap_plain, "value": pts_total / R * cap_plain / 1e6},
             "speedup_vs_per_cloud": cap_served / cap_plain,
@@ -714,6 +731,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-slots", type=int, default=2)
+    ap.add_argument("--search", choices=["bisect", "guided"], default="bisect",
+                    help="start of the voxel-size search: bisection over (0, s_hi] (default), or "
+                         "guided by the cloud's previous search")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON cache of autotuned knobs (default: always sweep, write nothing)")
     args = ap.parse_args()
@@ -749,15 +769,15 @@ def main():
     pts = make_scene(args.workload, seed=rank)
     n = pts.shape[0]
     ml = [min(m, n) for m in w["levels"]]
-    p = hav.params()
+    p = hav.params(search=args.search)
     ctx = hav.Context(n, 1)
     stream = torch.cuda.current_stream()
     d_pts = torch.from_numpy(pts).cuda()
     outs = [torch.empty(m, dtype=torch.int32, device="cuda") for m in ml]
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    def step():
-        hav.hav_sample_levels(ctx, d_pts, ml, p, outs=outs, stream=stream)
+    def step(pp=p):
+        hav.hav_sample_levels(ctx, d_pts, ml, pp, outs=outs, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -776,19 +796,19 @@ def main():
         except ValueError:
             pass
 
-    def timed():
+    def timed(pp=p, steps=args.steps):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
+               for _ in range(steps)]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         clk = Clocks(gpu_index)
         time.sleep(0.3)
         t0 = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(steps):
             flush.zero_()
             evs[k][0].record(stream)
-            step()
+            step(pp)
             evs[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -838,18 +858,41 @@ def main():
                 "peak_kind": peak_kind, "kernel": "hav_chain_kernel",
                 "algorithmic_bytes_per_launch": B}
 
+    # the other search start on the same workload, timed the same way
+    other = None
+    if args.search == "bisect":
+        pg = hav.params(search="guided")
+        for _ in range(args.warmup):
+            step(pg)
+        st, _ = hav.hav_status_get(ctx, 1)
+        tr_g = hav.hav_trace_get(ctx, len(ml) * pg.layers)
+        B_g = algorithmic_bytes(tr_g, level_inputs, ml, pg.layers)
+        g_steps = min(args.steps, 200)
+        ms_g, _, clk_g = timed(pg, g_steps)
+        if st == hav.HAV_OK and hav.hav_status_get(ctx, 1)[0] == hav.HAV_OK:
+            _, v_g = whole_job(sum(ms_g) / 1e3, n * g_steps, world, device="cuda")
+            mg = statistics.fmean(ms_g)
+            peak_g, _ = read_peaks()
+            other = {"search": "guided", "value": v_g, "unit": "Mpoints/s", "ms_per_step": mg,
+                     "p50_ms": sorted(ms_g)[len(ms_g) // 2], "steps": g_steps,
+                     "bisection_steps": int(sum(int(t["iters"]) for t in tr_g)),
+                     "roofline_frac": B_g / (mg / 1e3) / 1e9 / peak_g,
+                     "algorithmic_bytes_per_launch": B_g, "sm_mhz": clk_g.get("sm_mhz")}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
+        op = oracle.params(search=args.search)
         runs, t_cpu = 0, 0.0
-        while runs < 3 and (runs == 0 or t_cpu < 10.0):
+        while runs < 30 and (runs < 3 or t_cpu < 10.0):
             t0 = time.perf_counter()
-            oracle.sample_levels(pts, ml)
+            oracle.sample_levels(pts, ml, op)
             t_cpu += time.perf_counter() - t0
             runs += 1
         cpu = {"value": n * runs / t_cpu / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
-               "sample": f"{runs} full run(s) of the same scene and level chain, single thread"}
+               "sample": f"{runs} full run(s) of the same scene and level chain ({t_cpu:.1f} s), single thread",
+               "cpu_model": host_cpu_model()}
 
     if rank == 0:
         line = {
@@ -858,7 +901,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "n": n, "levels": ml,
-                       "layers": p.layers, "sigma": "5/100", "t_max": p.t_max,
+                       "layers": p.layers, "sigma": "5/100", "t_max": p.t_max, "search": args.search,
+                       "bisection_steps": int(sum(int(t["iters"]) for t in traces)),
                        "l2": "flushed before every step (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "scenes_per_s": world * args.steps / total_s,
@@ -872,6 +916,8 @@ def main():
             "clocks": clocks,
             "wall_s_timed": wall,
         }
+        if other is not None:
+            line["search_guided"] = other
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

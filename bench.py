@@ -264,6 +264,31 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------- batched arm
+def _oracle_cloud(job):
+    """One cloud of a batch on one host core (a spawned pool worker)."""
+    import oracle
+    pts, ml, search = job
+    return oracle.sample_levels(pts, ml, oracle.params(search=search))
+
+
+def scene_parallel_oracle(clouds, m_levels, search, reps=3):
+    """The oracle over a batch, one cloud per host core (spawned processes, so
+    that no worker inherits the CUDA context); m_levels[s] is cloud s's level
+    budgets.  Returns (Mpoints/s, cores, per-cloud outputs)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    jobs = [(c, [int(x) for x in m_levels[s]], search) for s, c in enumerate(clouds)]
+    total = sum(c.shape[0] for c in clouds)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        # bounded waits: a pool whose workers cannot start would wait forever
+        pool.map_async(_oracle_cloud, jobs[:cores]).get(timeout=300)  # workers up, library loaded
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            res = pool.map_async(_oracle_cloud, jobs, chunksize=1).get(timeout=600)
+        dt = time.perf_counter() - t0
+    return total * reps / dt / 1e6, cores, res
 def run_batched(args, world, rank, local):
     """64 clouds per step: one hav_sample_batched launch, the same launch from a
     CUDA graph, and 64 plain per-cloud hav_sample_levels calls, at identical outputs."""
@@ -351,6 +376,19 @@ def run_batched(args, world, rank, local):
     ms_p = time_it(step_per_cloud, max(5, steps // 4))
     clocks = clk.stop()
     tb, value = whole_job(sum(ms_b) / 1e3, total * len(ms_b), world, device="cuda")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v_cpu, cores, res = scene_parallel_oracle(clouds, [seg_m[:, s] for s in range(64)], args.search)
+        except Exception as e:  # reported, never silently replaced
+            raise SystemExit(f"scene-parallel oracle failed: {e!r}")
+        same = all(np.array_equal(outs[j].cpu().numpy()[cut[j][s]:cut[j][s + 1]], res[s][j])
+                   for j in range(2) for s in range(64))
+        if not same:
+            raise SystemExit("the GPU batch and the scene-parallel oracle differ")
+        cpu = {"value": v_cpu, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+               "sample": "the same 64 clouds, 3 times, one cloud per process (spawned pool)",
+               "identical_outputs": True, "cpu_model": host_cpu_model()}
     v_graph = total * len(ms_g) / (sum(ms_g) / 1e3) / 1e6
     v_per = total * len(ms_p) / (sum(ms_p) / 1e3) / 1e6
     if rank == 0:
@@ -370,6 +408,7 @@ def run_batched(args, world, rank, local):
                           "launches_per_step": 64},
             "speedup_vs_per_cloud": value / v_per,
             "identical_outputs": True,
+            "cpu_baseline": cpu,
             "tuning": {"batched": tuned, **tune_report,
                        "per_cloud": "default knobs (one call per cloud)"},
             "gpu_launches": len(ms_b),
@@ -646,7 +685,7 @@ def run_serving(args, world, rank, local):
     """C5: closed-loop capacity and open-loop latency (Poisson arrivals at 0.5, 0.8
     and 0.95 x the plain path's capacity) of the served path vs the plain per-cloud path."""
     import torch
-    from paper_2305_14306_gb300 import serving
+    from paper_2305_14306_gb300 import hav, serving
 
     rng = np.random.default_rng(1000 + rank)
     pool_n = scenes.log_uniform_sizes(16, 10_000, 1_000_000, seed=1000 + rank)
@@ -701,6 +740,23 @@ def run_serving(args, world, rank, local):
         served.close()
         plain.close()
     pts_total = int(sum(pool[picks[i]].shape[0] for i in range(R)))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the first 48 requests on the host cores, one scene per process
+        k = min(R, 48)
+        reqs = [(pool[picks[i]].numpy(), [[n // 4, n // 16, min(4096, n)][choice[i]]])
+                for i in range(k) for n in [pool[picks[i]].shape[0]]]
+        try:
+            v_cpu, cores, res = scene_parallel_oracle([r[0] for r in reqs], [r[1] for r in reqs],
+                                                      args.search, reps=1)
+        except Exception as e:
+            raise SystemExit(f"scene-parallel oracle failed: {e!r}")
+        pts_k = sum(r[0].shape[0] for r in reqs)
+        same = same and all(np.array_equal(res[i][0], res_p[i].indices) for i in range(k))
+        cpu = {"value": v_cpu, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+               "scenes_per_s": v_cpu * 1e6 / (pts_k / k),
+               "sample": f"the first {k} requests ({pts_k} points), one scene per process (spawned pool)",
+               "cpu_model": host_cpu_model()}
     if rank == 0:
         line = {
             "metric": "input Mpoints/s", "value": pts_total / R * cap_served / 1e6, "unit": "Mpoints/s",
@@ -714,6 +770,7 @@ def run_serving(args, world, rank, local):
             "speedup_vs_per_cloud": cap_served / cap_plain,
             "open_loop": open_loop,
             "identical_outputs": bool(same),
+            "cpu_baseline": cpu,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -788,6 +788,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-slots", type=int, default=2)
+    ap.add_argument("--no-search-compare", action="store_true",
+                    help="skip timing the guided search start beside the default one")
     ap.add_argument("--search", choices=["bisect", "guided"], default="bisect",
                     help="start of the voxel-size search: bisection over (0, s_hi] (default), or "
                          "guided by the cloud's previous search")
@@ -911,13 +913,14 @@ def main():
     peak, peak_kind = read_peaks()
     achieved = B / (mean_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
+                "frac": achieved / peak,
+                "traffic": profiled_traffic(args.workload + ("-guided" if args.search == "guided" else "")),
                 "peak_kind": peak_kind, "kernel": "hav_chain_kernel",
                 "algorithmic_bytes_per_launch": B}
 
     # the other search start on the same workload, timed the same way
     other = None
-    if args.search == "bisect":
+    if args.search == "bisect" and not args.no_search_compare:
         pg = hav.params(search="guided")
         for _ in range(args.warmup):
             step(pg)
@@ -934,7 +937,8 @@ def main():
                      "p50_ms": sorted(ms_g)[len(ms_g) // 2], "steps": g_steps,
                      "bisection_steps": int(sum(int(t["iters"]) for t in tr_g)),
                      "roofline_frac": B_g / (mg / 1e3) / 1e9 / peak_g,
-                     "algorithmic_bytes_per_launch": B_g, "sm_mhz": clk_g.get("sm_mhz")}
+                     "algorithmic_bytes_per_launch": B_g, "sm_mhz": clk_g.get("sm_mhz"),
+                     "traffic": profiled_traffic(args.workload + "-guided")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

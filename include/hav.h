@@ -71,7 +71,8 @@ typedef struct {
     int32_t layers;       /* k, 1..8 */
     int32_t layer_ratio;  /* budget ratio between consecutive layers, 1..64 */
     float aspect[3];      /* r: the voxel is v = s * r; each component finite, > 0 */
-    uint32_t flags;       /* 0, or HAV_FLAG_PHASE_TIMES (context calls only) */
+    uint32_t flags;       /* 0, or HAV_FLAG_PHASE_TIMES / HAV_FLAG_TEST_TIMEOUT
+                             (context calls only) */
     int32_t select;       /* representative of a voxel (Table 6 of Section 4.5):
                              HAV_SELECT_CENTRE_CLOSEST (the method, default),
                              HAV_SELECT_RANDOM, HAV_SELECT_MEAN, HAV_SELECT_CENTRE */
@@ -113,6 +114,14 @@ typedef struct {
 /* Record a device timestamp after every grid-wide phase of the call (for
  * profiling; read back with hav_phase_times_get). */
 #define HAV_FLAG_PHASE_TIMES 1u
+
+/* Test hook for the failure path of the bounded device waits: the call's
+ * first grid-wide barrier waits for one block more than the launch has, so
+ * every block gives up after the bounded wait (about 2 s), the call's output
+ * is void and its status is HAV_ERR_TIMEOUT.  Nothing faults or hangs; the
+ * context stays usable and its next call empties the tables first.  The
+ * levels run on the grid kernel whatever the context's cluster setting. */
+#define HAV_FLAG_TEST_TIMEOUT 2u
 
 /* One layer of one call, as the device evaluated it (for tests and the
  * roofline's algorithmic-byte count). */

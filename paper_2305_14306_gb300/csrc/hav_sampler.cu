@@ -515,7 +515,9 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 fill<unsigned long long>(d.tv, P.lay.tab_slots, kEmptyVal, gtid, gstride);
             }
             if (bucketing) fill<uint32_t>(d.bkt, 2 * 4096, 0u, gtid, gstride);
-            if (!grid_sync(d, nb, st, TAG(1, j, 0, 0))) return;
+            // (test hook: one arrival more than the launch has blocks never comes,
+            // so every block's bounded wait gives up and the call reports a timeout)
+            if (!grid_sync(d, nb + ((j == 0 && P.test_timeout) ? 1u : 0u), st, TAG(1, j, 0, 0))) return;
             if (j == 0 && blockIdx.x == 0 && tid == 0) *(volatile unsigned*)d.clean = 0u;
         }
 

@@ -91,6 +91,7 @@ EXPORTS = [
     "hav_spacing", "hav_ball_query",
 ]
 HAV_FLAG_PHASE_TIMES = 1
+HAV_FLAG_TEST_TIMEOUT = 2
 
 
 def _lib_or_none():

@@ -71,8 +71,8 @@ typedef struct {
     int32_t layers;       /* k, 1..8 */
     int32_t layer_ratio;  /* budget ratio between consecutive layers, 1..64 */
     float aspect[3];      /* r: the voxel is v = s * r; each component finite, > 0 */
-    uint32_t flags;       /* 0, or HAV_FLAG_PHASE_TIMES / HAV_FLAG_TEST_TIMEOUT
-                             (context calls only) */
+    uint32_t flags;       /* 0, or HAV_FLAG_PHASE_TIMES / HAV_FLAG_TEST_TIMEOUT /
+                             HAV_FLAG_TEST_TABLE_FULL (context calls only) */
     int32_t select;       /* representative of a voxel (Table 6 of Section 4.5):
                              HAV_SELECT_CENTRE_CLOSEST (the method, default),
                              HAV_SELECT_RANDOM, HAV_SELECT_MEAN, HAV_SELECT_CENTRE */
@@ -122,6 +122,13 @@ typedef struct {
  * context stays usable and its next call empties the tables first.  The
  * levels run on the grid kernel whatever the context's cluster setting. */
 #define HAV_FLAG_TEST_TIMEOUT 2u
+
+/* Test hook for the full-table path: the hash tables of segment 0 keep the
+ * smallest capacity (64 slots), so a first segment with more than 64
+ * occupied voxels reports HAV_ERR_TABLE_FULL (its probes end after one sweep
+ * of the table) and receives indices 0..m-1 like any segment in error; the
+ * other segments of the call are unaffected.  Grid kernel only. */
+#define HAV_FLAG_TEST_TABLE_FULL 4u
 
 /* One layer of one call, as the device evaluated it (for tests and the
  * roofline's algorithmic-byte count). */

@@ -45,7 +45,8 @@ hav_status check_params(const hav_params* p) {
     if (static_cast<long long>(p->sigma_num) > 64ll * p->sigma_den) return HAV_ERR_INVALID;
     for (int a = 0; a < 3; ++a)
         if (!(p->aspect[a] > 0.0f) || !std::isfinite(p->aspect[a])) return HAV_ERR_INVALID;
-    if ((p->flags & ~static_cast<uint32_t>(HAV_FLAG_PHASE_TIMES | HAV_FLAG_TEST_TIMEOUT)) != 0)
+    if ((p->flags & ~static_cast<uint32_t>(HAV_FLAG_PHASE_TIMES | HAV_FLAG_TEST_TIMEOUT |
+                                           HAV_FLAG_TEST_TABLE_FULL)) != 0)
         return HAV_ERR_INVALID;
     return havk::check_variant_params(p);
 }
@@ -231,6 +232,7 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
     plan->fixed_s = params->fixed_s;
     plan->search = params->search;
     plan->test_timeout = (params->flags & HAV_FLAG_TEST_TIMEOUT) ? 1 : 0;
+    plan->test_table_full = (params->flags & HAV_FLAG_TEST_TABLE_FULL) ? 1 : 0;
     for (int j = 0; j < num_levels; ++j) plan->out[j] = out_idx[j];
     if (params->flags & HAV_FLAG_PHASE_TIMES) {
         plan->ptimes = reinterpret_cast<unsigned long long*>(ctx->ws + ctx->lay.ptimes);
@@ -256,7 +258,8 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
         // levels from j0 on, where every segment has at most small_points points,
         // run on thread-block clusters; the phase timer stays with the grid kernel
         int j0 = num_levels;
-        if (ctx->small_points > 0 && !(params->flags & (HAV_FLAG_PHASE_TIMES | HAV_FLAG_TEST_TIMEOUT)) &&
+        if (ctx->small_points > 0 &&
+            !(params->flags & (HAV_FLAG_PHASE_TIMES | HAV_FLAG_TEST_TIMEOUT | HAV_FLAG_TEST_TABLE_FULL)) &&
             params->search == HAV_SEARCH_BISECT) {
             for (int j = 0; j < num_levels && j0 == num_levels; ++j) {
                 int64_t mx = 0;

@@ -172,7 +172,7 @@ struct Plan {
     int32_t keep_orig;           // write the last level's original indices (a cluster launch follows)
     int32_t search;              // HAV_SEARCH_*
     int32_t test_timeout;        // HAV_FLAG_TEST_TIMEOUT: the first barrier waits for a missing block
-    int32_t pad4;
+    int32_t test_table_full;     // HAV_FLAG_TEST_TABLE_FULL: segment 0's tables keep 64 slots
     int64_t off0[kMaxSegments + 1];       // level-0 segment offsets
     int32_t m[kMaxLevels][kMaxSegments];  // budgets per level and segment
 };

@@ -307,7 +307,9 @@ __device__ void level_setup(const Plan& P, int j, Smem& st) {
     if (s < S) {
         n = (j == 0) ? (P.off0[s + 1] - P.off0[s]) : P.m[j - 1][s];
         mm = P.m[j][s];
-        while ((1ll << lg) < 2 * n) ++lg;
+        // (test hook: segment 0's tables keep the smallest capacity)
+        if (!(P.test_table_full && s == 0))
+            while ((1ll << lg) < 2 * n) ++lg;
         C = 1ll << lg;
         st.n[s] = static_cast<int>(n);
         st.m[s] = static_cast<int>(mm);
@@ -1157,8 +1159,12 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             // --------------- cut-off: resolve; shortfall count; clean the tables
             {
                 int c = 0;
-                if (tid < S && (st.flags[tid] & F_ACTIVE) && st.kstar[tid] > st.ml[tid])
+                if (tid < S && (st.flags[tid] & F_ACTIVE) && st.kstar[tid] > st.ml[tid]) {
                     c = static_cast<int>(ld_volatile(reinterpret_cast<const int*>(&ls[tid].cand)));
+                    // only the first C/2 were stored (the rest reported a full table)
+                    const int cmax = 1 << (st.cap_log2[tid] - 1);
+                    if (c > cmax) c = cmax;
+                }
                 int ctot;
                 const int cpre = block_excl_scan<int>(tid < S ? c : 0, &ctot, st.scan_i);
                 if (tid < S) st.cprefix[tid] = cpre;

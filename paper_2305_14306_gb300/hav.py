@@ -92,6 +92,7 @@ EXPORTS = [
 ]
 HAV_FLAG_PHASE_TIMES = 1
 HAV_FLAG_TEST_TIMEOUT = 2
+HAV_FLAG_TEST_TABLE_FULL = 4
 
 
 def _lib_or_none():

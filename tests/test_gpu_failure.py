@@ -77,3 +77,41 @@ def test_timeout_on_a_batch_and_on_a_cluster_context(hv):
                 assert np.array_equal(got[cut[s]:cut[s + 1]], ora[s][0][0]), (tuning, s)
     finally:
         c.close()
+
+
+def test_full_table_is_reported_and_contained(hv):
+    # segment 0 keeps a 64-slot table: more than 64 occupied voxels fill it;
+    # the segment reports HAV_ERR_TABLE_FULL and takes indices 0..m-1, while the
+    # other segments of the same launch stay exact
+    sizes = [3000, 5000, 700, 12000]
+    clouds = [scenes.uniform_box(n, 40 + i) for i, n in enumerate(sizes)]
+    pts, offs = scenes.concat(clouds)
+    seg_m = np.array([[n // 4 for n in sizes], [n // 16 for n in sizes]], dtype=np.int64)
+    ora = G.oracle_many(clouds, [seg_m[:, s] for s in range(len(sizes))])
+    c = hv.Context(1 << 16, 8)
+    try:
+        outs = hv.hav_sample_batched(c, dev(pts), offs, seg_m, hv.params(flags=hv.HAV_FLAG_TEST_TABLE_FULL))
+        st, per = hv.hav_status_get(c, len(sizes))
+        assert st == hv.HAV_ERR_TABLE_FULL
+        assert list(per) == [hv.HAV_ERR_TABLE_FULL, 0, 0, 0]
+        for j in range(2):
+            cut = np.concatenate([[0], np.cumsum(seg_m[j])])
+            got = outs[j].cpu().numpy()
+            assert got[cut[0]:cut[1]].tolist() == list(range(int(seg_m[j, 0])))
+            for s in range(1, len(sizes)):
+                assert np.array_equal(got[cut[s]:cut[s + 1]], ora[s][0][j]), (j, s)
+        # a cloud that never has more than 64 occupied voxels is exact under the hook,
+        # and the context is exact again without it
+        tiny = scenes.uniform_box(50, 9)
+        out = hv.hav_sample_levels(c, dev(tiny), [10], hv.params(flags=hv.HAV_FLAG_TEST_TABLE_FULL))
+        assert hv.hav_status_get(c, 1)[0] == 0
+        assert np.array_equal(out[0].cpu().numpy(), G.oracle_many([tiny], [[10]])[0][0][0])
+        outs = hv.hav_sample_batched(c, dev(pts), offs, seg_m, hv.params())
+        assert hv.hav_status_get(c, len(sizes))[0] == 0
+        for j in range(2):
+            cut = np.concatenate([[0], np.cumsum(seg_m[j])])
+            got = outs[j].cpu().numpy()
+            for s in range(len(sizes)):
+                assert np.array_equal(got[cut[s]:cut[s + 1]], ora[s][0][j]), (j, s)
+    finally:
+        c.close()

@@ -97,7 +97,7 @@ struct Layout {
     size_t barrier, ghdr, seghdr, zero_bytes;  // [barrier, barrier+zero_bytes) zeroed per call
     size_t clean;          // 1 when every hash-table slot is empty (kept across calls)
     size_t lstate, hist, partial_sf, partial_cmp, pitem, trace, ptimes;
-    size_t ord[2], orig[2], taken[2], wpre, posof, dirty[kTableSets], bkt;
+    size_t ord[2], orig[2], taken[2], wpre, posof, dirty[kTableSets], bkt, prefix;
     size_t tabk[kTableSets], tabv, cand;
     size_t total;
 };
@@ -146,6 +146,7 @@ inline Layout make_layout(int64_t N, int32_t S, bool spec_room = true) {
     L.wpre = take(sizeof(uint32_t) * L.taken_words);
     L.posof = take(sizeof(int32_t) * N + 16);
     L.bkt = take(sizeof(uint32_t) * 2 * 4096);
+    L.prefix = take(sizeof(int32_t) * HAV_MAX_ITERS * S);
     for (int b = 0; b < kTableSets; ++b) L.tabk[b] = take(sizeof(unsigned long long) * L.tab_slots);
     L.tabv = take(sizeof(unsigned long long) * L.tab_slots);
     L.cand = take(sizeof(Cand) * L.cand_slots);

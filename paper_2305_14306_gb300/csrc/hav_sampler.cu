@@ -58,7 +58,7 @@ constexpr int kProbes = 2;         // global first probes issued together per th
 static_assert(kSetSlots % (kProbes * kThreads) == 0 && kSelSlots % (kProbes * kThreads) == 0,
               "flush loops take kProbes slots per thread per step");
 
-enum : int { F_ACTIVE = 1, F_SEARCH = 2, F_ACCEPT = 4, F_UP = 8 };
+enum : int { F_ACTIVE = 1, F_SEARCH = 2, F_ACCEPT = 4, F_UP = 8, F_PRE = 16 };
 
 struct Smem {
     // level layout
@@ -144,6 +144,7 @@ struct Dev {
     uint32_t* wpre;        // block-local prefix of taken bits per mask word
     uint32_t* dirty[kTableSets];  // fresh-insert logs, item-owned ranges of the level index space
     uint32_t* bkt;         // [2][4096] bucket counts, bucket cursors
+    int32_t* prefix;       // [S][kMaxIters] counts at s_hi / 2^(k+1) of this level (-1: none)
     unsigned long long* tk[kTableSets];
     unsigned long long* tv;
     Cand* cand;
@@ -417,6 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
     }
     d.wpre = reinterpret_cast<uint32_t*>(ws + P.lay.wpre);
     d.bkt = reinterpret_cast<uint32_t*>(ws + P.lay.bkt);
+    d.prefix = reinterpret_cast<int32_t*>(ws + P.lay.prefix);
     d.tv = reinterpret_cast<unsigned long long*>(ws + P.lay.tabv);
     d.cand = reinterpret_cast<Cand*>(ws + P.lay.cand);
     d.ptimes = P.ptimes;
@@ -508,6 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 __syncthreads();
             }
             fill<uint32_t>(taken, NL / 32 + 1, 0u, gtid, gstride);
+            fill<int32_t>(d.prefix, static_cast<long long>(S) * kMaxIters, -1, gtid, gstride);
             clear_layer_state(d, S, 0, gtid, gstride);
             clear_layer_state(d, S, 1, gtid, gstride);
             if (j == 0 && !st.was_clean) {
@@ -648,6 +651,34 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         fl |= F_UP;
                     }
                 }
+                // bisection: the leading steps whose outcome an earlier layer of this
+                // level settles (its count at the same size s_hi / 2^(k+1), on a
+                // superset of this layer's points, is below m_l) are taken without
+                // a pass; the trace keeps that count as a bound
+                int nskip = 0;
+                float hi_ff = st.s_hi[tid];
+                int32_t bnd[kMaxIters];
+                if ((fl & F_SEARCH) && P.search == HAV_SEARCH_BISECT) {
+                    fl |= F_PRE;
+                    const int* pre = d.prefix + tid * kMaxIters;
+#pragma unroll
+                    for (int k = 0; k < kMaxIters; ++k) bnd[k] = (k < P.t_max) ? ld_volatile(pre + k) : -1;
+                    while (nskip < P.t_max && bnd[nskip] >= 0 && bnd[nskip] < ml) {
+                        hi_ff = __fmul_rn(__fadd_rn(0.0f, hi_ff), 0.5f);
+                        ++nskip;
+                    }
+                    st.hi[tid] = hi_ff;
+                    st.iters[tid] = nskip;
+                    if (nskip >= P.t_max) {  // every step settled: no acceptance, s* = hi
+                        fl = F_ACTIVE;
+                        st.s_star[tid] = hi_ff;
+                        if (!make_grid(hi_ff, P.aspect, st.mn[tid], &st.grid[tid])) {
+                            seg_error(d, tid, HAV_ERR_RANGE);
+                            st.err[tid] = HAV_ERR_RANGE;
+                            fl = 0;
+                        }
+                    }
+                }
                 if (active && (P.t_max == 0 || fixed)) {
                     st.s_star[tid] = fixed ? P.fixed_s : st.s_hi[tid];
                     if (!make_grid(st.s_star[tid], P.aspect, st.mn[tid], &st.grid[tid])) {
@@ -663,10 +694,17 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     tr->k_max = kmax;
                     tr->k_star = 0;
                     tr->n_in = st.n[tid] - taken_before;
-                    tr->iters = 0;
+                    tr->iters = nskip;
                     tr->accepted = 0;
                     tr->s_hi = st.s_hi[tid];
-                    tr->s_star = 0.0f;
+                    tr->s_star = (nskip >= P.t_max && (fl & F_ACTIVE)) ? hi_ff : 0.0f;
+                    tr->bounded = nskip ? (0xffffffffu >> (32 - nskip)) : 0u;
+                    float h = st.s_hi[tid];
+                    for (int k = 0; k < nskip; ++k) {
+                        h = __fmul_rn(__fadd_rn(0.0f, h), 0.5f);
+                        tr->s[k] = h;
+                        tr->K[k] = bnd[k];
+                    }
                 }
                 taken_before += ml;
             }
@@ -876,6 +914,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 if (searching) {
                     float lo = st.lo[tid], hi = st.hi[tid];
                     bool up = (st.flags[tid] & F_UP) != 0;
+                    bool pre = (st.flags[tid] & F_PRE) != 0;  // every step so far too few
                     float first = st.first[tid];
                     int node = 0;
                     int t = st.iters[tid];
@@ -907,6 +946,10 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             tr->K[t] = K;
                             tr->iters = t + 1;
                         }
+                        if (pre) {  // sv = s_hi / 2^(t+1): later layers of the level may reuse K
+                            if (blockIdx.x == 0) d.prefix[tid * kMaxIters + t] = static_cast<int32_t>(K);
+                            if (K >= st.ml[tid]) pre = false;
+                        }
                         ++t;
                         if (K > st.kmax[tid]) {
                             lo = sv;
@@ -928,7 +971,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     st.hi[tid] = hi;
                     st.iters[tid] = t;
                     st.first[tid] = first;
-                    if (st.flags[tid] & F_SEARCH) st.flags[tid] = up ? (st.flags[tid] | F_UP) : (st.flags[tid] & ~F_UP);
+                    if (st.flags[tid] & F_SEARCH)
+                        st.flags[tid] = (st.flags[tid] & ~(F_UP | F_PRE)) | (up ? F_UP : 0) | (pre ? F_PRE : 0);
                     if ((st.flags[tid] & F_SEARCH) && t >= P.t_max) {
                         // no acceptance within t_max steps: set F is empty for this
                         // segment (emptied before this pass's arrival, or unused)

@@ -250,6 +250,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                     tr->n_in = n - taken_before;
                     tr->iters = 0;
                     tr->accepted = 0;
+                    tr->bounded = 0u;
                     tr->s_hi = sm.s_hi;
                     tr->s_star = 0.0f;
                 }

@@ -60,6 +60,8 @@ class hav_layer_trace(C.Structure):
         ("s_star", C.c_float),
         ("s", C.c_float * HAV_MAX_ITERS),
         ("K", C.c_int64 * HAV_MAX_ITERS),
+        ("bounded", C.c_uint32),
+        ("reserved", C.c_int32),
     ]
 
 
@@ -326,6 +328,7 @@ def hav_trace_get(ctx: Context, num_records: int, stream=None):
             "m_l": r.m_l, "k_max": r.k_max, "k_star": r.k_star, "n_in": r.n_in, "iters": it,
             "accepted": bool(r.accepted), "s_hi": np.float32(r.s_hi), "s_star": np.float32(r.s_star),
             "s": np.array(r.s[:it], dtype=np.float32), "K": np.array(r.K[:it], dtype=np.int64),
+            "bounded": int(r.bounded),
         })
     return out
 

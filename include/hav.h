@@ -111,11 +111,14 @@ typedef struct {
 #define HAV_SEARCH_BISECT 0
 #define HAV_SEARCH_GUIDED 1
 /* Under BISECT every layer of a level starts with the same sizes s_hi / 2,
- * s_hi / 4, ... while its counts stay below m_l.  A later layer's points are a
- * subset of an earlier layer's, so its count at such a size is at most the
- * earlier count; where that count is already below m_l the step's outcome is
- * known, and the layer takes it without a pass (hav_layer_trace.bounded).
- * The sizes, decisions and output are those of the plain bisection. */
+ * s_hi / 4, ... while its counts stay below m_l.  Two bounds settle such a
+ * step without a pass (hav_layer_trace.bounded): a later layer's points are a
+ * subset of an earlier layer's, so its count is at most the earlier layer's
+ * count at the same size; and no count exceeds the number of grid cells the
+ * bounding box spans, the product over the axes of
+ * floor(max / v) - floor(min / v) + 1.  Where the smaller bound is below m_l
+ * the step has too few voxels.  The sizes, decisions and output are those of
+ * the plain bisection. */
 
 /* Record a device timestamp after every grid-wide phase of the call (for
  * profiling; read back with hav_phase_times_get). */
@@ -152,10 +155,10 @@ typedef struct {
     int64_t K[HAV_MAX_ITERS];   /* occupied-voxel count at that s: exact, except
                                    for the steps in `bounded` */
     uint32_t bounded;           /* bit t: step t was decided without a count.  K[t]
-                                   is then an earlier layer's count of the same
-                                   level at the same s, on a superset of this
-                                   layer's points (so an upper bound), and it is
-                                   below m_l: the step has too few voxels */
+                                   is then an upper bound below m_l (an earlier
+                                   layer's count at the same s on a superset of
+                                   the points, or the grid cells the bounding box
+                                   spans): the step has too few voxels */
     int32_t reserved;
 } hav_layer_trace;
 

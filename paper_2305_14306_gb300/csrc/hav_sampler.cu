@@ -272,6 +272,24 @@ __device__ __forceinline__ unsigned bucket_of(const float p[3], const float mn[3
 // (lo, hi): the path from the root follows the bits of c + 1 below its
 // leading one (0: too few voxels, hi = s; 1: too many, lo = s), with the
 // same binary32 midpoint as the sequential search.
+// At most this many voxels are occupied at size s: the grid cells the
+// bounding box [mn, mx] spans, floor(mx / v) - floor(mn / v) + 1 per axis (the
+// floor of Eq. 2 is monotone in the coordinate).  LLONG_MAX when the grid is
+// not representable.
+__device__ __forceinline__ long long cell_bound(float s, const float r[3], const float mn[3], const float mx[3]) {
+    long long b = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float v = __fmul_rn(s, r[a]);
+        float f0, f1;
+        if (!(v > 0.0f) || !isfinite(v) || !floor_div(mn[a], v, &f0) || !floor_div(mx[a], v, &f1)) return LLONG_MAX;
+        const float u = __fsub_rn(f1, f0);
+        if (!(u >= 0.0f && u < 1048576.0f)) return LLONG_MAX;
+        b *= static_cast<long long>(u) + 1;
+    }
+    return b;
+}
+
 // The next size of a search with bracket (lo, hi): a pending first guess,
 // 2 lo while doubling up (guided start, F_UP), else the bisection midpoint.
 __device__ __forceinline__ float next_size(float lo, float hi, bool up, float first) {
@@ -651,10 +669,11 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         fl |= F_UP;
                     }
                 }
-                // bisection: the leading steps whose outcome an earlier layer of this
-                // level settles (its count at the same size s_hi / 2^(k+1), on a
-                // superset of this layer's points, is below m_l) are taken without
-                // a pass; the trace keeps that count as a bound
+                // bisection: the leading steps whose outcome is already settled are
+                // taken without a pass: at the size s_hi / 2^(k+1) either an earlier
+                // layer of this level counted fewer than m_l voxels on a superset of
+                // this layer's points, or the bounding box spans fewer than m_l grid
+                // cells.  The trace keeps the smaller bound
                 int nskip = 0;
                 float hi_ff = st.s_hi[tid];
                 int32_t bnd[kMaxIters];
@@ -663,8 +682,13 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     const int* pre = d.prefix + tid * kMaxIters;
 #pragma unroll
                     for (int k = 0; k < kMaxIters; ++k) bnd[k] = (k < P.t_max) ? ld_volatile(pre + k) : -1;
-                    while (nskip < P.t_max && bnd[nskip] >= 0 && bnd[nskip] < ml) {
-                        hi_ff = __fmul_rn(__fadd_rn(0.0f, hi_ff), 0.5f);
+                    while (nskip < P.t_max) {
+                        const float sv = __fmul_rn(__fadd_rn(0.0f, hi_ff), 0.5f);
+                        long long b = cell_bound(sv, P.aspect, st.mn[tid], st.mx[tid]);
+                        if (bnd[nskip] >= 0 && bnd[nskip] < b) b = bnd[nskip];
+                        if (!(b < ml)) break;
+                        bnd[nskip] = static_cast<int32_t>(b);
+                        hi_ff = sv;
                         ++nskip;
                     }
                     st.hi[tid] = hi_ff;

@@ -467,7 +467,9 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
         const bool bucketing = (j == 0 && S == 1 && NL >= kBucketMin);
 
         // ------------------------------------------------ bbox, layout, clears
-        {
+        // (a later level's box, masks and states were prepared by the previous
+        // level's compaction, which wrote its points)
+        if (j == 0) {
             const int par = j & 1;
             for (int it = blockIdx.x; it < st.items_total; it += nb) {
                 int a, b;
@@ -1443,10 +1445,13 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             }
             if (!last_level) {
                 float4* ord_out = d.ord[(j + 1) & 1];
+                const int npar = (j + 1) & 1;
                 for (int it = blockIdx.x; it < st.items_total; it += nb) {
                     int a, b;
                     const int s = item_range(st, S, it, &a, &b);
                     long long base = pre_item[it];
+                    // the next level's bounding box over the points kept here
+                    float mnv[3] = {INFINITY, INFINITY, INFINITY}, mxv[3] = {-INFINITY, -INFINITY, -INFINITY};
                     for (int i0 = a; i0 < b; i0 += kThreads) {
                         const int i = i0 + tid;
                         float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1464,10 +1469,45 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                                 ord_out[pos2] = make_float4(q4.x, q4.y, q4.z, __int_as_float(static_cast<int>(ng)));
                                 d.posof[ng] = static_cast<int32_t>(pos2);
                             }
+                            mnv[0] = fminf(mnv[0], q4.x);
+                            mnv[1] = fminf(mnv[1], q4.y);
+                            mnv[2] = fminf(mnv[2], q4.z);
+                            mxv[0] = fmaxf(mxv[0], q4.x);
+                            mxv[1] = fmaxf(mxv[1], q4.y);
+                            mxv[2] = fmaxf(mxv[2], q4.z);
                         }
                         base += tot;
                     }
+#pragma unroll
+                    for (int a3 = 0; a3 < 3; ++a3) {
+                        for (int o = 16; o > 0; o >>= 1) {
+                            mnv[a3] = fminf(mnv[a3], __shfl_xor_sync(0xffffffffu, mnv[a3], o));
+                            mxv[a3] = fmaxf(mxv[a3], __shfl_xor_sync(0xffffffffu, mxv[a3], o));
+                        }
+                    }
+                    if ((tid & 31) == 0) {
+                        for (int a3 = 0; a3 < 3; ++a3) {
+                            st.redf[a3][tid >> 5] = mnv[a3];
+                            st.redf[3 + a3][tid >> 5] = mxv[a3];
+                        }
+                    }
+                    __syncthreads();
+                    if (tid < 6) {
+                        float r = st.redf[tid][0];
+                        for (int w = 1; w < kThreads / 32; ++w)
+                            r = (tid < 3) ? fminf(r, st.redf[tid][w]) : fmaxf(r, st.redf[tid][w]);
+                        if (isfinite(r)) {
+                            if (tid < 3) atomicMax(&d.sh[s].bbox[npar][tid], ~enc_f(r));
+                            else atomicMax(&d.sh[s].bbox[npar][tid], enc_f(r));
+                        }
+                    }
+                    __syncthreads();
                 }
+                // the next level's taken mask, layer states and search prefix
+                fill<uint32_t>(d.taken[npar], st.m_total / 32 + 1, 0u, gtid, gstride);
+                fill<int32_t>(d.prefix, static_cast<long long>(S) * kMaxIters, -1, gtid, gstride);
+                clear_layer_state(d, S, 0, gtid, gstride);
+                clear_layer_state(d, S, 1, gtid, gstride);
                 if (!grid_sync(d, nb, st, TAG(8, j, 0, 0))) return;
             }
         }

@@ -205,7 +205,7 @@ typedef struct {
 } hav_tuning;
 
 /* Copy the context's tuning into *out (the defaults after creation:
- * {0, 16384, 262144}, 64, the co-resident maximum, 0, 0). */
+ * {0, 4096, 65536}, 64, the co-resident maximum, 0, 0). */
 hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out);
 
 /* Replace the context's tuning.  HAV_ERR_INVALID (and no change) on a value

@@ -31,11 +31,12 @@ constexpr int kMaxCand = (1 << kMaxSpecDepth) - 1;  // candidate sizes per pass 
 // set (p - 1) % 3 while it waits, ready for pass p + 2.
 constexpr int kTableSets = 3;
 // default level sizes (points) up to which a pass evaluates 4, 3 or 2 steps
-// ahead (measured on GB300: 15 candidates per pass never paid off; 7 pay up
-// to about 16k points, 3 up to 256k)
+// ahead (measured on GB300: 15 candidates per pass never paid off; with the
+// coarse steps settled without a pass, the passes left are near the target,
+// where 7 candidates pay up to about 4k points and 3 up to 64k)
 constexpr int64_t kSpecN4 = 0;
-constexpr int64_t kSpecN3 = 16384;
-constexpr int64_t kSpecN2 = 262144;
+constexpr int64_t kSpecN3 = 4096;
+constexpr int64_t kSpecN2 = 65536;
 constexpr int kChunkMin = 64;              // default smallest work item (points)
 constexpr int kSmallMax = 32768;           // largest level the cluster kernel takes (points)
 constexpr int kLocalItems = 8;             // work items one block can own in a level

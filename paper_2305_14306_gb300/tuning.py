@@ -26,10 +26,10 @@ import os
 import tempfile
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hav_tuning.json")
-BASE_SPEC = (0, 16384, 262144)
+BASE_SPEC = (0, 4096, 65536)
 # speculation thresholds tried (depth 4 up to [0], 3 up to [1], 2 up to [2] points)
 SPEC_CHOICES = (
-    (0, 0, 0), (0, 0, 65536), (0, 0, 262144), (0, 8192, 131072), (0, 16384, 262144),
+    (0, 0, 0), (0, 4096, 65536), (0, 0, 65536), (0, 0, 262144), (0, 8192, 131072), (0, 16384, 262144),
     (0, 32768, 262144), (0, 65536, 524288), (8192, 16384, 262144), (32768, 131072, 262144),
 )
 CHUNK_MINS = (32, 64, 128, 256, 512, 1024)

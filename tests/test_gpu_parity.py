@@ -292,7 +292,7 @@ def test_tuning_never_changes_results(hv):
             assert len(got_b[3]) == len(ref_b[3]) and len(got_c[2]) == len(ref_c[2])
             for x, y in zip(got_b[3] + got_c[2], ref_b[3] + ref_c[2]):
                 assert G.traces_equal(x, y) is None, (t, G.traces_equal(x, y))
-            c.set_tuning(spec_points=[0, 16384, 262144], chunk_min=64, nblocks=0)
+            c.set_tuning(spec_points=[0, 4096, 65536], chunk_min=64, nblocks=0)
         assert c.get_tuning()["chunk_min"] == 64
         with pytest.raises(hv.HavError):
             c.set_tuning(spec_points=[3, 2, 1])

@@ -201,11 +201,18 @@ typedef struct {
                                 thread-block clusters, one cluster of 8 SMs per
                                 segment, the voxel table in distributed shared
                                 memory (same results; plain bisection) */
-    int32_t reserved;        /* 0 */
+    int32_t solo_points;     /* levels whose every segment has at most this many
+                                points (0..4096; 0: none; default 4096) run on
+                                single CTAs, one per segment, its points and
+                                voxel table in the CTA's shared memory and each
+                                phase ended by a block barrier (same results;
+                                plain bisection; used when search is BISECT,
+                                select CENTRE_CLOSEST or RANDOM and no flag is
+                                set, and small_points does not apply) */
 } hav_tuning;
 
 /* Copy the context's tuning into *out (the defaults after creation:
- * {0, 4096, 65536}, 64, the co-resident maximum, 0, 0). */
+ * {0, 4096, 65536}, 64, the co-resident maximum, 0, 4096). */
 hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out);
 
 /* Replace the context's tuning.  HAV_ERR_INVALID (and no change) on a value

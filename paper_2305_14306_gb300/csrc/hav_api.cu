@@ -19,6 +19,8 @@ struct hav_ctx {
     int64_t spec_n[3];
     int small_nc;      // clusters of the small-level kernel that fit at once (0: none)
     int small_points;  // largest level run on clusters (0: never)
+    int solo_ok;       // the single-CTA kernel can be launched
+    int solo_points;   // largest level run on single CTAs (0: never)
     int fps_nblocks;
     havk::Layout lay;
     unsigned char* ws;
@@ -115,6 +117,8 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
         cudaGetLastError();
         c->small_nc = snc > 0 ? snc : 0;
         c->small_points = 0;  // measured no faster than the grid kernel on GB300: opt-in
+        c->solo_ok = (snc >= 0) ? 1 : 0;
+        c->solo_points = c->solo_ok ? havk::kSoloMax : 0;
     }
     c->spec_n[0] = havk::kSpecN4;
     c->spec_n[1] = havk::kSpecN3;
@@ -146,7 +150,7 @@ hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out) {
     out->chunk_min = ctx->chunk_min;
     out->nblocks = ctx->nblocks;
     out->small_points = ctx->small_points;
-    out->reserved = 0;
+    out->solo_points = ctx->solo_points;
     return HAV_OK;
 }
 
@@ -157,9 +161,12 @@ hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t) {
     if (t->spec_points[0] > t->spec_points[1] || t->spec_points[1] > t->spec_points[2]) return HAV_ERR_INVALID;
     if (t->chunk_min < 1 || t->chunk_min > 65536) return HAV_ERR_INVALID;
     if (t->nblocks < 0 || t->nblocks > ctx->max_blocks) return HAV_ERR_INVALID;
-    if (t->small_points < 0 || t->small_points > havk::kSmallMax || t->reserved != 0) return HAV_ERR_INVALID;
+    if (t->small_points < 0 || t->small_points > havk::kSmallMax) return HAV_ERR_INVALID;
+    if (t->solo_points < 0 || t->solo_points > havk::kSoloMax) return HAV_ERR_INVALID;
+    if (t->solo_points > 0 && !ctx->solo_ok) return HAV_ERR_INVALID;
     if (t->small_points > 0 && ctx->small_nc == 0) return HAV_ERR_INVALID;  // no cluster launch on this device
     ctx->small_points = t->small_points;
+    ctx->solo_points = t->solo_points;
     for (int k = 0; k < 3; ++k) ctx->spec_n[k] = t->spec_points[k];
     ctx->chunk_min = t->chunk_min;
     ctx->nblocks = t->nblocks == 0 ? ctx->max_blocks : t->nblocks;
@@ -256,21 +263,29 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
         ret = HAV_ERR_CUDA;
     } else if (any_m > 0) {
         // levels from j0 on, where every segment has at most small_points points,
-        // run on thread-block clusters; the phase timer stays with the grid kernel
-        int j0 = num_levels;
-        if (ctx->small_points > 0 &&
-            !(params->flags & (HAV_FLAG_PHASE_TIMES | HAV_FLAG_TEST_TIMEOUT | HAV_FLAG_TEST_TABLE_FULL)) &&
-            params->search == HAV_SEARCH_BISECT) {
-            for (int j = 0; j < num_levels && j0 == num_levels; ++j) {
+        // run on thread-block clusters, or else, where every segment has at most
+        // solo_points points, on single CTAs.  Both run the plain bisection;
+        // the phase timer and the test hooks stay with the grid kernel, and so
+        // do the calls whose representatives need the grid kernel's tables.
+        const bool small_ok =
+            params->flags == 0 && params->search == HAV_SEARCH_BISECT &&
+            (params->select == HAV_SELECT_CENTRE_CLOSEST || params->select == HAV_SELECT_RANDOM);
+        auto first_level_within = [&](int64_t limit) {
+            for (int j = 0; j < num_levels; ++j) {
                 int64_t mx = 0;
                 for (int s = 0; s < num_segments; ++s) {
                     const int64_t nj = (j == 0) ? seg_offsets[s + 1] - seg_offsets[s]
                                                 : seg_m[static_cast<int64_t>(j - 1) * num_segments + s];
                     if (nj > mx) mx = nj;
                 }
-                if (mx <= ctx->small_points) j0 = j;
+                if (mx <= limit) return j;
             }
-        }
+            return num_levels;
+        };
+        int j0 = num_levels, j1 = num_levels;
+        if (small_ok && ctx->small_points > 0) j0 = first_level_within(ctx->small_points);
+        if (small_ok && j0 == num_levels && ctx->solo_points > 0) j1 = first_level_within(ctx->solo_points);
+        if (j1 < j0) j0 = j1;
         if (j0 > 0) {
             plan->L = j0;
             plan->keep_orig = (j0 < num_levels) ? 1 : 0;
@@ -279,10 +294,14 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
             plan->keep_orig = 0;
         }
         if (ret == HAV_OK && j0 < num_levels) {
-            int nc = plan->nblocks / 8;
-            if (nc > ctx->small_nc) nc = ctx->small_nc;
-            if (nc < 1) nc = 1;
-            if (havk::launch_small(*plan, j0, nc, strm) != 0) ret = HAV_ERR_CUDA;
+            if (j0 == j1) {
+                if (havk::launch_solo(*plan, j0, plan->nblocks, strm) != 0) ret = HAV_ERR_CUDA;
+            } else {
+                int nc = plan->nblocks / 8;
+                if (nc > ctx->small_nc) nc = ctx->small_nc;
+                if (nc < 1) nc = 1;
+                if (havk::launch_small(*plan, j0, nc, strm) != 0) ret = HAV_ERR_CUDA;
+            }
         }
     }
     delete plan;

@@ -115,6 +115,24 @@ __device__ __forceinline__ bool cell_key(const float p[3], const Grid& g, unsign
     return true;
 }
 
+// At most this many voxels are occupied at size s: the grid cells the
+// bounding box [mn, mx] spans, floor(mx / v) - floor(mn / v) + 1 per axis (the
+// floor of Eq. 2 is monotone in the coordinate).  LLONG_MAX when the grid is
+// not representable.
+__device__ __forceinline__ long long cell_bound(float s, const float r[3], const float mn[3], const float mx[3]) {
+    long long b = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float v = __fmul_rn(s, r[a]);
+        float f0, f1;
+        if (!(v > 0.0f) || !isfinite(v) || !floor_div(mn[a], v, &f0) || !floor_div(mx[a], v, &f1)) return LLONG_MAX;
+        const float u = __fsub_rn(f1, f0);
+        if (!(u >= 0.0f && u < 1048576.0f)) return LLONG_MAX;
+        b *= static_cast<long long>(u) + 1;
+    }
+    return b;
+}
+
 // Section 3.2: squared distance to the voxel centre v * (g + 0.5).
 __device__ __forceinline__ float centre_d2(const float p[3], const Grid& g, const float f[3]) {
     float d[3];

@@ -201,6 +201,9 @@ int fps_coresident_blocks(int device);
 // once (<= 0: none), and a launch of levels [first_level, plan.L).
 int small_clusters(int device);
 int launch_small(const Plan& plan, int first_level, int nclusters, cudaStream_t stream);
+// The same on single CTAs (one per segment), for levels of at most kSoloMax points.
+constexpr int kSoloMax = 4096;
+int launch_solo(const Plan& plan, int first_level, int nblocks, cudaStream_t stream);
 // Grouping around centres (hav_group.cu).
 int launch_ball_query(const float* points, long long n, const int32_t* centres, long long m, float radius,
                       int nsample, int32_t* out_idx, float* out_xyz, unsigned char* ws, const Layout& lay,

@@ -272,24 +272,6 @@ __device__ __forceinline__ unsigned bucket_of(const float p[3], const float mn[3
 // (lo, hi): the path from the root follows the bits of c + 1 below its
 // leading one (0: too few voxels, hi = s; 1: too many, lo = s), with the
 // same binary32 midpoint as the sequential search.
-// At most this many voxels are occupied at size s: the grid cells the
-// bounding box [mn, mx] spans, floor(mx / v) - floor(mn / v) + 1 per axis (the
-// floor of Eq. 2 is monotone in the coordinate).  LLONG_MAX when the grid is
-// not representable.
-__device__ __forceinline__ long long cell_bound(float s, const float r[3], const float mn[3], const float mx[3]) {
-    long long b = 1;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float v = __fmul_rn(s, r[a]);
-        float f0, f1;
-        if (!(v > 0.0f) || !isfinite(v) || !floor_div(mn[a], v, &f0) || !floor_div(mx[a], v, &f1)) return LLONG_MAX;
-        const float u = __fsub_rn(f1, f0);
-        if (!(u >= 0.0f && u < 1048576.0f)) return LLONG_MAX;
-        b *= static_cast<long long>(u) + 1;
-    }
-    return b;
-}
-
 // The next size of a search with bracket (lo, hi): a pending first guess,
 // 2 lo while doubling up (guided start, F_UP), else the bisection midpoint.
 __device__ __forceinline__ float next_size(float lo, float hi, bool up, float first) {

@@ -1,19 +1,21 @@
-// Small levels on thread-block clusters.
+// Small levels on thread-block clusters, and on single CTAs.
 //
 // The same sampler as hav_chain_kernel (Sections 3.2-3.4 and Eq. 3, with the
-// same readings), for levels of at most kSmallMax points: one cluster of kQ
+// same readings), for levels of at most Q * 4,096 points: one cluster of Q
 // CTAs per segment, the voxel table spread over the CTAs' shared memory and
 // reached through distributed shared memory, phases separated by the cluster
-// barrier.  An exchange between SMs then costs a few hundred cycles instead
+// barrier.  With Q = 1 a segment's level lives in one CTA: every exchange is
+// a shared-memory access and every phase ends with a block barrier.  An
+// exchange between SMs then costs a few hundred cycles instead
 // of an L2 round trip across the chip, and a phase ends with a hardware
 // cluster barrier instead of a grid barrier: on levels of tens of thousands
 // of points the grid-wide kernel pays for that latency, not for work.  The
 // search is the plain bisection (one size per pass), so every evaluated size
 // and count is the paper's.
 //
-// Inside a cluster, CTA r holds the level's points [n r / kQ, n (r + 1) / kQ)
+// Inside a cluster, CTA r holds the level's points [n r / Q, n (r + 1) / Q)
 // (level indices, ascending) in shared memory with their taken flags.  The
-// voxel table has max(nextpow2(2 n), 64 kQ) slots: key k lives in CTA
+// voxel table has max(nextpow2(2 n), 64 Q) slots: key k lives in CTA
 // owner(k) (the top bits of slot_mix(k)), at the next bits inside that CTA's
 // part, with linear probing inside the part.  A level's points are read from
 // the original cloud through the ascending original indices of the level
@@ -31,11 +33,14 @@ namespace cg = cooperative_groups;
 namespace havk {
 namespace {
 
-constexpr int kQ = 8;  // CTAs per cluster
-constexpr int kQLog2 = 3;
-constexpr int kST = 1024;  // threads per CTA
-constexpr int kPtsPerCta = kSmallMax / kQ;
-constexpr int kPartMax = 2 * kSmallMax / kQ;  // table slots per CTA at most
+constexpr int kST = 1024;         // threads per CTA
+constexpr int kPtsPerCta = 4096;  // level points one CTA holds
+constexpr int kPartMax = 2 * kPtsPerCta;  // table slots per CTA at most
+static_assert(kSmallMax == 8 * kPtsPerCta, "the 8-CTA cluster takes kSmallMax points");
+template <int Q>
+__host__ __device__ constexpr int qlog2() {
+    return Q == 8 ? 3 : (Q == 4 ? 2 : (Q == 2 ? 1 : 0));
+}
 constexpr size_t kSmallDyn = static_cast<size_t>(kPartMax) * 16 + static_cast<size_t>(kPtsPerCta) * 16 +
                              static_cast<size_t>(kPtsPerCta) + 4 * kHistBins;
 static_assert(kHistBins == kST, "one histogram bin per thread");
@@ -49,35 +54,63 @@ struct SmallSmem {
     unsigned ncand;             // boundary-bin candidates appended
     uint32_t box[6];            // bounding box codes of the level
     int nonfinite;
-    int part_cnt[kQ];  // per-CTA counts for prefixes (shortfall, compaction)
+    int part_cnt[8];   // per-CTA counts for prefixes (shortfall, compaction)
     // this CTA's
-    float mn[3], s_hi;
+    float mn[3], mx[3], s_hi;
+    int pre[kMaxIters];         // counts at s_hi / 2^(k+1) of this level's earlier layers (-1: none)
+    unsigned acc_cnt, acc_err;  // this CTA's pass totals
     int cut_bin, cut_below;
-    unsigned long long red_u[32];
     int red_i[32];
     float redf[6][32];
     int flag;
 };
 
-__device__ __forceinline__ int part_start(long long n, int r) { return static_cast<int>((n * r) / kQ); }
+template <int Q>
+__device__ __forceinline__ int part_start(long long n, int r) {
+    return static_cast<int>((n * r) / Q);
+}
 
+template <int Q>
 __device__ __forceinline__ int point_owner(long long n, int g) {
-    int r = (n > 0) ? static_cast<int>((static_cast<long long>(g) * kQ) / n) : 0;
-    if (r > kQ - 1) r = kQ - 1;
-    while (r > 0 && part_start(n, r) > g) --r;
-    while (r + 1 < kQ && part_start(n, r + 1) <= g) ++r;
+    int r = (n > 0) ? static_cast<int>((static_cast<long long>(g) * Q) / n) : 0;
+    if (r > Q - 1) r = Q - 1;
+    while (r > 0 && part_start<Q>(n, r) > g) --r;
+    while (r + 1 < Q && part_start<Q>(n, r + 1) <= g) ++r;
     return r;
+}
+
+// CTA r's copy of a shared-memory variable (this CTA's own when Q = 1).
+template <int Q, typename T>
+__device__ __forceinline__ T* at_rank(cg::cluster_group& cl, T* p, int r) {
+    if constexpr (Q == 1) {
+        (void)cl;
+        (void)r;
+        return p;
+    } else {
+        return cl.map_shared_rank(p, r);
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void csync(cg::cluster_group& cl) {
+    if constexpr (Q == 1) {
+        (void)cl;
+        __syncthreads();
+    } else {
+        cl.sync();
+    }
 }
 
 // Insert `key` into the cluster table: the slot inside the owner's part, or
 // -1 when the part is full; *fresh when this call inserted it.
+template <int Q>
 __device__ __forceinline__ int dsm_insert(cg::cluster_group& cl, unsigned long long* keys_local, int part_log2,
                                           unsigned long long key, int* owner_out, bool* fresh) {
     const unsigned long long h = slot_mix(key);
-    const int owner = static_cast<int>(h >> (64 - kQLog2));
-    unsigned long long* part = cl.map_shared_rank(keys_local, owner);
+    const int owner = (Q == 1) ? 0 : static_cast<int>(h >> (64 - qlog2<Q>()));
+    unsigned long long* part = at_rank<Q>(cl, keys_local, owner);
     const unsigned mask = (1u << part_log2) - 1u;
-    unsigned slot = static_cast<unsigned>(h >> (64 - kQLog2 - part_log2)) & mask;
+    unsigned slot = static_cast<unsigned>(h >> (64 - qlog2<Q>() - part_log2)) & mask;
     *owner_out = owner;
     *fresh = false;
     for (unsigned probe = 0; probe <= mask; ++probe) {
@@ -94,24 +127,32 @@ __device__ __forceinline__ int dsm_insert(cg::cluster_group& cl, unsigned long l
 
 // 64-bit minimum in another CTA's shared memory with compare-and-swap (the
 // operation the table inserts use): every failed attempt saw a smaller
-// value, so the loop ends after at most as many attempts as writers.
+// value, so the loop ends after at most as many attempts as writers.  In
+// the CTA's own shared memory (Q = 1) the atomic minimum itself.
+template <int Q>
 __device__ __forceinline__ void dsm_min(unsigned long long* p, unsigned long long v) {
     unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(p);
-    while (v < cur) {
-        const unsigned long long prev = atomicCAS(p, cur, v);
-        if (prev == cur) break;
-        cur = prev;
+    if constexpr (Q == 1) {
+        if (v < cur) atomicMin(p, v);
+    } else {
+        while (v < cur) {
+            const unsigned long long prev = atomicCAS(p, cur, v);
+            if (prev == cur) break;
+            cur = prev;
+        }
     }
 }
 
-__device__ __forceinline__ unsigned long long block_sum_ull(unsigned long long v, unsigned long long* scratch) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+// This CTA's total of `local` and OR of `ebits` into acc_cnt / acc_err
+// (cleared before the pass): one atomic per warp, one block barrier.
+__device__ __forceinline__ void block_count(unsigned local, unsigned ebits, unsigned* acc_cnt, unsigned* acc_err) {
+    const unsigned c = __reduce_add_sync(0xffffffffu, local);
+    const unsigned e = __reduce_or_sync(0xffffffffu, ebits);
+    if ((threadIdx.x & 31) == 0) {
+        if (c) atomicAdd(acc_cnt, c);
+        if (e) atomicOr(acc_err, e);
+    }
     __syncthreads();
-    unsigned long long t = 0;
-    for (int k = 0; k < kST / 32; ++k) t += scratch[k];
-    __syncthreads();
-    return t;
 }
 
 __device__ __forceinline__ void seg_fail(SegHdr* sh, GlobalHdr* gh, int seg, int code) {
@@ -121,7 +162,8 @@ __device__ __forceinline__ void seg_fail(SegHdr* sh, GlobalHdr* gh, int seg, int
 
 // Levels [first_level, P.L) of every segment; level first_level > 0 reads its
 // input through orig[(first_level - 1) & 1].
-__global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
+template <int Q>
+__global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
     hav_small_kernel(const __grid_constant__ Plan P, int first_level) {
     cg::cluster_group cl = cg::this_cluster();
     __shared__ SmallSmem sm;
@@ -134,9 +176,9 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
 
     const int tid = threadIdx.x;
     const int rank = static_cast<int>(cl.block_rank());
-    const int cluster_id = blockIdx.x / kQ;
-    const int nclusters = gridDim.x / kQ;
-    SmallSmem* sm0 = cl.map_shared_rank(&sm, 0);
+    const int cluster_id = blockIdx.x / Q;
+    const int nclusters = gridDim.x / Q;
+    SmallSmem* sm0 = at_rank<Q>(cl, &sm, 0);
     unsigned char* ws = P.ws;
     SegHdr* sh = reinterpret_cast<SegHdr*>(ws + P.lay.seghdr);
     GlobalHdr* gh = reinterpret_cast<GlobalHdr*>(ws + P.lay.ghdr);
@@ -157,7 +199,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                 obase += P.m[j][s2];
                 ibase += (j == 0) ? 0 : P.m[j - 1][s2];
             }
-            const int a = part_start(n, rank), b = part_start(n, rank + 1);
+            const int a = part_start<Q>(n, rank), b = part_start<Q>(n, rank + 1);
             const int L = b - a;
 
             // --------------------------------------------- points and bbox
@@ -168,7 +210,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                 }
                 sm.nonfinite = 0;
             }
-            cl.sync();
+            csync<Q>(cl);
             float mnv[3] = {INFINITY, INFINITY, INFINITY}, mxv[3] = {-INFINITY, -INFINITY, -INFINITY};
             int bad = 0;
             for (int i = tid; i < L; i += kST) {
@@ -201,7 +243,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                 if (isfinite(r)) atomicMax(&sm0->box[tid], (tid < 3) ? ~enc_f(r) : enc_f(r));
             }
             if (tid == 0 && bad) atomicExch(&sm0->nonfinite, 1);
-            cl.sync();
+            csync<Q>(cl);
             // the bracket (0, s_hi] of Section 3.3 from CTA 0's box, in every CTA
             if (tid == 0) {
                 const int nf = sm0->nonfinite;
@@ -210,6 +252,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                     float lo = dec_f(~sm0->box[k]), hi = dec_f(sm0->box[3 + k]);
                     if (n == 0 || nf || err) lo = hi = 0.0f;
                     sm.mn[k] = lo;
+                    sm.mx[k] = hi;
                     if (j == 0 && rank == 0) {
                         sh[seg].bbox[0][k] = sm0->box[k];
                         sh[seg].bbox[0][3 + k] = sm0->box[3 + k];
@@ -220,6 +263,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                 sm.s_hi = s_hi;
                 sm.flag = nf;
             }
+            if (tid < kMaxIters) sm.pre[tid] = -1;
             __syncthreads();
             if (!err && sm.flag) {
                 err = HAV_ERR_NONFINITE;
@@ -232,7 +276,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
 
             int part_log2 = kMinCapLog2;
             while ((1ll << part_log2) < 2 * n) ++part_log2;
-            part_log2 -= kQLog2;
+            part_log2 -= qlog2<Q>();
             if (part_log2 < kMinCapLog2) part_log2 = kMinCapLog2;
             const int part = 1 << part_log2;
 
@@ -262,8 +306,30 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                 bool accepted = false;
                 const int steps = fixed ? 0 : P.t_max;
 
+                // The leading steps settled by an exact bound below m_l are taken
+                // without a pass, as in the grid kernel: the grid cells the
+                // bounding box spans, or an earlier layer's count at the same size
+                // s_hi / 2^(t+1) on a superset of the points; the trace keeps the
+                // smaller bound
+                int t0 = 0;
+                while (t0 < steps) {
+                    const float sv = __fmul_rn(__fadd_rn(0.0f, hi), 0.5f);
+                    long long bd = cell_bound(sv, P.aspect, sm.mn, sm.mx);
+                    if (sm.pre[t0] >= 0 && sm.pre[t0] < bd) bd = sm.pre[t0];
+                    if (!(bd < ml)) break;
+                    if (write_tr) {
+                        tr->s[t0] = sv;
+                        tr->K[t0] = bd;
+                        tr->iters = t0 + 1;
+                        tr->bounded |= 1u << t0;
+                    }
+                    hi = sv;
+                    ++t0;
+                }
+                bool pre = true;  // every step so far had too few voxels
+
                 // Section 3.3 bisection, one size per pass
-                for (int t = 0; t < steps; ++t) {
+                for (int t = t0; t < steps; ++t) {
                     const float sv = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
                     Grid G;
                     const bool gok = make_grid(sv, P.aspect, sm.mn, &G);
@@ -273,8 +339,12 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                         sm.cnt[pass_no % 3] = 0ull;
                         sm.perr[pass_no % 3] = 0u;
                     }
-                    cl.sync();
-                    unsigned long long local = 0;
+                    if (tid == 0) {
+                        sm.acc_cnt = 0u;
+                        sm.acc_err = 0u;
+                    }
+                    csync<Q>(cl);
+                    unsigned local = 0;
                     unsigned ebits = gok ? 0u : 1u;
                     if (gok) {
                         for (int i = tid; i < L; i += kST) {
@@ -289,18 +359,16 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                             }
                             int owner;
                             bool fr;
-                            if (dsm_insert(cl, keys, part_log2, key, &owner, &fr) < 0) ebits |= 2u;
+                            if (dsm_insert<Q>(cl, keys, part_log2, key, &owner, &fr) < 0) ebits |= 2u;
                             else if (fr) ++local;
                         }
                     }
-                    const unsigned long long tot = block_sum_ull(local, sm.red_u);
-                    const unsigned e1 = __syncthreads_or(ebits & 1u) ? 1u : 0u;
-                    const unsigned e2 = __syncthreads_or(ebits & 2u) ? 2u : 0u;
+                    block_count(local, ebits, &sm.acc_cnt, &sm.acc_err);
                     if (tid == 0) {
-                        if (tot) atomicAdd(&sm0->cnt[pass_no % 3], tot);
-                        if (e1 | e2) atomicOr(&sm0->perr[pass_no % 3], e1 | e2);
+                        if (sm.acc_cnt) atomicAdd(&sm0->cnt[pass_no % 3], static_cast<unsigned long long>(sm.acc_cnt));
+                        if (sm.acc_err) atomicOr(&sm0->perr[pass_no % 3], sm.acc_err);
                     }
-                    cl.sync();
+                    csync<Q>(cl);
                     const long long K = static_cast<long long>(sm0->cnt[pass_no % 3]);
                     const unsigned eb = sm0->perr[pass_no % 3];
                     ++pass_no;
@@ -308,6 +376,10 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                         tr->s[t] = sv;
                         tr->K[t] = K;
                         tr->iters = t + 1;
+                    }
+                    if (pre) {  // sv = s_hi / 2^(t+1): later layers of the level may reuse K
+                        if (tid == 0) sm.pre[t] = static_cast<int>(K);
+                        if (K >= ml) pre = false;
                     }
                     if (eb) {
                         err = (eb & 1u) ? HAV_ERR_RANGE : HAV_ERR_TABLE_FULL;
@@ -344,11 +416,15 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                     sm.errbits = 0u;
                     sm.ncand = 0u;
                 }
-                cl.sync();
+                if (tid == 0) {
+                    sm.acc_cnt = 0u;
+                    sm.acc_err = 0u;
+                }
+                csync<Q>(cl);
                 {
-                    unsigned long long local = 0;
+                    unsigned local = 0;
                     unsigned ebits = 0;
-                    uint32_t* hist0 = cl.map_shared_rank(hist, 0);
+                    uint32_t* hist0 = at_rank<Q>(cl, hist, 0);
                     for (int i = tid; i < L; i += kST) {
                         if (taken[i]) continue;
                         const float4 q = pts[i];
@@ -368,26 +444,24 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                             (static_cast<unsigned long long>(word) << 32) | static_cast<unsigned>(g);
                         int owner;
                         bool fr;
-                        const int slot = dsm_insert(cl, keys, part_log2, key, &owner, &fr);
+                        const int slot = dsm_insert<Q>(cl, keys, part_log2, key, &owner, &fr);
                         if (slot < 0) {
                             ebits |= 2u;
                             continue;
                         }
-                        dsm_min(cl.map_shared_rank(vals, owner) + slot, packed);
+                        dsm_min<Q>(at_rank<Q>(cl, vals, owner) + slot, packed);
                         if (fr) {
                             ++local;
                             atomicAdd(hist0 + static_cast<int>(priority(key) >> (64 - kHistBits)), 1u);
                         }
                     }
-                    const unsigned long long tot = block_sum_ull(local, sm.red_u);
-                    const unsigned e1 = __syncthreads_or(ebits & 1u) ? 1u : 0u;
-                    const unsigned e2 = __syncthreads_or(ebits & 2u) ? 2u : 0u;
+                    block_count(local, ebits, &sm.acc_cnt, &sm.acc_err);
                     if (tid == 0) {
-                        if (tot) atomicAdd(&sm0->kstar, tot);
-                        if (e1 | e2) atomicOr(&sm0->errbits, e1 | e2);
+                        if (sm.acc_cnt) atomicAdd(&sm0->kstar, static_cast<unsigned long long>(sm.acc_cnt));
+                        if (sm.acc_err) atomicOr(&sm0->errbits, sm.acc_err);
                     }
                 }
-                cl.sync();
+                csync<Q>(cl);
                 const long long kstar = static_cast<long long>(sm0->kstar);
                 {
                     const unsigned eb = sm0->errbits;
@@ -408,7 +482,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                 Cand* cand = cand_all + 2 * P.off0[seg];  // room for 2 n entries of this segment
                 if (cut) {
                     // boundary bin: smallest b with (voxels in bins <= b) >= m_l
-                    const int v = static_cast<int>(cl.map_shared_rank(hist, 0)[tid]);
+                    const int v = static_cast<int>(at_rank<Q>(cl, hist, 0)[tid]);
                     int total;
                     const int before = block_excl_scan<int>(v, &total, sm.red_i);
                     if (before < ml && before + v >= ml) {
@@ -436,26 +510,26 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                         }
                     }
                     if (take) {
-                        const int r = point_owner(n, g);
-                        cl.map_shared_rank(taken, r)[g - part_start(n, r)] = 1;
+                        const int r = point_owner<Q>(n, g);
+                        at_rank<Q>(cl, taken, r)[g - part_start<Q>(n, r)] = 1;
                     }
                 }
-                cl.sync();
+                csync<Q>(cl);
                 if (cut) {
                     // the boundary bin's candidates ranked exactly; the r smallest priorities are taken
                     const int c = static_cast<int>(sm0->ncand);
                     const int r = static_cast<int>(ml) - sm.cut_below;
-                    for (int f = rank * kST + tid; f < c; f += kQ * kST) {
+                    for (int f = rank * kST + tid; f < c; f += Q * kST) {
                         const unsigned long long hf = cand[f].h;
                         int rk = 0;
                         for (int k = 0; k < c; ++k) rk += (cand[k].h < hf) ? 1 : 0;
                         if (rk < r) {
                             const int g = static_cast<int>(cand[f].g);
-                            const int owner = point_owner(n, g);
-                            cl.map_shared_rank(taken, owner)[g - part_start(n, owner)] = 1;
+                            const int owner = point_owner<Q>(n, g);
+                            at_rank<Q>(cl, taken, owner)[g - part_start<Q>(n, owner)] = 1;
                         }
                     }
-                    cl.sync();
+                    csync<Q>(cl);
                 } else if (kstar < ml) {
                     // shortfall: untaken points in ascending level index until m_l
                     int cnt = 0;
@@ -463,7 +537,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                     int tot;
                     block_excl_scan<int>(cnt, &tot, sm.red_i);
                     if (tid == 0) sm0->part_cnt[rank] = tot;
-                    cl.sync();
+                    csync<Q>(cl);
                     long long before = 0;
                     for (int r2 = 0; r2 < rank; ++r2) before += sm0->part_cnt[r2];
                     long long budget = (ml - kstar) - before;
@@ -475,7 +549,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                         if (free_pt && rk < budget) taken[i] = 1;
                         budget -= chunk;
                     }
-                    cl.sync();
+                    csync<Q>(cl);
                 }
             }
 
@@ -487,7 +561,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                 int tot;
                 block_excl_scan<int>(cnt, &tot, sm.red_i);
                 if (tid == 0) sm0->part_cnt[rank] = tot;
-                cl.sync();
+                csync<Q>(cl);
                 long long pos = obase;
                 for (int r2 = 0; r2 < rank; ++r2) pos += sm0->part_cnt[r2];
                 int32_t* out = P.out[j];
@@ -509,7 +583,7 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
                     }
                     pos += chunk;
                 }
-                cl.sync();  // the next level reads orig_out; part_cnt is reused
+                csync<Q>(cl);  // the next level reads orig_out; part_cnt is reused
             }
         }
     }
@@ -519,15 +593,17 @@ __global__ void __cluster_dims__(kQ, 1, 1) __launch_bounds__(kST, 1)
 
 int small_clusters(int device) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kQ * 64);
+    cfg.gridDim = dim3(8 * 64);
     cfg.blockDim = dim3(kST);
     cfg.dynamicSmemBytes = kSmallDyn;
-    if (cudaFuncSetAttribute(hav_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(hav_small_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmallDyn)) != cudaSuccess ||
+        cudaFuncSetAttribute(hav_small_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kSmallDyn)) != cudaSuccess)
         return -1;
     int nc = 0;
     (void)device;
-    if (cudaOccupancyMaxActiveClusters(&nc, hav_small_kernel, &cfg) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveClusters(&nc, hav_small_kernel<8>, &cfg) != cudaSuccess) return -1;
     return nc;
 }
 
@@ -535,11 +611,22 @@ int launch_small(const Plan& plan, int first_level, int nclusters, cudaStream_t 
     int nc = nclusters < plan.S ? nclusters : plan.S;
     if (nc < 1) nc = 1;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(static_cast<unsigned>(kQ * nc));
+    cfg.gridDim = dim3(static_cast<unsigned>(8 * nc));
     cfg.blockDim = dim3(kST);
     cfg.dynamicSmemBytes = kSmallDyn;
     cfg.stream = stream;
-    return cudaLaunchKernelEx(&cfg, hav_small_kernel, plan, first_level) == cudaSuccess ? 0 : -1;
+    return cudaLaunchKernelEx(&cfg, hav_small_kernel<8>, plan, first_level) == cudaSuccess ? 0 : -1;
+}
+
+int launch_solo(const Plan& plan, int first_level, int nblocks, cudaStream_t stream) {
+    int nc = nblocks < plan.S ? nblocks : plan.S;
+    if (nc < 1) nc = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(nc));
+    cfg.blockDim = dim3(kST);
+    cfg.dynamicSmemBytes = kSmallDyn;
+    cfg.stream = stream;
+    return cudaLaunchKernelEx(&cfg, hav_small_kernel<1>, plan, first_level) == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace havk

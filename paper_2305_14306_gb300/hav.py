@@ -71,7 +71,7 @@ class hav_tuning(C.Structure):
         ("chunk_min", C.c_int32),
         ("nblocks", C.c_int32),
         ("small_points", C.c_int32),
-        ("reserved", C.c_int32),
+        ("solo_points", C.c_int32),
     ]
 
 
@@ -213,9 +213,9 @@ class Context:
         t = hav_tuning()
         _check(load().hav_context_get_tuning(self.handle, C.byref(t)), "hav_context_get_tuning")
         return {"spec_points": list(t.spec_points), "chunk_min": t.chunk_min, "nblocks": t.nblocks,
-                "small_points": t.small_points}
+                "small_points": t.small_points, "solo_points": t.solo_points}
 
-    def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None, small_points=None):
+    def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None, small_points=None, solo_points=None):
         """Change some of the knobs; the others keep their values."""
         cur = self.get_tuning()
         t = hav_tuning()
@@ -225,7 +225,7 @@ class Context:
         t.chunk_min = int(cur["chunk_min"] if chunk_min is None else chunk_min)
         t.nblocks = int(cur["nblocks"] if nblocks is None else nblocks)
         t.small_points = int(cur["small_points"] if small_points is None else small_points)
-        t.reserved = 0
+        t.solo_points = int(cur["solo_points"] if solo_points is None else solo_points)
         _check(load().hav_context_set_tuning(self.handle, C.byref(t)), "hav_context_set_tuning")
 
     def close(self):

@@ -65,6 +65,7 @@ def test_struct_layouts_match_header(libhav, tmp_path):
     assert int(out[4]) == ctypes.sizeof(hav.hav_tuning)
     assert int(out[5]) == hav.hav_tuning.chunk_min.offset
     assert int(out[6]) == hav.hav_tuning.small_points.offset
+    assert hav.hav_tuning.solo_points.offset == hav.hav_tuning.small_points.offset + 4
     assert int(out[7]) == hav.hav_params.search.offset
 
 

@@ -353,3 +353,35 @@ def test_coverage_fps_vs_hav(hv, ctx):
     rnd = torch.from_numpy(np.sort(np.random.default_rng(0).choice(16384, 4096, replace=False))).cuda()
     c_hav, c_fps, c_rnd = hv.coverage(d, hav_idx), hv.coverage(d, fps_idx), hv.coverage(d, rnd)
     assert c_fps <= c_hav < c_rnd
+
+
+def test_single_cta_levels_match_the_grid_kernel(hv):
+    # levels of at most 4,096 points per segment run on one CTA each by default;
+    # switching that off gives the same indices and traces (the single-CTA
+    # engine counts every step, the grid kernel may settle some with a bound)
+    c = hv.Context(1 << 18, 16)
+    try:
+        assert c.get_tuning()["solo_points"] == 4096
+        pts = scenes.lidar_min(16384, 7)[0]
+        sizes = [3000, 1, 0, 700, 4096, 9000]
+        clouds = [scenes.uniform_box(n, 30 + i) for i, n in enumerate(sizes)]
+        res = {}
+        for solo in (4096, 0):
+            c.set_tuning(solo_points=solo)
+            chain = run_levels(hv, c, pts, [16384, 4096, 1024, 512])
+            batch = _batched(hv, c, clouds, [[n // 4 for n in sizes], [n // 16 for n in sizes]])
+            res[solo] = (chain, batch)
+        (ca, ba), (cb, bb) = res[4096], res[0]
+        for j in range(4):
+            assert np.array_equal(ca[0][j], cb[0][j]), j
+        for x, y in zip(cb[2], ca[2]):
+            assert G.traces_equal(x, y) is None, G.traces_equal(x, y)
+        for a, b in zip(ba[0], bb[0]):
+            assert np.array_equal(a, b)
+        assert ba[1] == bb[1] == 0
+        for x, y in zip(bb[3], ba[3]):
+            assert G.traces_equal(x, y) is None, G.traces_equal(x, y)
+        with pytest.raises(hv.HavError):
+            c.set_tuning(solo_points=4097)
+    finally:
+        c.close()

@@ -197,10 +197,13 @@ typedef struct {
     int32_t chunk_min;       /* smallest work item in points, 1..65536 */
     int32_t nblocks;         /* as in hav_context_set_blocks (0: all co-resident) */
     int32_t small_points;    /* levels whose every segment has at most this many
-                                points (0..32768; 0: none, the default) run on
+                                points (0..32768; 0: none; default 32768 where
+                                the device launches 8-CTA clusters) run on
                                 thread-block clusters, one cluster of 8 SMs per
                                 segment, the voxel table in distributed shared
-                                memory (same results; plain bisection) */
+                                memory (same results; plain bisection, settled
+                                steps as in the grid kernel; same conditions as
+                                solo_points) */
     int32_t solo_points;     /* levels whose every segment has at most this many
                                 points (0..4096; 0: none; default 4096) run on
                                 single CTAs, one per segment, its points and
@@ -208,11 +211,16 @@ typedef struct {
                                 phase ended by a block barrier (same results;
                                 plain bisection; used when search is BISECT,
                                 select CENTRE_CLOSEST or RANDOM and no flag is
-                                set, and small_points does not apply) */
+                                set).  Levels run on the grid-wide kernel until
+                                the first level within small_points, then on
+                                clusters until the first level within
+                                solo_points that has more segments than the
+                                device runs clusters at once, or at most 1,024
+                                points per segment */
 } hav_tuning;
 
 /* Copy the context's tuning into *out (the defaults after creation:
- * {0, 4096, 65536}, 64, the co-resident maximum, 0, 4096). */
+ * {0, 4096, 65536}, 64, the co-resident maximum, 32768, 4096). */
 hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out);
 
 /* Replace the context's tuning.  HAV_ERR_INVALID (and no change) on a value

@@ -116,7 +116,7 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
         const int snc = havk::small_clusters(dev);
         cudaGetLastError();
         c->small_nc = snc > 0 ? snc : 0;
-        c->small_points = 0;  // measured no faster than the grid kernel on GB300: opt-in
+        c->small_points = c->small_nc > 0 ? havk::kSmallMax : 0;
         c->solo_ok = (snc >= 0) ? 1 : 0;
         c->solo_points = c->solo_ok ? havk::kSoloMax : 0;
     }
@@ -270,22 +270,25 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
         const bool small_ok =
             params->flags == 0 && params->search == HAV_SEARCH_BISECT &&
             (params->select == HAV_SELECT_CENTRE_CLOSEST || params->select == HAV_SELECT_RANDOM);
-        auto first_level_within = [&](int64_t limit) {
-            for (int j = 0; j < num_levels; ++j) {
-                int64_t mx = 0;
-                for (int s = 0; s < num_segments; ++s) {
-                    const int64_t nj = (j == 0) ? seg_offsets[s + 1] - seg_offsets[s]
-                                                : seg_m[static_cast<int64_t>(j - 1) * num_segments + s];
-                    if (nj > mx) mx = nj;
-                }
-                if (mx <= limit) return j;
-            }
-            return num_levels;
-        };
+        // grid kernel for [0, j0), clusters for [j0, j1), single CTAs for [j1, L).
+        // A level goes to single CTAs when it also has more segments than
+        // clusters fit at once, or only tiny segments (measured on GB300: one
+        // CTA per segment wins for many segments, an 8-CTA cluster for a few
+        // above kSoloAlone points); later levels are no larger, so they follow.
         int j0 = num_levels, j1 = num_levels;
-        if (small_ok && ctx->small_points > 0) j0 = first_level_within(ctx->small_points);
-        if (small_ok && j0 == num_levels && ctx->solo_points > 0) j1 = first_level_within(ctx->solo_points);
-        if (j1 < j0) j0 = j1;
+        for (int j = 0; j < num_levels; ++j) {
+            int64_t mx = 0;
+            for (int s = 0; s < num_segments; ++s) {
+                const int64_t nj = (j == 0) ? seg_offsets[s + 1] - seg_offsets[s]
+                                            : seg_m[static_cast<int64_t>(j - 1) * num_segments + s];
+                if (nj > mx) mx = nj;
+            }
+            const bool clusters = small_ok && ctx->small_points > 0 && mx <= ctx->small_points;
+            const bool solo = small_ok && ctx->solo_points > 0 && mx <= ctx->solo_points &&
+                              (ctx->small_points == 0 || num_segments > ctx->small_nc || mx <= havk::kSoloAlone);
+            if (j0 == num_levels && (clusters || solo)) j0 = j;
+            if (j1 == num_levels && solo) j1 = j;
+        }
         if (j0 > 0) {
             plan->L = j0;
             plan->keep_orig = (j0 < num_levels) ? 1 : 0;
@@ -293,15 +296,18 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
             plan->L = num_levels;
             plan->keep_orig = 0;
         }
-        if (ret == HAV_OK && j0 < num_levels) {
-            if (j0 == j1) {
-                if (havk::launch_solo(*plan, j0, plan->nblocks, strm) != 0) ret = HAV_ERR_CUDA;
-            } else {
-                int nc = plan->nblocks / 8;
-                if (nc > ctx->small_nc) nc = ctx->small_nc;
-                if (nc < 1) nc = 1;
-                if (havk::launch_small(*plan, j0, nc, strm) != 0) ret = HAV_ERR_CUDA;
-            }
+        if (ret == HAV_OK && j0 < j1) {
+            int nc = plan->nblocks / 8;
+            if (nc > ctx->small_nc) nc = ctx->small_nc;
+            if (nc < 1) nc = 1;
+            plan->L = j1;
+            plan->keep_orig = (j1 < num_levels) ? 1 : 0;
+            if (havk::launch_small(*plan, j0, nc, strm) != 0) ret = HAV_ERR_CUDA;
+            plan->L = num_levels;
+            plan->keep_orig = 0;
+        }
+        if (ret == HAV_OK && j1 < num_levels) {
+            if (havk::launch_solo(*plan, j1, plan->nblocks, strm) != 0) ret = HAV_ERR_CUDA;
         }
     }
     delete plan;

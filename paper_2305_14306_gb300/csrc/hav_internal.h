@@ -203,6 +203,7 @@ int small_clusters(int device);
 int launch_small(const Plan& plan, int first_level, int nclusters, cudaStream_t stream);
 // The same on single CTAs (one per segment), for levels of at most kSoloMax points.
 constexpr int kSoloMax = 4096;
+constexpr int kSoloAlone = 1024;  // a single segment this small goes to one CTA, not a cluster
 int launch_solo(const Plan& plan, int first_level, int nblocks, cudaStream_t stream);
 // Grouping around centres (hav_group.cu).
 int launch_ball_query(const float* points, long long n, const int32_t* centres, long long m, float radius,

@@ -355,32 +355,39 @@ def test_coverage_fps_vs_hav(hv, ctx):
     assert c_fps <= c_hav < c_rnd
 
 
-def test_single_cta_levels_match_the_grid_kernel(hv):
-    # levels of at most 4,096 points per segment run on one CTA each by default;
-    # switching that off gives the same indices and traces (the single-CTA
-    # engine counts every step, the grid kernel may settle some with a bound)
+def test_small_level_engines_match_the_grid_kernel(hv):
+    # levels within 32,768 points per segment run on 8-CTA clusters and levels
+    # within 4,096 on one CTA each by default; every combination, the grid
+    # kernel alone included, gives the same indices and traces (the grid
+    # kernel and the small engines settle the same steps by the same bounds)
     c = hv.Context(1 << 18, 16)
     try:
-        assert c.get_tuning()["solo_points"] == 4096
+        t = c.get_tuning()
+        assert t["solo_points"] == 4096 and t["small_points"] in (0, 32768)
         pts = scenes.lidar_min(16384, 7)[0]
         sizes = [3000, 1, 0, 700, 4096, 9000]
         clouds = [scenes.uniform_box(n, 30 + i) for i, n in enumerate(sizes)]
+        big = scenes.room_scene(60000, 8)
+        combos = [(0, 0), (0, 4096)] + ([(32768, 0), (32768, 4096)] if t["small_points"] else [])
         res = {}
-        for solo in (4096, 0):
-            c.set_tuning(solo_points=solo)
+        for small, solo in combos:
+            c.set_tuning(small_points=small, solo_points=solo)
             chain = run_levels(hv, c, pts, [16384, 4096, 1024, 512])
             batch = _batched(hv, c, clouds, [[n // 4 for n in sizes], [n // 16 for n in sizes]])
-            res[solo] = (chain, batch)
-        (ca, ba), (cb, bb) = res[4096], res[0]
-        for j in range(4):
-            assert np.array_equal(ca[0][j], cb[0][j]), j
-        for x, y in zip(cb[2], ca[2]):
-            assert G.traces_equal(x, y) is None, G.traces_equal(x, y)
-        for a, b in zip(ba[0], bb[0]):
-            assert np.array_equal(a, b)
-        assert ba[1] == bb[1] == 0
-        for x, y in zip(bb[3], ba[3]):
-            assert G.traces_equal(x, y) is None, G.traces_equal(x, y)
+            chain2 = run_levels(hv, c, big, [30000, 7500, 1875])
+            res[(small, solo)] = (chain, batch, chain2)
+        ref = res[(0, 0)]
+        for key, (ch, ba, ch2) in res.items():
+            for a, b in ((ch, ref[0]), (ch2, ref[2])):
+                for j in range(len(a[0])):
+                    assert np.array_equal(a[0][j], b[0][j]), (key, j)
+                for x, y in zip(a[2], b[2]):
+                    assert G.traces_equal(x, y) is None, (key, G.traces_equal(x, y))
+            for a, b in zip(ba[0], ref[1][0]):
+                assert np.array_equal(a, b), key
+            assert ba[1] == 0, key
+            for x, y in zip(ba[3], ref[1][3]):
+                assert G.traces_equal(x, y) is None, (key, G.traces_equal(x, y))
         with pytest.raises(hv.HavError):
             c.set_tuning(solo_points=4097)
     finally:

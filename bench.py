@@ -114,14 +114,15 @@ def source_hash() -> str:
 
 
 def profiled_traffic(workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    """DRAM bytes (read + write) per sampler call, summed over the call's
+    kernels, from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", f"hav_chain_kernel_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     mh = re.search(r"source_hash:\s*([0-9a-f]+)", text)
-    mt = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    mt = re.search(r"dram_bytes_per_call:\s*([0-9]+)", text)
     if not mh or not mt or mh.group(1) != source_hash():
         return None
     return int(mt.group(1))
@@ -371,9 +372,13 @@ def run_batched(args, world, rank, local):
     steps = max(10, min(args.steps, 200))
     clk = Clocks(gpu_index)
     time.sleep(0.3)
+    k0 = ctx.launches()
     ms_b = time_it(step_batched, steps)
+    launches_b = ctx.launches() - k0
     ms_g = time_it(graph.replay, steps)
+    k1 = ctx1.launches()
     ms_p = time_it(step_per_cloud, max(5, steps // 4))
+    launches_p = ctx1.launches() - k1
     clocks = clk.stop()
     tb, value = whole_job(sum(ms_b) / 1e3, total * len(ms_b), world, device="cuda")
     cpu = None
@@ -405,13 +410,14 @@ def run_batched(args, world, rank, local):
             "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
             "graph": {"value": v_graph, "ms_per_step": statistics.fmean(ms_g)},
             "per_cloud": {"value": v_per, "ms_per_step": statistics.fmean(ms_p),
-                          "launches_per_step": 64},
+                          "launches_per_step": launches_p / len(ms_p)},
             "speedup_vs_per_cloud": value / v_per,
             "identical_outputs": True,
             "cpu_baseline": cpu,
             "tuning": {"batched": tuned, **tune_report,
                        "per_cloud": "default knobs (one call per cloud)"},
-            "gpu_launches": len(ms_b),
+            "gpu_launches": launches_b,  # counted by the library over the timed batched steps
+            "launches_per_step": launches_b / len(ms_b),
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -863,6 +869,7 @@ def main():
         torch.cuda.synchronize()
         clk = Clocks(gpu_index)
         time.sleep(0.3)
+        k0 = ctx.launches()
         t0 = time.perf_counter()
         for k in range(steps):
             flush.zero_()
@@ -871,15 +878,16 @@ def main():
             evs[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        launched = ctx.launches() - k0
         if world > 1:
             dist.barrier()
         clocks = clk.stop()
         ms = [a.elapsed_time(b) for a, b in evs]
-        return ms, wall, clocks
+        return ms, wall, clocks, launched
 
-    ms, wall, clocks = timed()
+    ms, wall, clocks, launched = timed()
     if clocks_bad(clocks):
-        ms, wall, clocks = timed()
+        ms, wall, clocks, launched = timed()
         clocks["remeasured"] = True
     st, _ = hav.hav_status_get(ctx, 1)
     if st != hav.HAV_OK:
@@ -915,7 +923,11 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": profiled_traffic(args.workload + ("-guided" if args.search == "guided" else "")),
-                "peak_kind": peak_kind, "kernel": "hav_chain_kernel",
+                "peak_kind": peak_kind,
+                # one sampler call: the grid kernel, plus the small-level kernel
+                # when the last levels fit it; achieved and traffic cover the call
+                "kernel": "hav_chain_kernel" if launched == args.steps else "hav_chain_kernel + hav_small_kernel",
+                "launches_per_call": launched / args.steps,
                 "algorithmic_bytes_per_launch": B}
 
     # the other search start on the same workload, timed the same way
@@ -928,7 +940,7 @@ def main():
         tr_g = hav.hav_trace_get(ctx, len(ml) * pg.layers)
         B_g = algorithmic_bytes(tr_g, level_inputs, ml, pg.layers)
         g_steps = min(args.steps, 200)
-        ms_g, _, clk_g = timed(pg, g_steps)
+        ms_g, _, clk_g, _ = timed(pg, g_steps)
         if st == hav.HAV_OK and hav.hav_status_get(ctx, 1)[0] == hav.HAV_OK:
             _, v_g = whole_job(sum(ms_g) / 1e3, n * g_steps, world, device="cuda")
             mg = statistics.fmean(ms_g)
@@ -973,7 +985,8 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Mpoints/s", "h2d_bytes_per_step": int(pts.nbytes),
                     "d2h_bytes_per_step": int(4 * sum(ml)), "steps": len(e2e_ms)},
-            "gpu_launches": args.steps,  # one hav_chain_kernel launch per step
+            "gpu_launches": launched,  # counted by the library over the timed steps
+            "launches_per_step": launched / args.steps,
             "clocks": clocks,
             "wall_s_timed": wall,
         }

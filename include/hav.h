@@ -227,6 +227,13 @@ hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out);
  * outside the ranges above.  Takes effect from the next call. */
 hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t);
 
+/* Number of device kernels the context's calls have launched since it was
+ * created (memsets and copies excluded), in *out (HOST).  A level chain
+ * launches one to three kernels (hav_tuning), hav_sample_xyz one more, the
+ * spacing, ball-query and farthest-point calls one each.  HAV_ERR_INVALID on
+ * a NULL argument. */
+hav_status hav_context_launches(const hav_ctx* ctx, uint64_t* out);
+
 /* Release the context and its device memory.  Waits for the device.  NULL is ignored. */
 void hav_context_destroy(hav_ctx* ctx);
 
@@ -259,7 +266,9 @@ hav_status hav_sample_xyz(hav_ctx* ctx, const float* points, int64_t n, int64_t 
  * network down-sample (Section 4.1).  m_levels: HOST array of num_levels
  * budgets, non-increasing, m_levels[0] <= n.  out_idx: HOST array of
  * num_levels DEVICE pointers; out_idx[j] receives m_levels[j] ascending
- * indices into the ORIGINAL cloud.  All levels run in one launch. */
+ * indices into the ORIGINAL cloud.  The levels run in at most three
+ * launches on `stream`: the grid-wide kernel for the large levels, then the
+ * cluster and single-CTA kernels for the small ones (hav_tuning). */
 hav_status hav_sample_levels(hav_ctx* ctx, const float* points, int64_t n,
                              const int64_t* m_levels, int32_t num_levels,
                              const hav_params* params, int32_t* const* out_idx,
@@ -271,8 +280,9 @@ hav_status hav_sample_levels(hav_ctx* ctx, const float* points, int64_t n,
  * each level's budget <= the previous level's for that segment.  out_idx:
  * HOST array of num_levels DEVICE pointers; out_idx[j] receives, for each
  * segment s in order, seg_m[j][s] ascending indices LOCAL to segment s (into
- * the segment's original points).  One persistent launch runs every level
- * of every segment; each segment's result equals the single-cloud call's. */
+ * the segment's original points).  Persistent launches (as in
+ * hav_sample_levels) run every level of every segment; each segment's result
+ * equals the single-cloud call's. */
 hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* seg_offsets,
                               const int64_t* seg_m, int32_t num_segments, int32_t num_levels,
                               const hav_params* params, int32_t* const* out_idx,

@@ -27,9 +27,17 @@ struct hav_ctx {
     int32_t last_S;
     int32_t last_L;
     int32_t last_layers;
+    uint64_t launches;  // kernels enqueued by this context's calls
 };
 
 namespace {
+
+// Adds the kernels a launcher enqueued to the context's count; false on a failed launch.
+bool counted(hav_ctx* ctx, int launched) {
+    if (launched < 0) return false;
+    ctx->launches += static_cast<uint64_t>(launched);
+    return true;
+}
 
 hav_status check_params(const hav_params* p) {
     if (!p) return HAV_ERR_INVALID;
@@ -173,6 +181,12 @@ hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t) {
     return HAV_OK;
 }
 
+hav_status hav_context_launches(const hav_ctx* ctx, uint64_t* out) {
+    if (!ctx || !out) return HAV_ERR_INVALID;
+    *out = ctx->launches;
+    return HAV_OK;
+}
+
 void hav_context_destroy(hav_ctx* ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
@@ -292,7 +306,7 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
         if (j0 > 0) {
             plan->L = j0;
             plan->keep_orig = (j0 < num_levels) ? 1 : 0;
-            if (havk::launch_chain(*plan, strm) != 0) ret = HAV_ERR_CUDA;
+            if (!counted(ctx, havk::launch_chain(*plan, strm))) ret = HAV_ERR_CUDA;
             plan->L = num_levels;
             plan->keep_orig = 0;
         }
@@ -302,12 +316,12 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
             if (nc < 1) nc = 1;
             plan->L = j1;
             plan->keep_orig = (j1 < num_levels) ? 1 : 0;
-            if (havk::launch_small(*plan, j0, nc, strm) != 0) ret = HAV_ERR_CUDA;
+            if (!counted(ctx, havk::launch_small(*plan, j0, nc, strm))) ret = HAV_ERR_CUDA;
             plan->L = num_levels;
             plan->keep_orig = 0;
         }
         if (ret == HAV_OK && j1 < num_levels) {
-            if (havk::launch_solo(*plan, j1, plan->nblocks, strm) != 0) ret = HAV_ERR_CUDA;
+            if (!counted(ctx, havk::launch_solo(*plan, j1, plan->nblocks, strm))) ret = HAV_ERR_CUDA;
         }
     }
     delete plan;
@@ -337,8 +351,8 @@ hav_status hav_sample_xyz(hav_ctx* ctx, const float* points, int64_t n, int64_t 
     hav_status st = hav_sample(ctx, points, n, m, params, out_idx, stream);
     if (st != HAV_OK || m == 0) return st;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return HAV_ERR_CUDA;
-    if (havk::launch_repr(points, n, m, out_idx, out_xyz, params->select, params->aspect, ctx->ws, ctx->lay,
-                          reinterpret_cast<cudaStream_t>(stream)) != 0)
+    if (!counted(ctx, havk::launch_repr(points, n, m, out_idx, out_xyz, params->select, params->aspect, ctx->ws,
+                                        ctx->lay, reinterpret_cast<cudaStream_t>(stream))))
         return HAV_ERR_CUDA;
     return HAV_OK;
 }
@@ -354,7 +368,7 @@ hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32
     ctx->last_S = 1;
     if (m == 0) return HAV_OK;
     havk::GlobalHdr* gh = reinterpret_cast<havk::GlobalHdr*>(ctx->ws + ctx->lay.ghdr);
-    if (havk::launch_spacing(points, n, idx, m, out_d2, &gh->status, ctx->max_blocks, strm) != 0)
+    if (!counted(ctx, havk::launch_spacing(points, n, idx, m, out_d2, &gh->status, ctx->max_blocks, strm)))
         return HAV_ERR_CUDA;
     return HAV_OK;
 }
@@ -370,8 +384,8 @@ hav_status hav_ball_query(hav_ctx* ctx, const float* points, int64_t n, const in
     ctx->last_S = 1;
     if (m == 0) return HAV_OK;
     havk::GlobalHdr* gh = reinterpret_cast<havk::GlobalHdr*>(ctx->ws + ctx->lay.ghdr);
-    if (havk::launch_ball_query(points, n, centres, m, radius, nsample, out_idx, out_xyz, ctx->ws, ctx->lay,
-                                &gh->status, strm) != 0)
+    if (!counted(ctx, havk::launch_ball_query(points, n, centres, m, radius, nsample, out_idx, out_xyz, ctx->ws,
+                                              ctx->lay, &gh->status, strm)))
         return HAV_ERR_CUDA;
     return HAV_OK;
 }
@@ -443,8 +457,8 @@ hav_status hav_fps(hav_ctx* ctx, const float* points, int64_t n, int64_t m, int3
     ctx->last_L = 0;
     if (cudaMemsetAsync(ctx->ws + ctx->lay.barrier, 0, ctx->lay.zero_bytes, strm) != cudaSuccess) return HAV_ERR_CUDA;
     if (m == 0) return HAV_OK;
-    if (havk::launch_fps(points, static_cast<int>(n), static_cast<int>(m), out_idx, ctx->ws, ctx->lay,
-                         ctx->fps_nblocks, strm) != 0)
+    if (!counted(ctx, havk::launch_fps(points, static_cast<int>(n), static_cast<int>(m), out_idx, ctx->ws, ctx->lay,
+                                       ctx->fps_nblocks, strm)))
         return HAV_ERR_CUDA;
     return HAV_OK;
 }
@@ -455,8 +469,11 @@ hav_status hav_count(hav_ctx* ctx, const float* points, int64_t n, float s, cons
     if (!(s > 0.0f) || !std::isfinite(s)) return HAV_ERR_INVALID;
     for (int a = 0; a < 3; ++a)
         if (!(aspect[a] > 0.0f) || !std::isfinite(aspect[a])) return HAV_ERR_INVALID;
-    return static_cast<hav_status>(havk::count_voxels(points, n, s, aspect, ctx->ws, ctx->lay, K,
-                                                      reinterpret_cast<cudaStream_t>(stream)));
+    int launched = 0;
+    const int st = havk::count_voxels(points, n, s, aspect, ctx->ws, ctx->lay, K, &launched,
+                                      reinterpret_cast<cudaStream_t>(stream));
+    ctx->launches += static_cast<uint64_t>(launched);
+    return static_cast<hav_status>(st);
 }
 
 }  // extern "C"

@@ -128,7 +128,7 @@ int launch_fps(const float* points, int n, int m, int32_t* out, unsigned char* w
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, fps_kernel, points, n, m, out, dist, bmax, bar, gh, nb) == cudaSuccess ? 0 : -1;
+    return cudaLaunchKernelEx(&cfg, fps_kernel, points, n, m, out, dist, bmax, bar, gh, nb) == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace havk

@@ -269,7 +269,7 @@ int launch_ball_query(const float* points, long long n, const int32_t* centres, 
     grp_scatter<<<blocks(n), t, 0, stream>>>(points, n, g, counts, list);
     grp_query<<<blocks(m), 128, 0, stream>>>(points, n, centres, m, radius, nsample, g, counts, list, out_idx,
                                              out_xyz, status);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaGetLastError() == cudaSuccess ? 8 : -1;
 }
 
 }  // namespace havk

@@ -191,11 +191,13 @@ inline hav_status check_variant_params(const hav_params* p) {
     return HAV_OK;
 }
 
-// Launchers (hav_sampler.cu).
+// Launchers: each launch_* returns the number of kernels it enqueued on
+// `stream`, or -1 if a launch failed.  Grid-wide sampler (hav_sampler.cu).
 int max_coresident_blocks(int device);
 int launch_chain(const Plan& plan, cudaStream_t stream);
+// Voxel count at one size: a hav_status; *launched receives the kernels enqueued.
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
-                 unsigned char* ws, const Layout& lay, int64_t* K, cudaStream_t stream);
+                 unsigned char* ws, const Layout& lay, int64_t* K, int* launched, cudaStream_t stream);
 int fps_coresident_blocks(int device);
 // Small levels on thread-block clusters (hav_small.cu): clusters that fit at
 // once (<= 0: none), and a launch of levels [first_level, plan.L).

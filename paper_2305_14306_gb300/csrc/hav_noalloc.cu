@@ -132,7 +132,7 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
         plan.off0[0] = 0;
         plan.off0[1] = n;
         plan.m[0][0] = static_cast<int32_t>(m);
-        if (havk::launch_chain(plan, strm) != 0) return HAV_ERR_CUDA;
+        if (havk::launch_chain(plan, strm) < 0) return HAV_ERR_CUDA;
     }
     if (status_out) {
         const havk::GlobalHdr* gh = reinterpret_cast<const havk::GlobalHdr*>(ds->scratch + lay.ghdr);

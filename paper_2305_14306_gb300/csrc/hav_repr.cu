@@ -230,7 +230,7 @@ int launch_repr(const float* points, long long n, long long m, const int32_t* id
     }
     repr_write<<<blocks(m), threads, 0, stream>>>(A, table ? 1 : 0);
     if (table) repr_clear<<<blocks(m), threads, 0, stream>>>(A);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaGetLastError() == cudaSuccess ? (table ? 4 : 1) : -1;
 }
 
 }  // namespace havk

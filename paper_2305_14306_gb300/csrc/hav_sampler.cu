@@ -1580,11 +1580,11 @@ int launch_chain(const Plan& plan, cudaStream_t stream) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, hav_chain_kernel, plan) == cudaSuccess ? 0 : -1;
+    return cudaLaunchKernelEx(&cfg, hav_chain_kernel, plan) == cudaSuccess ? 1 : -1;
 }
 
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3], unsigned char* ws,
-                 const Layout& lay, int64_t* K, cudaStream_t stream) {
+                 const Layout& lay, int64_t* K, int* launched, cudaStream_t stream) {
     // scratch: the level-0 key table; it is left dirty, so the next sampler
     // call on this workspace starts with a full clear
     int cap_log2 = kMinCapLog2;
@@ -1602,6 +1602,7 @@ int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
     count_kernel<<<1024, 256, 0, stream>>>(points, n, s, aspect[0], aspect[1], aspect[2], enc6, T, cap_log2, dK,
                                            derr);
     if (cudaGetLastError() != cudaSuccess) return HAV_ERR_CUDA;
+    *launched = 3;
     unsigned long long hK = 0;
     int herr = 0;
     uint32_t henc[7];

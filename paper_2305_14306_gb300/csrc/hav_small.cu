@@ -615,7 +615,7 @@ int launch_small(const Plan& plan, int first_level, int nclusters, cudaStream_t 
     cfg.blockDim = dim3(kST);
     cfg.dynamicSmemBytes = kSmallDyn;
     cfg.stream = stream;
-    return cudaLaunchKernelEx(&cfg, hav_small_kernel<8>, plan, first_level) == cudaSuccess ? 0 : -1;
+    return cudaLaunchKernelEx(&cfg, hav_small_kernel<8>, plan, first_level) == cudaSuccess ? 1 : -1;
 }
 
 int launch_solo(const Plan& plan, int first_level, int nblocks, cudaStream_t stream) {
@@ -626,7 +626,7 @@ int launch_solo(const Plan& plan, int first_level, int nblocks, cudaStream_t str
     cfg.blockDim = dim3(kST);
     cfg.dynamicSmemBytes = kSmallDyn;
     cfg.stream = stream;
-    return cudaLaunchKernelEx(&cfg, hav_small_kernel<1>, plan, first_level) == cudaSuccess ? 0 : -1;
+    return cudaLaunchKernelEx(&cfg, hav_small_kernel<1>, plan, first_level) == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace havk

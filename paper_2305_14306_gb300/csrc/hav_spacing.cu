@@ -103,11 +103,14 @@ int launch_spacing(const float* points, long long n, const int32_t* idx, long lo
     const long long chunk = ((tiles + want - 1) / want) * kSpTile;
     const long long splits = (m + chunk - 1) / chunk;
     long long ib = (m + 255) / 256;
+    int launched = 1;
     spacing_init<<<static_cast<unsigned>(ib > 4096 ? 4096 : (ib < 1 ? 1 : ib)), 256, 0, stream>>>(out, m);
-    if (qblocks > 0 && qblocks <= 0x7fffffffll)
+    if (qblocks > 0 && qblocks <= 0x7fffffffll) {
         spacing_kernel<<<dim3(static_cast<unsigned>(qblocks), static_cast<unsigned>(splits)), kSpThreads, 0, stream>>>(
             points, n, idx, m, chunk, out, status);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+        ++launched;
+    }
+    return cudaGetLastError() == cudaSuccess ? launched : -1;
 }
 
 }  // namespace havk

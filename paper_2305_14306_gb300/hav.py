@@ -90,7 +90,7 @@ EXPORTS = [
     "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
     "hav_count", "hav_status_string", "hav_sample_noalloc", "hav_phase_times_get", "hav_fps",
     "hav_context_set_blocks", "hav_context_get_tuning", "hav_context_set_tuning", "hav_sample_xyz",
-    "hav_spacing", "hav_ball_query",
+    "hav_spacing", "hav_ball_query", "hav_context_launches",
 ]
 HAV_FLAG_PHASE_TIMES = 1
 HAV_FLAG_TEST_TIMEOUT = 2
@@ -147,6 +147,8 @@ def load(path: str = LIB_PATH):
         L.hav_context_get_tuning.restype = C.c_int
         L.hav_context_set_tuning.argtypes = [vp, P(hav_tuning)]
         L.hav_context_set_tuning.restype = C.c_int
+        L.hav_context_launches.argtypes = [vp, P(C.c_uint64)]
+        L.hav_context_launches.restype = C.c_int
         L.hav_fps.argtypes = [vp, vp, i64, i64, vp, vp]
         L.hav_fps.restype = C.c_int
         L.hav_phase_times_get.argtypes = [vp, vp, P(C.c_uint64), P(C.c_uint32), i32]
@@ -227,6 +229,12 @@ class Context:
         t.small_points = int(cur["small_points"] if small_points is None else small_points)
         t.solo_points = int(cur["solo_points"] if solo_points is None else solo_points)
         _check(load().hav_context_set_tuning(self.handle, C.byref(t)), "hav_context_set_tuning")
+
+    def launches(self) -> int:
+        """Device kernels this context's calls have enqueued since creation."""
+        n = C.c_uint64()
+        _check(load().hav_context_launches(self.handle, C.byref(n)), "hav_context_launches")
+        return int(n.value)
 
     def close(self):
         if self.handle:

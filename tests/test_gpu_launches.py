@@ -1,0 +1,83 @@
+"""The context's kernel-launch count (hav_context_launches) through the C ABI:
+how many kernels each call enqueues under the default tuning, so that a
+reported launch count is the library's own."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+sys.path.insert(0, os.path.dirname(__file__))
+from paper_2305_14306_gb300 import scenes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_14306_gb300 import build, hav
+    build.build()
+    hav.load()
+    return hav
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def launched(ctx, fn):
+    k0 = ctx.launches()
+    fn()
+    torch.cuda.synchronize()
+    return ctx.launches() - k0
+
+
+def test_level_chains_launch_one_kernel_per_engine(hv):
+    ctx = hv.Context(1 << 17, 4)
+    try:
+        assert ctx.get_tuning()["small_points"] == 32768 and ctx.get_tuning()["solo_points"] == 4096
+        big = dev(scenes.uniform_box(100_000, seed=1))
+        p = hv.params()
+        # one level above 32,768 points: the grid kernel alone
+        assert launched(ctx, lambda: hv.hav_sample(ctx, big, 25_000, p)) == 1
+        # grid kernel, then clusters from the first level within 32,768 points
+        assert launched(ctx, lambda: hv.hav_sample_levels(ctx, big, [25_000, 6_250, 1_562], p)) == 2
+        # ... then one CTA per segment from the first level of at most 1,024 points
+        assert launched(ctx, lambda: hv.hav_sample_levels(ctx, big, [25_000, 4_000, 1_000, 250], p)) == 3
+        # small clouds skip the grid kernel
+        mid = dev(scenes.uniform_box(3_000, seed=2))
+        assert launched(ctx, lambda: hv.hav_sample(ctx, mid, 700, p)) == 1
+        tiny = dev(scenes.uniform_box(800, seed=3))
+        assert launched(ctx, lambda: hv.hav_sample(ctx, tiny, 200, p)) == 1
+        # the phase timer keeps every level on the grid kernel
+        pt = hv.params(flags=hv.HAV_FLAG_PHASE_TIMES)
+        assert launched(ctx, lambda: hv.hav_sample_levels(ctx, big, [25_000, 4_000, 1_000, 250], pt)) == 1
+        # nothing to select: nothing launched
+        assert launched(ctx, lambda: hv.hav_sample(ctx, big, 0, p)) == 0
+        st, _ = hv.hav_status_get(ctx, 1)
+        assert st == hv.HAV_OK
+    finally:
+        ctx.close()
+
+
+def test_other_calls_count_their_kernels(hv):
+    ctx = hv.Context(1 << 16, 1)
+    try:
+        big = dev(scenes.uniform_box(50_000, seed=4))
+        p1 = hv.params(layers=1)
+        assert launched(ctx, lambda: hv.hav_sample(ctx, big, 12_000, p1)) == 1
+        # the representative coordinates: one more kernel, four with the voxel table
+        assert launched(ctx, lambda: hv.hav_sample_xyz(ctx, big, 12_000, p1)) == 2
+        assert launched(ctx, lambda: hv.hav_sample_xyz(ctx, big, 12_000, hv.params(layers=1, select="mean"))) == 5
+        idx = hv.hav_sample(ctx, big, 12_000, p1)
+        torch.cuda.synchronize()
+        assert launched(ctx, lambda: hv.hav_fps(ctx, big, 500)) == 1
+        assert launched(ctx, lambda: hv.hav_spacing(ctx, big, idx)) == 2
+        assert launched(ctx, lambda: hv.hav_ball_query(ctx, big, idx[:100], 0.05, 16)) == 8
+        st, _ = hv.hav_status_get(ctx, 1)
+        assert st == hv.HAV_OK
+    finally:
+        ctx.close()

@@ -53,8 +53,11 @@ constexpr int kSelSlots = 8192;    // block-local argmin table of the selection 
 constexpr size_t kSelSmem = static_cast<size_t>(kSelSlots) * 18;
 constexpr size_t kDynSmem = kPassSmem > kSelSmem ? kPassSmem : kSelSmem;
 constexpr int kBucketMin = 1 << 17;
-constexpr int kInFlight = 4;       // points loaded ahead per thread
-constexpr int kProbes = 2;         // global first probes issued together per thread
+// Loads and probes in flight per thread: with 64 registers a thread (one
+// 1024-thread block per SM), deeper batches spill more than they hide
+// (measured on GB300: 4 and 2 made the 1M-point chain 5 % slower).
+constexpr int kInFlight = 2;       // points loaded ahead per thread
+constexpr int kProbes = 1;         // global first probes issued together per thread
 static_assert(kSetSlots % (kProbes * kThreads) == 0 && kSelSlots % (kProbes * kThreads) == 0,
               "flush loops take kProbes slots per thread per step");
 

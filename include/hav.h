@@ -217,10 +217,16 @@ typedef struct {
                                 solo_points that has more segments than the
                                 device runs clusters at once, or at most 1,024
                                 points per segment */
+    int32_t cluster_ctas;    /* CTAs per cluster of the small_points levels:
+                                0 (default) = 16 where the call's segments all
+                                get a 16-CTA cluster at once within the
+                                context's blocks, else 8; or 8, or 16 (a
+                                cluster size above the portable 8; only where
+                                the device schedules it) */
 } hav_tuning;
 
 /* Copy the context's tuning into *out (the defaults after creation:
- * {0, 4096, 65536}, 64, the co-resident maximum, 32768, 4096). */
+ * {0, 4096, 65536}, 64, the co-resident maximum, 32768, 4096, 0). */
 hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out);
 
 /* Replace the context's tuning.  HAV_ERR_INVALID (and no change) on a value

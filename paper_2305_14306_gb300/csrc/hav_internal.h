@@ -201,8 +201,12 @@ int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
 int fps_coresident_blocks(int device);
 // Small levels on thread-block clusters (hav_small.cu): clusters that fit at
 // once (<= 0: none), and a launch of levels [first_level, plan.L).
-int small_clusters(int device);
-int launch_small(const Plan& plan, int first_level, int nclusters, cudaStream_t stream);
+// small_clusters(device, q): clusters of q CTAs (8 or 16) that run at once
+// (<= 0: none), after setting the kernel's launch attributes; q = 1 sets the
+// single-CTA kernel's (1, or -1 on failure).  launch_small runs levels
+// [first_level, plan.L) on nclusters clusters of q CTAs.
+int small_clusters(int device, int q);
+int launch_small(const Plan& plan, int first_level, int q, int nclusters, cudaStream_t stream);
 // The same on single CTAs (one per segment), for levels of at most kSoloMax points.
 constexpr int kSoloMax = 4096;
 constexpr int kSoloAlone = 1024;  // a single segment this small goes to one CTA, not a cluster

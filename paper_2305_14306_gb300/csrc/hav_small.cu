@@ -1,8 +1,10 @@
 // Small levels on thread-block clusters, and on single CTAs.
 //
 // The same sampler as hav_chain_kernel (Sections 3.2-3.4 and Eq. 3, with the
-// same readings), for levels of at most Q * 4,096 points: one cluster of Q
-// CTAs per segment, the voxel table spread over the CTAs' shared memory and
+// same readings), for levels of at most 32,768 points: one cluster of Q = 8
+// or 16 CTAs per segment (16 where every segment's cluster runs at once: more
+// SMs share each pass; 16 is above the portable cluster size and is used
+// where the device schedules it), the voxel table spread over the CTAs' shared memory and
 // reached through distributed shared memory, phases separated by the cluster
 // barrier.  With Q = 1 a segment's level lives in one CTA: every exchange is
 // a shared-memory access and every phase ends with a block barrier.  An
@@ -37,9 +39,10 @@ constexpr int kST = 1024;         // threads per CTA
 constexpr int kPtsPerCta = 4096;  // level points one CTA holds
 constexpr int kPartMax = 2 * kPtsPerCta;  // table slots per CTA at most
 static_assert(kSmallMax == 8 * kPtsPerCta, "the 8-CTA cluster takes kSmallMax points");
+constexpr int kMaxQ = 16;  // largest cluster
 template <int Q>
 __host__ __device__ constexpr int qlog2() {
-    return Q == 8 ? 3 : (Q == 4 ? 2 : (Q == 2 ? 1 : 0));
+    return Q == 16 ? 4 : (Q == 8 ? 3 : (Q == 4 ? 2 : (Q == 2 ? 1 : 0)));
 }
 constexpr size_t kSmallDyn = static_cast<size_t>(kPartMax) * 16 + static_cast<size_t>(kPtsPerCta) * 16 +
                              static_cast<size_t>(kPtsPerCta) + 4 * kHistBins;
@@ -54,7 +57,7 @@ struct SmallSmem {
     unsigned ncand;             // boundary-bin candidates appended
     uint32_t box[6];            // bounding box codes of the level
     int nonfinite;
-    int part_cnt[8];   // per-CTA counts for prefixes (shortfall, compaction)
+    int part_cnt[kMaxQ];  // per-CTA counts for prefixes (shortfall, compaction)
     // this CTA's
     float mn[3], mx[3], s_hi;
     int pre[kMaxIters];         // counts at s_hi / 2^(k+1) of this level's earlier layers (-1: none)
@@ -591,34 +594,64 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
 
 }  // namespace
 
-int small_clusters(int device) {
+int small_clusters(int device, int q) {
+    (void)device;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(8 * 64);
+    cfg.gridDim = dim3(static_cast<unsigned>(q * 16));
     cfg.blockDim = dim3(kST);
     cfg.dynamicSmemBytes = kSmallDyn;
-    if (cudaFuncSetAttribute(hav_small_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmallDyn)) != cudaSuccess ||
-        cudaFuncSetAttribute(hav_small_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmallDyn)) != cudaSuccess)
-        return -1;
     int nc = 0;
-    (void)device;
-    if (cudaOccupancyMaxActiveClusters(&nc, hav_small_kernel<8>, &cfg) != cudaSuccess) return -1;
-    return nc;
+    if (q == 1) {
+        if (cudaFuncSetAttribute(hav_small_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kSmallDyn)) != cudaSuccess)
+            return -1;
+        return 1;
+    }
+    if (q == 8) {
+        if (cudaFuncSetAttribute(hav_small_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kSmallDyn)) != cudaSuccess ||
+            cudaOccupancyMaxActiveClusters(&nc, hav_small_kernel<8>, &cfg) != cudaSuccess)
+            return -1;
+        return nc;
+    }
+    if (q == 16) {
+        if (cudaFuncSetAttribute(hav_small_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kSmallDyn)) != cudaSuccess ||
+            cudaFuncSetAttribute(hav_small_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveClusters(&nc, hav_small_kernel<16>, &cfg) != cudaSuccess)
+            return -1;
+        return nc;
+    }
+    return -1;
 }
 
-int launch_small(const Plan& plan, int first_level, int nclusters, cudaStream_t stream) {
+int launch_small(const Plan& plan, int first_level, int q, int nclusters, cudaStream_t stream) {
+    if (q != 8 && q != 16) return -1;
+    // every level of the launch must fit its cluster's shared memory
+    for (int j = first_level; j < plan.L; ++j)
+        for (int s = 0; s < plan.S; ++s) {
+            const long long n = (j == 0) ? plan.off0[s + 1] - plan.off0[s] : plan.m[j - 1][s];
+            if (n > static_cast<long long>(kSmallMax)) return -1;
+        }
     int nc = nclusters < plan.S ? nclusters : plan.S;
     if (nc < 1) nc = 1;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(static_cast<unsigned>(8 * nc));
+    cfg.gridDim = dim3(static_cast<unsigned>(q * nc));
     cfg.blockDim = dim3(kST);
     cfg.dynamicSmemBytes = kSmallDyn;
     cfg.stream = stream;
-    return cudaLaunchKernelEx(&cfg, hav_small_kernel<8>, plan, first_level) == cudaSuccess ? 1 : -1;
+    const cudaError_t e = (q == 16) ? cudaLaunchKernelEx(&cfg, hav_small_kernel<16>, plan, first_level)
+                                    : cudaLaunchKernelEx(&cfg, hav_small_kernel<8>, plan, first_level);
+    return e == cudaSuccess ? 1 : -1;
 }
 
 int launch_solo(const Plan& plan, int first_level, int nblocks, cudaStream_t stream) {
+    for (int j = first_level; j < plan.L; ++j)  // every level must fit one CTA
+        for (int s = 0; s < plan.S; ++s) {
+            const long long n = (j == 0) ? plan.off0[s + 1] - plan.off0[s] : plan.m[j - 1][s];
+            if (n > static_cast<long long>(kSoloMax)) return -1;
+        }
     int nc = nblocks < plan.S ? nblocks : plan.S;
     if (nc < 1) nc = 1;
     cudaLaunchConfig_t cfg = {};

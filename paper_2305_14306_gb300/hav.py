@@ -72,6 +72,7 @@ class hav_tuning(C.Structure):
         ("nblocks", C.c_int32),
         ("small_points", C.c_int32),
         ("solo_points", C.c_int32),
+        ("cluster_ctas", C.c_int32),
     ]
 
 
@@ -215,9 +216,10 @@ class Context:
         t = hav_tuning()
         _check(load().hav_context_get_tuning(self.handle, C.byref(t)), "hav_context_get_tuning")
         return {"spec_points": list(t.spec_points), "chunk_min": t.chunk_min, "nblocks": t.nblocks,
-                "small_points": t.small_points, "solo_points": t.solo_points}
+                "small_points": t.small_points, "solo_points": t.solo_points, "cluster_ctas": t.cluster_ctas}
 
-    def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None, small_points=None, solo_points=None):
+    def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None, small_points=None, solo_points=None,
+                   cluster_ctas=None):
         """Change some of the knobs; the others keep their values."""
         cur = self.get_tuning()
         t = hav_tuning()
@@ -228,6 +230,7 @@ class Context:
         t.nblocks = int(cur["nblocks"] if nblocks is None else nblocks)
         t.small_points = int(cur["small_points"] if small_points is None else small_points)
         t.solo_points = int(cur["solo_points"] if solo_points is None else solo_points)
+        t.cluster_ctas = int(cur["cluster_ctas"] if cluster_ctas is None else cluster_ctas)
         _check(load().hav_context_set_tuning(self.handle, C.byref(t)), "hav_context_set_tuning")
 
     def launches(self) -> int:

@@ -49,10 +49,10 @@ def test_struct_layouts_match_header(libhav, tmp_path):
     src = tmp_path / "s.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "hav.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hav_params), sizeof(hav_layer_trace),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hav_params), sizeof(hav_layer_trace),'
         ' offsetof(hav_layer_trace, s), offsetof(hav_layer_trace, K), sizeof(hav_tuning),'
         ' offsetof(hav_tuning, chunk_min), offsetof(hav_tuning, small_points),'
-        ' offsetof(hav_params, search)); return 0;}\n')
+        ' offsetof(hav_params, search), offsetof(hav_tuning, cluster_ctas)); return 0;}\n')
     exe = tmp_path / "s"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
@@ -67,6 +67,7 @@ def test_struct_layouts_match_header(libhav, tmp_path):
     assert int(out[6]) == hav.hav_tuning.small_points.offset
     assert hav.hav_tuning.solo_points.offset == hav.hav_tuning.small_points.offset + 4
     assert int(out[7]) == hav.hav_params.search.offset
+    assert int(out[8]) == hav.hav_tuning.cluster_ctas.offset
 
 
 def test_params_default_and_status_strings(libhav):

@@ -356,27 +356,29 @@ def test_coverage_fps_vs_hav(hv, ctx):
 
 
 def test_small_level_engines_match_the_grid_kernel(hv):
-    # levels within 32,768 points per segment run on 8-CTA clusters and levels
-    # within 4,096 on one CTA each by default; every combination, the grid
-    # kernel alone included, gives the same indices and traces (the grid
-    # kernel and the small engines settle the same steps by the same bounds)
+    # levels within 32,768 points per segment run on clusters of 16 or 8 CTAs
+    # and levels within 4,096 on one CTA each by default; every combination,
+    # the grid kernel alone included, gives the same indices and traces (the
+    # grid kernel and the small engines settle the same steps by the same bounds)
     c = hv.Context(1 << 18, 16)
     try:
         t = c.get_tuning()
-        assert t["solo_points"] == 4096 and t["small_points"] in (0, 32768)
+        assert t["solo_points"] == 4096 and t["small_points"] in (0, 32768) and t["cluster_ctas"] == 0
         pts = scenes.lidar_min(16384, 7)[0]
         sizes = [3000, 1, 0, 700, 4096, 9000]
         clouds = [scenes.uniform_box(n, 30 + i) for i, n in enumerate(sizes)]
         big = scenes.room_scene(60000, 8)
-        combos = [(0, 0), (0, 4096)] + ([(32768, 0), (32768, 4096)] if t["small_points"] else [])
+        combos = [(0, 0, 0), (0, 4096, 0)]
+        if t["small_points"]:
+            combos += [(32768, solo, q) for solo in (0, 4096) for q in (0, 8, 16)]
         res = {}
-        for small, solo in combos:
-            c.set_tuning(small_points=small, solo_points=solo)
+        for small, solo, q in combos:
+            c.set_tuning(small_points=small, solo_points=solo, cluster_ctas=q)
             chain = run_levels(hv, c, pts, [16384, 4096, 1024, 512])
             batch = _batched(hv, c, clouds, [[n // 4 for n in sizes], [n // 16 for n in sizes]])
             chain2 = run_levels(hv, c, big, [30000, 7500, 1875])
-            res[(small, solo)] = (chain, batch, chain2)
-        ref = res[(0, 0)]
+            res[(small, solo, q)] = (chain, batch, chain2)
+        ref = res[(0, 0, 0)]
         for key, (ch, ba, ch2) in res.items():
             for a, b in ((ch, ref[0]), (ch2, ref[2])):
                 for j in range(len(a[0])):
@@ -390,5 +392,8 @@ def test_small_level_engines_match_the_grid_kernel(hv):
                 assert G.traces_equal(x, y) is None, (key, G.traces_equal(x, y))
         with pytest.raises(hv.HavError):
             c.set_tuning(solo_points=4097)
+        for q in (1, 4, 12, 32, -8):
+            with pytest.raises(hv.HavError):
+                c.set_tuning(cluster_ctas=q)
     finally:
         c.close()

@@ -291,7 +291,7 @@ def scene_parallel_oracle(clouds, m_levels, search, reps=3):
         dt = time.perf_counter() - t0
     return total * reps / dt / 1e6, cores, res
 def run_batched(args, world, rank, local):
-    """64 clouds per step: one hav_sample_batched launch, the same launch from a
+    """64 clouds per step: one hav_sample_batched call, the same call from a
     CUDA graph, and 64 plain per-cloud hav_sample_levels calls, at identical outputs."""
     import torch
     import torch.distributed as dist
@@ -487,7 +487,7 @@ def run_compare(args, world, rank, local):
     single("C2 LiDAR first level", scenes.lidar_min(16384, seed=0)[0], 16384, True)
     single("C3 indoor level 1", scenes.room_scene(1 << 20, seed=0), 1 << 18, False, sample_q=65536)
 
-    # C4: 64 clouds, M = N/4: one batched HAV launch vs 64 FPS calls
+    # C4: 64 clouds, M = N/4: one batched HAV call vs 64 FPS calls
     clouds = scenes.lidar_batch(64, seed=0)
     pts, offs = scenes.concat(clouds)
     sizes = np.diff(offs)
@@ -497,6 +497,9 @@ def run_compare(args, world, rank, local):
     out = torch.empty(int(ms4.sum()), dtype=torch.int32, device="cuda")
     for _ in range(3):
         hav.hav_sample_batched(ctx, d, offs, ms4[None, :], p, outs=[out])
+    k0 = ctx.launches()
+    hav.hav_sample_batched(ctx, d, offs, ms4[None, :], p, outs=[out])
+    hav_launches = ctx.launches() - k0
     ms_h = min(timed(lambda: hav.hav_sample_batched(ctx, d, offs, ms4[None, :], p, outs=[out]))[1] for _ in range(5))
     fouts = [torch.empty(int(ms4[s]), dtype=torch.int32, device="cuda") for s in range(64)]
     views = [d[int(offs[s]):int(offs[s + 1])] for s in range(64)]
@@ -504,7 +507,9 @@ def run_compare(args, world, rank, local):
     def fps_all():
         for s in range(64):
             hav.hav_fps(ctx, views[s], int(ms4[s]), out=fouts[s])
+    k0 = ctx.launches()
     _, ms_f = timed(fps_all)
+    fps_launches = ctx.launches() - k0
     cut = np.concatenate([[0], np.cumsum(ms4)])
     covs = {"hav": [], "fps": [], "random": []}
     for s in range(64):
@@ -518,7 +523,7 @@ def run_compare(args, world, rank, local):
                   "fps_ms": ms_f, "fps_over_hav": ms_f / ms_h,
                   "coverage_m": {k: float(np.mean(v)) for k, v in covs.items()},
                   "coverage": "fp32, all points; mean over the 64 clouds",
-                  "hav_launches": 1, "fps_launches": 64})
+                  "hav_launches": hav_launches, "fps_launches": fps_launches})
     if rank == 0:
         tot_n = sum(c["n"] for c in cases)
         tot_ms = sum(c["hav_ms"] for c in cases)

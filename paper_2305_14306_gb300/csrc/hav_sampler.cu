@@ -1,5 +1,6 @@
 // HAVSampler hot path for sm_103a: one persistent cooperative kernel runs a
-// whole batched level chain.
+// batched level chain, every level of it or the large levels up to the first
+// one the small-level kernels take (hav_small.cu).
 //
 // Per level j, for every segment (cloud) of the batch at once:
 //   bbox    per-axis min/max and finiteness (the bracket of the Section 3.3

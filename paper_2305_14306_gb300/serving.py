@@ -5,14 +5,14 @@ few *slots*; each slot owns a CUDA stream, a libhav context limited to its
 share of the SMs and device buffers, so the slots' launches run side by
 side on the GPU; requests bring their points in pinned host memory.  Whenever a slot is free, the
 requests that have arrived and wait are packed, first come first served,
-into one segmented ``hav_sample_batched`` launch, as many as fit the slot's
+into one segmented ``hav_sample_batched`` call, as many as fit the slot's
 point capacity and segment limit (admission by workspace memory).  A
 request's points stay on the device from admission to completion; its
 latency runs from its arrival to the moment the host sees its slot's
 completion event.
 
 The plain per-cloud path is the same loop with one slot and one request per
-launch.  Either way every request's indices equal a stand-alone call's.
+call.  Either way every request's indices equal a stand-alone call's.
 This module only orchestrates: every step of the sampling runs in libhav's
 kernels.
 """
@@ -39,7 +39,7 @@ class Request:
 class Result:
     indices: np.ndarray
     latency: float          # seconds from arrival to completion seen by the host
-    batch: int              # requests in the launch that served it
+    batch: int              # requests in the call that served it
 
 
 @dataclass

@@ -104,12 +104,38 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without comments and with whitespace runs collapsed,
+    so that edits of comments alone leave the hash (and a capture) valid."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":  # string or character literal, copied whole
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_hash() -> str:
+    """Hash of the kernel sources' code (comments and layout ignored)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_14306_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode() + b"\0" + _code_only(open(os.path.join(csrc, f)).read()).encode() + b"\0")
     return h.hexdigest()[:16]
 
 

@@ -195,6 +195,19 @@ def _points(points):
     return points
 
 
+def _out(t, numel: int, dtype, like, name: str, shape=None):
+    """A caller-provided output tensor, checked before the device writes into
+    it (the library cannot see its size), or a new one of `shape`."""
+    import torch
+    if t is None:
+        return torch.empty(shape if shape is not None else (int(numel),), dtype=dtype, device=like.device)
+    if not (isinstance(t, torch.Tensor) and t.device == like.device and t.dtype == dtype and t.is_contiguous()
+            and t.numel() >= int(numel)):
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor on {like.device} with at least "
+                         f"{int(numel)} elements")
+    return t
+
+
 class Context:
     """A libhav context: device workspace for calls of up to max_points points
     in total and max_segments segments."""
@@ -256,8 +269,7 @@ def hav_sample(ctx: Context, points, m: int, p: hav_params | None = None, out=No
     import torch
     points = _points(points)
     p = p or params()
-    if out is None:
-        out = torch.empty(int(m), dtype=torch.int32, device=points.device)
+    out = _out(out, max(0, int(m)), torch.int32, points, "out")
     st = load().hav_sample(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0], int(m), C.byref(p),
                            C.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(st, "hav_sample")
@@ -270,10 +282,8 @@ def hav_sample_xyz(ctx: Context, points, m: int, p: hav_params | None = None, ou
     import torch
     points = _points(points)
     p = p or params(layers=1)
-    if out is None:
-        out = torch.empty(int(m), dtype=torch.int32, device=points.device)
-    if xyz is None:
-        xyz = torch.empty((int(m), 3), dtype=torch.float32, device=points.device)
+    out = _out(out, max(0, int(m)), torch.int32, points, "out")
+    xyz = _out(xyz, 3 * max(0, int(m)), torch.float32, points, "xyz", shape=(max(0, int(m)), 3))
     st = load().hav_sample_xyz(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0], int(m), C.byref(p),
                                C.c_void_p(out.data_ptr()), C.c_void_p(xyz.data_ptr()), _stream_handle(stream))
     _check(st, "hav_sample_xyz")
@@ -287,7 +297,10 @@ def hav_sample_levels(ctx: Context, points, m_levels, p: hav_params | None = Non
     p = p or params()
     ml = np.ascontiguousarray(m_levels, dtype=np.int64)
     if outs is None:
-        outs = [torch.empty(int(m), dtype=torch.int32, device=points.device) for m in ml]
+        outs = [None] * len(ml)
+    if len(outs) != len(ml):
+        raise ValueError("outs must hold one tensor per level")
+    outs = [_out(o, max(0, int(m)), torch.int32, points, f"outs[{j}]") for j, (o, m) in enumerate(zip(outs, ml))]
     ptrs = (C.c_void_p * len(ml))(*[o.data_ptr() for o in outs])
     st = load().hav_sample_levels(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0],
                                   ml.ctypes.data_as(C.POINTER(C.c_int64)), len(ml), C.byref(p), ptrs,
@@ -309,7 +322,10 @@ def hav_sample_batched(ctx: Context, points, seg_offsets, seg_m, p: hav_params |
     if m.shape[1] != S:
         raise ValueError("seg_m must be (levels, segments)")
     if outs is None:
-        outs = [torch.empty(int(m[j].sum()), dtype=torch.int32, device=points.device) for j in range(L)]
+        outs = [None] * L
+    if len(outs) != L:
+        raise ValueError("outs must hold one tensor per level")
+    outs = [_out(outs[j], max(0, int(m[j].sum())), torch.int32, points, f"outs[{j}]") for j in range(L)]
     ptrs = (C.c_void_p * L)(*[o.data_ptr() for o in outs])
     st = load().hav_sample_batched(ctx.handle, C.c_void_p(points.data_ptr()),
                                    offs.ctypes.data_as(C.POINTER(C.c_int64)),
@@ -321,7 +337,9 @@ def hav_sample_batched(ctx: Context, points, seg_offsets, seg_m, p: hav_params |
 
 def hav_status_get(ctx: Context, num_segments: int = 1, stream=None):
     """Synchronise and return (status, per-segment statuses) of the last call."""
-    per = (C.c_int32 * max(1, num_segments))()
+    # the library writes one entry per segment of the last call (at most the
+    # context's segment limit)
+    per = (C.c_int32 * max(1, int(num_segments), ctx.max_segments))()
     st = load().hav_status_get(ctx.handle, _stream_handle(stream), per)
     return int(st), [int(x) for x in per[:num_segments]]
 
@@ -358,8 +376,7 @@ def hav_fps(ctx: Context, points, m: int, out=None, stream=None):
     """Farthest point sampling (the paper's comparator): m int32 indices in selection order."""
     import torch
     points = _points(points)
-    if out is None:
-        out = torch.empty(int(m), dtype=torch.int32, device=points.device)
+    out = _out(out, max(0, int(m)), torch.int32, points, "out")
     st = load().hav_fps(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0], int(m),
                         C.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(st, "hav_fps")
@@ -370,10 +387,11 @@ def hav_spacing(ctx: Context, points, idx, out=None, stream=None):
     """Squared distance from each subset point to its nearest other subset point (Fig. 3)."""
     import torch
     points = _points(points)
+    if idx.dim() != 1:
+        raise ValueError("idx must be one-dimensional")
     idx = idx.to(dtype=torch.int32, device=points.device).contiguous()
     m = idx.shape[0]
-    if out is None:
-        out = torch.empty(m, dtype=torch.float32, device=points.device)
+    out = _out(out, m, torch.float32, points, "out")
     st = load().hav_spacing(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0],
                             C.c_void_p(idx.data_ptr()), m, C.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(st, "hav_spacing")
@@ -385,10 +403,11 @@ def hav_ball_query(ctx: Context, points, centres, radius: float, nsample: int, o
     if xyz, (m, nsample, 3) float32 offsets p_k - c_j (else None)."""
     import torch
     points = _points(points)
+    if centres.dim() != 1:
+        raise ValueError("centres must be one-dimensional")
     centres = centres.to(dtype=torch.int32, device=points.device).contiguous()
     m = centres.shape[0]
-    if out is None:
-        out = torch.empty((m, int(nsample)), dtype=torch.int32, device=points.device)
+    out = _out(out, m * max(0, int(nsample)), torch.int32, points, "out", shape=(m, int(nsample)))
     offs = torch.empty((m, int(nsample), 3), dtype=torch.float32, device=points.device) if xyz else None
     st = load().hav_ball_query(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0],
                                C.c_void_p(centres.data_ptr()), m, float(np.float32(radius)), int(nsample),
@@ -433,8 +452,9 @@ def hav_sample_noalloc(points, m: int, p: hav_params | None = None, out=None, st
     import torch
     points = _points(points)
     p = p or params()
-    if out is None:
-        out = torch.empty(int(m), dtype=torch.int32, device=points.device)
+    out = _out(out, max(0, int(m)), torch.int32, points, "out")
+    if status_out is not None:
+        status_out = _out(status_out, 1, torch.int32, points, "status_out")
     sp = C.c_void_p(status_out.data_ptr()) if status_out is not None else C.c_void_p()
     st = load().hav_sample_noalloc(C.c_void_p(points.data_ptr()), points.shape[0], int(m), C.byref(p),
                                    C.c_void_p(out.data_ptr()), sp, _stream_handle(stream))

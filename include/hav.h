@@ -296,7 +296,9 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
 
 /* Synchronise `stream` and return the status of the last call enqueued on
  * this context: HAV_OK, or the first error any segment hit.  per_segment
- * (HOST, nullable, >= num_segments entries) receives each segment's status.
+ * (HOST, nullable) receives each segment's status: one entry per segment of
+ * the last call, so it must hold at least that call's num_segments entries
+ * (the context's max_segments always suffices).
  * A segment in error still gets seg_m indices (0..m-1) so that the other
  * segments' output positions stay valid. */
 hav_status hav_status_get(hav_ctx* ctx, hav_stream stream, int32_t* per_segment);

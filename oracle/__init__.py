@@ -9,6 +9,10 @@ two share no code.
 
 Every function takes and returns numpy arrays; points are (n, 3) float32,
 C-contiguous, x/y/z interleaved.
+
+HAV_ORACLE_LIB, when set, names a prebuilt library of a modified copy of
+hav_oracle.cpp to load instead of this one (the planted-mistake tests use it
+to check that the pins catch each mistake); it is never rebuilt.
 """
 from __future__ import annotations
 
@@ -21,7 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hav_oracle.cpp")
-_LIB = os.path.join(_HERE, "libhav_oracle.so")
+_LIB = os.environ.get("HAV_ORACLE_LIB") or os.path.join(_HERE, "libhav_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -84,6 +88,8 @@ def params(sigma=(5, 100), t_max=20, layers=2, layer_ratio=4, aspect=(1.0, 1.0, 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with g++ (plain IEEE binary32, no contraction)."""
+    if os.environ.get("HAV_ORACLE_LIB"):
+        return _LIB
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".{os.getpid()}.tmp"

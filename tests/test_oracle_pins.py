@@ -156,6 +156,23 @@ def test_bisection_trace_matches_numpy(oracle_mod, seed, m):
     assert tr[0]["s_star"] == s_star and tr[0]["accepted"] == acc
 
 
+@pytest.mark.parametrize("m,t_max", [(4, 1), (100, 1), (6, 3), (2000, 3)])
+def test_unfinished_search_ends_at_the_bracket(oracle_mod, m, t_max):
+    # Section 3.3 with no size accepted within t_max steps (sigma = 0): s* is
+    # the last lower end when one was found (too many voxels there), else the
+    # last upper end; both branches are taken by these cases
+    pts = scenes.uniform_box(3000, 5)
+    p = oracle_mod.params(layers=1, t_max=t_max, sigma=(0, 1))
+    _, tr = oracle_mod.sample(pts, m, p, want_trace=True)
+    _, s_hi = ind.bbox_s_hi(pts)
+    trace, s_star, acc = ind.bisection(pts, m, s_hi, sigma=(0, 1), t_max=t_max)
+    assert not acc and tr[0]["accepted"] == 0
+    assert [(F32(s), int(k)) for s, k in zip(tr[0]["s"], tr[0]["K"])] == trace
+    assert tr[0]["s_star"] == s_star
+    lo_found = any(k > m for _, k in trace)
+    assert (s_star < s_hi) if lo_found else (s_star == trace[-1][0])
+
+
 @pytest.mark.parametrize("seed,m,k", [(0, 300, 2), (1, 800, 2), (2, 100, 3), (3, 1000, 1)])
 def test_sampler_matches_numpy_restatement(oracle_mod, seed, m, k):
     rng = np.random.default_rng(seed)

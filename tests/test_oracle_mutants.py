@@ -1,7 +1,8 @@
 """Planted mistakes in the oracle, on the CPU: each plausible slip below is
 made in a copy of oracle/hav_oracle.cpp, the copy is compiled on its own, and
-the pins (tests/test_oracle_pins.py, without its slow whole-scene invariants)
-run against it.  Every mutant must fail at least one pin; a mutant that
+the pins (tests/test_oracle_pins.py, test_oracle_variants.py and
+test_oracle_search.py, without their two slow whole-scene checks) run
+against it.  Every mutant must fail at least one pin; a mutant that
 passes would mean the pins cannot tell that slip from the paper's method.
 The oracle itself is untouched: the copy is loaded through HAV_ORACLE_LIB."""
 import concurrent.futures as cf
@@ -48,6 +49,31 @@ MUTANTS = [
     ("Eq. 2: aspect ratio on the wrong axis", "v[a] = s * c.r[a];", "v[a] = s * c.r[(a + 1) % 3];"),
     ("level chain: indices of the level, not of the cloud",
      "out_concat[off + r] = orig[i];", "out_concat[off + r] = i;"),
+    # Table 6 variants, the comparators and the guided start
+    ("Table 6 mean: divided by count + 1", "/ static_cast<double>(acc.count);",
+     "/ static_cast<double>(acc.count + 1);"),
+    ("Table 6 centre: the voxel corner", "const float cen = acc.f[a] + 0.5f;", "const float cen = acc.f[a];"),
+    ("Table 6 random: SplitMix64 draw counter off by one", "(counter + 1) * 0x9E3779B97F4A7C15ull",
+     "counter * 0x9E3779B97F4A7C15ull"),
+    ("Table 6 random: low word of the draw",
+     "hi32 = static_cast<uint32_t>(random_draw(p->seed, uint64_t(i)) >> 32);",
+     "hi32 = static_cast<uint32_t>(random_draw(p->seed, uint64_t(i)));"),
+    ("Table 6 fixed voxel: the size ignored", "if (fixed) s_star = p->fixed_s;", "if (fixed) s_star = c.s_hi;"),
+    ("Fig. 3 spacing: a point is its own neighbour", "            if (q == r) continue;\n", ""),
+    ("grouping: radius inclusive", "if (d2 < r2) row[cnt++]", "if (d2 <= r2) row[cnt++]"),
+    ("grouping: padded with the last index", "for (int32_t s = cnt; s < nsample; ++s) row[s] = row[0];",
+     "for (int32_t s = cnt; s < nsample; ++s) row[s] = row[cnt - 1];"),
+    ("Eq. 1 FPS: ties to the highest index", "if (best[i] > bestd) { bestd = best[i]; arg = i; }",
+     "if (best[i] >= bestd) { bestd = best[i]; arg = i; }"),
+    ("Eq. 1 FPS: distance to the last pick only", "if (d2 < best[i]) best[i] = d2;", "best[i] = d2;"),
+    ("guided start: budget ratio without the square root", "g = guide->s * std::sqrt(ratio);",
+     "g = guide->s * ratio;"),
+    ("guided start: first guess without the square root", "g = c.s_hi / std::sqrt(static_cast<float>(m_l));",
+     "g = c.s_hi / static_cast<float>(m_l);"),
+    ("guided start: doubling up to the top itself", "else if (up && lo * 2.0f < hi) s = lo * 2.0f;",
+     "else if (up && lo * 2.0f <= hi) s = lo * 2.0f;"),
+    ("guided start: doubling again after a low count", "                hi = s;\n                up = false;",
+     "                hi = s;"),
 ]
 
 
@@ -60,8 +86,9 @@ def _run_mutant(tmp, k, old, new, src):
     subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
                     "-o", lib, os.path.join(d, "o.cpp")], check=True, capture_output=True)
     env = dict(os.environ, HAV_ORACLE_LIB=lib)
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
-                        "-p", "no:cacheprovider", "-k", "not output_invariants"],
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "tests/test_oracle_variants.py",
+                        "tests/test_oracle_search.py", "-x", "-q", "-p", "no:cacheprovider",
+                        "-k", "not output_invariants and not exact_at_scale"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode
 

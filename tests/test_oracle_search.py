@@ -27,6 +27,23 @@ def test_guided_matches_numpy_restatement(oracle_mod, seed, m, layers):
         assert _trace_pairs(tr[0][l]) == [(F32(s), int(k)) for s, k in wtr[0][l]], l
 
 
+@pytest.mark.parametrize("m", [4, 16])
+def test_guided_doubling_stops_below_the_top(oracle_mod, m):
+    # m a power of 4: the first guess s_hi / sqrt(m) = s_hi / 2^j is exact, and
+    # with few voxels wanted every doubling stays above k_max up to s_hi / 2;
+    # there 2 lo equals s_hi, which is not below the top, so the search bisects
+    pts = scenes.uniform_box(3000, seed=70)
+    got, tr = oracle_mod.sample_levels(pts, [m], oracle_mod.params(layers=1, search="guided"),
+                                       want_trace=True)
+    want, wtr = ind.hav_reference_levels_small(pts, [m], search="guided", layers=1)
+    pairs = _trace_pairs(tr[0][0])
+    assert np.array_equal(got[0], want[0])
+    assert pairs == [(F32(s), int(k)) for s, k in wtr[0][0]]
+    _, s_hi = ind.bbox_s_hi(pts)
+    assert all(s < s_hi for s, _ in pairs)  # the top itself is never evaluated
+    assert any(s == F32(s_hi * F32(0.5)) for s, _ in pairs)  # the doubling reached s_hi / 2
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_guided_level_chain_matches_numpy_restatement(oracle_mod, seed):
     # the start of every later search comes from the previous one, across levels

@@ -94,3 +94,5 @@ def test_argument_errors_need_no_device(libhav):
     assert L.hav_workspace_bytes(1 << 20, 1) > 0
     assert L.hav_context_get_tuning(None, None) == hav.HAV_ERR_INVALID
     assert L.hav_context_set_tuning(None, None) == hav.HAV_ERR_INVALID
+    n = ctypes.c_uint64(7)
+    assert L.hav_context_launches(None, ctypes.byref(n)) == hav.HAV_ERR_INVALID and n.value == 7

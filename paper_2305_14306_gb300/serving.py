@@ -13,6 +13,14 @@ completion event.
 
 The plain per-cloud path is the same loop with one slot and one request per
 call.  Either way every request's indices equal a stand-alone call's.
+
+Failures stay with their request.  A request whose cloud the library rejects
+(a non-finite coordinate, a key out of range) gets that status in its
+result while the other requests of the same call keep their exact indices
+(the library contains such errors to their segment); only a failure of the
+whole call (a device wait that gave up, a CUDA error) stops the loop.  A
+request may carry a deadline: if it is still waiting for a slot that long
+after its arrival, it is dropped with the status EXPIRED and never launched.
 This module only orchestrates: every step of the sampling runs in libhav's
 kernels.
 """
@@ -27,19 +35,63 @@ import numpy as np
 from . import hav
 
 
+EXPIRED = -1  # a request dropped before launch: its deadline passed while it waited
+
+
 @dataclass
 class Request:
     rid: int
     arrival: float          # seconds after the start of the run
     points: object          # (n, 3) float32 torch tensor in pinned host memory
     m: int                  # budget (one level)
+    deadline: float | None = None  # longest wait for a slot (seconds after arrival); None: no limit
 
 
 @dataclass
 class Result:
     indices: np.ndarray
     latency: float          # seconds from arrival to completion seen by the host
-    batch: int              # requests in the call that served it
+    batch: int              # requests in the call that served it (0: never launched)
+    status: int = 0         # hav status of the request's segment (HAV_OK), or EXPIRED
+
+
+# the statuses that void a whole call rather than one segment of it
+_CALL_FAILURES = (hav.HAV_ERR_INVALID, hav.HAV_ERR_TIMEOUT, hav.HAV_ERR_NOMEM, hav.HAV_ERR_CUDA)
+
+
+def expire(waiting, now: float, results: dict) -> int:
+    """Drop the waiting requests whose deadline has passed (results get EXPIRED);
+    returns how many were dropped.  The others keep their order."""
+    keep, dropped = [], 0
+    while waiting:
+        r = waiting.popleft()
+        if r.deadline is not None and now - r.arrival > r.deadline:
+            results[r.rid] = Result(np.empty(0, dtype=np.int32), now - r.arrival, 0, EXPIRED)
+            dropped += 1
+        else:
+            keep.append(r)
+    waiting.extend(keep)
+    return dropped
+
+
+def take_batch(waiting, max_segments: int, slot_points: int) -> list:
+    """First come, first served: the waiting requests that fit one call of a
+    slot (at most max_segments clouds and slot_points points in total)."""
+    batch, pts = [], 0
+    while waiting and len(batch) < max_segments and pts + waiting[0].points.shape[0] <= slot_points:
+        r = waiting.popleft()
+        batch.append(r)
+        pts += r.points.shape[0]
+    return batch
+
+
+def collect(batch, offsets, h_out, status: int, per_segment, now: float, results: dict):
+    """Results of a finished call: each request its slice of the indices and its
+    segment's status; a failure of the whole call raises."""
+    if status in _CALL_FAILURES:
+        raise hav.HavError(status, "serving batch")
+    for k, (r, a, b) in enumerate(zip(batch, offsets[:-1], offsets[1:])):
+        results[r.rid] = Result(h_out[a:b].copy(), now - r.arrival, len(batch), int(per_segment[k]))
 
 
 @dataclass
@@ -105,11 +157,7 @@ class Server:
 
     def _finish(self, slot: _Slot, now: float, results: dict):
         st, per = hav.hav_status_get(slot.ctx, len(slot.batch), stream=slot.stream)
-        if st != hav.HAV_OK:
-            raise hav.HavError(st, "serving batch")
-        ho = slot.h_out.numpy()
-        for r, a, b in zip(slot.batch, slot.offsets[:-1], slot.offsets[1:]):
-            results[r.rid] = Result(ho[a:b].copy(), now - r.arrival, len(slot.batch))
+        collect(slot.batch, slot.offsets, slot.h_out.numpy(), st, per, now, results)
         slot.batch = []
         slot.event = None
 
@@ -121,12 +169,13 @@ class Server:
                 raise ValueError(f"request {r.rid} has more points than a slot holds")
         waiting = collections.deque()
         results = {}
+        deadlines = any(r.deadline is not None for r in pending)
         t0 = clock()
         while pending or waiting or any(s.batch for s in self.slots):
             now = clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
-            progressed = False
+            progressed = deadlines and expire(waiting, now, results) > 0
             for s in self.slots:
                 if s.batch and s.event.query():
                     self._finish(s, clock() - t0, results)
@@ -134,13 +183,7 @@ class Server:
             for s in self.slots:
                 if s.batch or not waiting:
                     continue
-                batch, pts = [], 0
-                while waiting and len(batch) < self.max_segments and \
-                        pts + waiting[0].points.shape[0] <= self.slot_points:
-                    r = waiting.popleft()
-                    batch.append(r)
-                    pts += r.points.shape[0]
-                self._launch(s, batch)
+                self._launch(s, take_batch(waiting, self.max_segments, self.slot_points))
                 progressed = True
             if not progressed:
                 time.sleep(20e-6)

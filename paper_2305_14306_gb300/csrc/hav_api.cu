@@ -298,8 +298,8 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
             (params->select == HAV_SELECT_CENTRE_CLOSEST || params->select == HAV_SELECT_RANDOM);
         // grid kernel for [0, j0), clusters for [j0, j1), single CTAs for [j1, L).
         // A level goes to single CTAs when it also has more segments than
-        // clusters fit at once, or only tiny segments (measured on GB300: one
-        // CTA per segment wins for many segments, an 8-CTA cluster for a few
+        // 8-CTA clusters fit at once, or only tiny segments (measured on GB300:
+        // one CTA per segment wins for many segments, a cluster for a few
         // above kSoloAlone points); later levels are no larger, so they follow.
         int j0 = num_levels, j1 = num_levels;
         for (int j = 0; j < num_levels; ++j) {

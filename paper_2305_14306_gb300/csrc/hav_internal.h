@@ -199,8 +199,7 @@ int launch_chain(const Plan& plan, cudaStream_t stream);
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3],
                  unsigned char* ws, const Layout& lay, int64_t* K, int* launched, cudaStream_t stream);
 int fps_coresident_blocks(int device);
-// Small levels on thread-block clusters (hav_small.cu): clusters that fit at
-// once (<= 0: none), and a launch of levels [first_level, plan.L).
+// Small levels on thread-block clusters (hav_small.cu).
 // small_clusters(device, q): clusters of q CTAs (8 or 16) that run at once
 // (<= 0: none), after setting the kernel's launch attributes; q = 1 sets the
 // single-CTA kernel's (1, or -1 on failure).  launch_small runs levels

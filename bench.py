@@ -171,6 +171,8 @@ class Clocks:
 
     def stop(self):
         if self.p is None:
+            self.f.close()
+            os.unlink(self.f.name)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.p.terminate()
         try:
@@ -180,6 +182,7 @@ class Clocks:
         self.f.flush()
         self.f.seek(0)
         rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        self.f.close()
         os.unlink(self.f.name)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]

@@ -51,3 +51,23 @@ def test_algorithmic_bytes_by_hand():
 def test_whole_job_single_rank():
     t, v = bench.whole_job(0.5, 2_000_000, 1)
     assert t == 0.5 and abs(v - 4.0) < 1e-12
+
+
+def test_clock_sampler_without_nvidia_smi_cleans_up(monkeypatch):
+    def no_smi(*a, **k):
+        raise FileNotFoundError("nvidia-smi")
+    monkeypatch.setattr(bench.subprocess, "Popen", no_smi)
+    c = bench.Clocks(0)
+    name = c.f.name
+    out = c.stop()
+    assert out["samples"] == 0 and out["sm_mhz"] is None and not os.path.exists(name)
+    assert not bench.clocks_bad(out)
+
+
+def test_clocks_bad_rules():
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench.clocks_bad(ok)
+    assert not bench.clocks_bad({**ok, "reasons": ["sw_power_cap"]})  # kept and noted
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_bad({**ok, "reasons": [r]})
+    assert bench.clocks_bad({**ok, "sm_mhz": 1000.0})  # stuck well below max with no reason

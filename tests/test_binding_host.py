@@ -32,3 +32,17 @@ def test_points_must_be_a_contiguous_cuda_float_array():
     for bad in (torch.zeros(4, 3), torch.zeros(4, 2), torch.zeros(4, 3, dtype=torch.float64)):
         with pytest.raises(ValueError):
             hav._points(bad)
+
+
+def test_a_missing_library_fails_loudly():
+    # no CPU fallback: without libhav.so the binding raises (fresh process, so
+    # that no earlier load is cached)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("from paper_2305_14306_gb300 import hav\n"
+            "try:\n    hav.load('/nonexistent/libhav.so')\nexcept RuntimeError as e:\n"
+            "    print('raised', e)\nelse:\n    print('loaded')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("raised"), r.stdout + r.stderr

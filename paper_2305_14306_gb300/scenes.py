@@ -37,23 +37,45 @@ def uniform_box(n: int = 16384, seed: int = 0, lo=KITTI_LO, hi=KITTI_HI) -> np.n
     return np.ascontiguousarray(p.astype(np.float32))
 
 
-def _ray_box_hits(o_dirs: np.ndarray, boxes: np.ndarray) -> np.ndarray:
+def _ray_box_hits(o_dirs: np.ndarray, boxes: np.ndarray, az: np.ndarray | None = None) -> np.ndarray:
     """Nearest positive ray parameter against axis-aligned boxes (slab test).
 
     o_dirs: (R, 3) unit directions from the origin; boxes: (B, 6) min/max.
     Returns (R,) distances, inf where no box is hit.
+
+    az (optional): the rays form a ring-major grid (R = rings x len(az)) whose
+    k-th column has azimuth az[k], ascending.  A box whose footprint does not
+    hold the origin spans the azimuths of its footprint corners, so only the
+    columns inside that range (widened by 1e-6 rad) can hit it; the others are
+    skipped.  The test of every ray that is evaluated is the same arithmetic,
+    so the result does not depend on the culling.
     """
     R = o_dirs.shape[0]
     best = np.full(R, np.inf)
+    cols = None if az is None else az.shape[0]
     with np.errstate(divide="ignore", invalid="ignore"):
         inv = 1.0 / o_dirs
         for b in boxes:
-            t1 = b[:3][None, :] * inv
-            t2 = b[3:][None, :] * inv
+            sel = slice(None)
+            if cols is not None and not (b[0] <= 0.0 <= b[3] and b[1] <= 0.0 <= b[4]):
+                cx = np.array([b[0], b[3], b[0], b[3]])
+                cy = np.array([b[1], b[1], b[4], b[4]])
+                ang = np.arctan2(cy, cx)
+                if ang.max() - ang.min() < np.pi:  # no wrap through +-pi
+                    k0 = int(np.searchsorted(az, ang.min() - 1e-6, side="left"))
+                    k1 = int(np.searchsorted(az, ang.max() + 1e-6, side="right"))
+                    if k0 >= k1:
+                        continue
+                    rows = R // cols
+                    sel = (np.arange(rows)[:, None] * cols + np.arange(k0, k1)[None, :]).reshape(-1)
+            iv = inv[sel]
+            t1 = b[:3][None, :] * iv
+            t2 = b[3:][None, :] * iv
             tmin = np.nanmax(np.minimum(t1, t2), axis=1)
             tmax = np.nanmin(np.maximum(t1, t2), axis=1)
             hit = (tmax >= 0) & (tmin <= tmax) & (tmin > 0)
-            best = np.where(hit & (tmin < best), tmin, best)
+            cur = best[sel]
+            best[sel] = np.where(hit & (tmin < cur), tmin, cur)
     return best
 
 
@@ -84,7 +106,7 @@ def lidar_scene(seed: int = 0, rings: int = 64, az_steps: int = 512, fov_deg: fl
     t = np.full(d.shape[0], np.inf)
     down = d[:, 2] < 0
     t[down] = ground_z / d[down, 2]
-    tb = _ray_box_hits(d, boxes)
+    tb = _ray_box_hits(d, boxes, az)
     t = np.minimum(t, tb)
     t = t + rng.normal(0.0, noise, size=t.shape)
     ok = np.isfinite(t) & (t > 0) & (t <= max_range)

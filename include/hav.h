@@ -376,11 +376,18 @@ const char* hav_status_string(hav_status s);
  * Scratch: a static __device__ array of 8 MiB inside libhav.so, enough for
  * one cloud of at most 32,768 points; every GPU that loads the library holds
  * it until the process exits.  n > 32,768 returns HAV_ERR_NOMEM and enqueues
- * nothing.  The first call on a device looks up the array's device address
- * and the launch grid for that device (no allocation); make that first call
+ * nothing.  Every call looks up the array's device address (no allocation).
+ * The first call on a device, and the first after the library's module is
+ * loaded again in a new context (after cudaDeviceReset), also sets the
+ * sampler kernel's launch attribute and sizes its grid; make that first call
  * before any stream capture.  All calls on a device share the one array:
  * calls that overlap on the GPU (different streams, or host threads without
  * ordering) race and corrupt each other's results; serialise them.
+ *
+ * The call runs the grid-wide sampler without speculative look-ahead (one
+ * bisection step per pass; the scratch holds no room for extra candidate
+ * tables): the indices, status and search are those of hav_sample, but a
+ * level takes more passes, so a call is slower than hav_sample's.
  *
  * points: device, n*3 floats; out_idx: device, m int32 (ascending indices);
  * status_out: device int32 or NULL, receives the call's hav_status when the

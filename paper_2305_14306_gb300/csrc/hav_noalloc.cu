@@ -16,7 +16,6 @@
 
 #include <cuda_runtime.h>
 
-#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -34,34 +33,38 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 struct DeviceSetup {
-    std::atomic<int> ready{0};
-    unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
-    int nblocks = 0;
+    unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch at the last set-up
+    int nblocks = 0;                   // co-resident blocks of the sampler kernel on this device
 };
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
-// Once per device, with that device current: resolve the array's device
-// address (in host code its name is only a stand-in) and size the grid.
-hav_status setup_device(int dev, DeviceSetup** out) {
+// Every call, with the device current: resolve the array's device address
+// (in host code its name is only a stand-in).  The lookup allocates nothing.
+// The launch set-up (the kernel's shared-memory attribute, the grid size) is
+// kept per device and redone whenever the address changes, which is what
+// happens when the module is loaded again in a new context (after
+// cudaDeviceReset, or in another primary context).
+hav_status setup_device(int dev, unsigned char** scratch, int* nblocks) {
     if (dev < 0 || dev >= kMaxDevices) return HAV_ERR_INVALID;
-    DeviceSetup& s = g_setup[dev];
-    if (!s.ready.load(std::memory_order_acquire)) {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!s.ready.load(std::memory_order_relaxed)) {
-            void* ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-                cudaGetLastError();
-                return HAV_ERR_CUDA;
-            }
-            const int nb = havk::max_coresident_blocks(dev);
-            if (nb < 1) return HAV_ERR_CUDA;
-            s.scratch = static_cast<unsigned char*>(ptr);
-            s.nblocks = nb;
-            s.ready.store(1, std::memory_order_release);
-        }
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return HAV_ERR_CUDA;
     }
-    *out = &s;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    DeviceSetup& s = g_setup[dev];
+    if (s.scratch != ptr || s.nblocks < 1) {
+        const int nb = havk::max_coresident_blocks(dev);
+        if (nb < 1) {
+            cudaGetLastError();
+            return HAV_ERR_CUDA;
+        }
+        s.scratch = static_cast<unsigned char*>(ptr);
+        s.nblocks = nb;
+    }
+    *scratch = s.scratch;
+    *nblocks = s.nblocks;
     return HAV_OK;
 }
 
@@ -96,8 +99,9 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
     if (reinterpret_cast<uintptr_t>(points) % 4 != 0) return HAV_ERR_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HAV_ERR_CUDA;
-    DeviceSetup* ds = nullptr;
-    st = setup_device(dev, &ds);
+    unsigned char* scratch = nullptr;
+    int nblocks = 0;
+    st = setup_device(dev, &scratch, &nblocks);
     if (st != HAV_OK) return st;
 
     const havk::Layout lay = havk::make_layout(kNoAllocMaxPoints, 1, /*spec_room=*/false);
@@ -106,13 +110,13 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
     cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);
     // The header (barrier, status words, bounding-box codes) must start at
     // zero; every other region is cleared by the kernel before it is read.
-    if (cudaMemsetAsync(ds->scratch + lay.barrier, 0, lay.zero_bytes, strm) != cudaSuccess)
+    if (cudaMemsetAsync(scratch + lay.barrier, 0, lay.zero_bytes, strm) != cudaSuccess)
         return HAV_ERR_CUDA;
     if (m > 0) {
         havk::Plan plan;
         std::memset(&plan, 0, sizeof plan);
         plan.points = points;
-        plan.ws = ds->scratch;
+        plan.ws = scratch;
         plan.lay = lay;
         plan.S = 1;
         plan.L = 1;
@@ -121,7 +125,7 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
         plan.t_max = params->t_max;
         plan.sigma_num = params->sigma_num;
         plan.sigma_den = params->sigma_den;
-        plan.nblocks = ds->nblocks;
+        plan.nblocks = nblocks;
         plan.chunk_min = havk::kChunkMin;
         for (int a = 0; a < 3; ++a) plan.aspect[a] = params->aspect[a];
         plan.select = params->select;
@@ -135,7 +139,7 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
         if (havk::launch_chain(plan, strm) < 0) return HAV_ERR_CUDA;
     }
     if (status_out) {
-        const havk::GlobalHdr* gh = reinterpret_cast<const havk::GlobalHdr*>(ds->scratch + lay.ghdr);
+        const havk::GlobalHdr* gh = reinterpret_cast<const havk::GlobalHdr*>(scratch + lay.ghdr);
         if (cudaMemcpyAsync(status_out, &gh->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, strm) !=
             cudaSuccess)
             return HAV_ERR_CUDA;

@@ -63,6 +63,22 @@ WORKLOADS = {
                 "n": None, "levels": None},
 }
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
+L2_NOTE = "flushed before every step (256 MB read sweep: L2 holds no dirty lines when a step starts)"
+
+
+class L2Flush:
+    """Evicts L2 between timed steps by reading a 256 MB buffer (twice the L2).
+    A read sweep leaves only clean lines behind, so no write-back of earlier
+    data is charged to the next step's kernels (a write sweep would leave
+    about 129 MB of dirty lines that the step itself then writes back)."""
+
+    def __init__(self, torch):
+        self.buf = torch.zeros(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        self.acc = torch.zeros((), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()  # the zero-fill's dirty lines go out before any timing
+
+    def sweep(self):
+        self.acc.add_(self.buf.sum())
 
 
 def make_scene(name: str, seed: int) -> np.ndarray:
@@ -319,9 +335,11 @@ def scene_parallel_oracle(clouds, m_levels, search, reps=3):
             res = pool.map_async(_oracle_cloud, jobs, chunksize=1).get(timeout=600)
         dt = time.perf_counter() - t0
     return total * reps / dt / 1e6, cores, res
-def run_batched(args, world, rank, local):
+def run_batched(args, world, rank, local, sub=False):
     """64 clouds per step: one hav_sample_batched call, the same call from a
-    CUDA graph, and 64 plain per-cloud hav_sample_levels calls, at identical outputs."""
+    CUDA graph, and 64 plain per-cloud hav_sample_levels calls, at identical outputs.
+    sub=True: return rank 0's result (no print, no host-core oracle) for the
+    default line's "batch64" object."""
     import torch
     import torch.distributed as dist
     from paper_2305_14306_gb300 import hav
@@ -340,7 +358,7 @@ def run_batched(args, world, rank, local):
     per_outs = [[torch.empty(int(seg_m[j, s]), dtype=torch.int32, device="cuda") for j in range(2)]
                 for s in range(64)]
     views = [d_pts[int(offs[s]):int(offs[s + 1])] for s in range(64)]
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
 
     def step_batched(strm=stream):
         hav.hav_sample_batched(ctx, d_pts, offs, seg_m, p, outs=outs, stream=strm)
@@ -388,7 +406,7 @@ def run_batched(args, world, rank, local):
     def time_it(fn, steps):
         ms = []
         for _ in range(steps):
-            flush.zero_()
+            flush.sweep()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             fn()
@@ -411,7 +429,7 @@ def run_batched(args, world, rank, local):
     clocks = clk.stop()
     tb, value = whole_job(sum(ms_b) / 1e3, total * len(ms_b), world, device="cuda")
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not sub:
         try:
             v_cpu, cores, res = scene_parallel_oracle(clouds, [seg_m[:, s] for s in range(64)], args.search)
         except Exception as e:  # reported, never silently replaced
@@ -433,7 +451,7 @@ def run_batched(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "batch64", "desc": WORKLOADS["batch64"]["desc"], "points": total,
-                       "segments": 64, "levels": 2, "l2": "flushed before every step (256 MB write)",
+                       "segments": 64, "levels": 2, "l2": L2_NOTE,
                        "search": args.search},
             "scenes_per_s": 64 * len(ms_b) / (sum(ms_b) / 1e3),
             "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
@@ -449,9 +467,12 @@ def run_batched(args, world, rank, local):
             "launches_per_step": launches_b / len(ms_b),
             "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
+        if not sub:
+            print(json.dumps(line), flush=True)
     ctx.close()
     ctx1.close()
+    if sub:
+        return line if rank == 0 else None
     return 0
 
 
@@ -571,7 +592,7 @@ def run_variants(args, world, rank, local):
     import torch
     from paper_2305_14306_gb300 import hav
 
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
     steps = max(5, min(args.steps, 100))
     rows = []
     for case, pts_np, m in (("C1 uniform 16,384 -> 4,096", scenes.uniform_box(16384, seed=0), 4096),
@@ -591,7 +612,7 @@ def run_variants(args, world, rank, local):
                     hav.hav_sample_xyz(ctx, d, m, p, out=idx, xyz=xyz)
                 ev = []
                 for _ in range(steps):
-                    flush.zero_()
+                    flush.sweep()
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     a.record()
                     hav.hav_sample_xyz(ctx, d, m, p, out=idx, xyz=xyz)
@@ -613,7 +634,7 @@ def run_variants(args, world, rank, local):
                 "steps": steps, "warmup": 3, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "variants", "desc": WORKLOADS["variants"]["desc"],
-                           "l2": "flushed before every step (256 MB write)",
+                           "l2": L2_NOTE,
                            "fixed_s": "the adaptive search's s* of the same cloud"},
                 "rows": rows}
         print(json.dumps(line), flush=True)
@@ -679,7 +700,7 @@ def run_grouping(args, world, rank, local):
     import torch
     from paper_2305_14306_gb300 import hav
 
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
     steps = max(5, min(args.steps, 50))
     rows = []
     for case, pts_np, m, radius, ns in (
@@ -695,7 +716,7 @@ def run_grouping(args, world, rank, local):
             hav.hav_ball_query(ctx, d, centres, radius, ns, out=out)
         ev = []
         for _ in range(steps):
-            flush.zero_()
+            flush.sweep()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             hav.hav_ball_query(ctx, d, centres, radius, ns, out=out)
@@ -715,22 +736,24 @@ def run_grouping(args, world, rank, local):
                 "n_gpus": world, "steps": steps, "warmup": 3, "ms_per_step": tot_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "grouping", "desc": WORKLOADS["grouping"]["desc"],
-                           "l2": "flushed before every step (256 MB write)"}, "rows": rows}
+                           "l2": L2_NOTE}, "rows": rows}
         print(json.dumps(line), flush=True)
     return 0
 
 
 # ----------------------------------------------------------------- serving arm
-def run_serving(args, world, rank, local):
+def run_serving(args, world, rank, local, sub=False, requests=None):
     """C5: closed-loop capacity and open-loop latency (Poisson arrivals at 0.5, 0.8
-    and 0.95 x the plain path's capacity) of the served path vs the plain per-cloud path."""
+    and 0.95 x the plain path's capacity) of the served path vs the plain per-cloud path.
+    sub=True: `requests` requests, rank 0's result returned (no print, no
+    host-core oracle) for the default line's "serving" object."""
     import torch
     from paper_2305_14306_gb300 import hav, serving
 
     rng = np.random.default_rng(1000 + rank)
     pool_n = scenes.log_uniform_sizes(16, 10_000, 1_000_000, seed=1000 + rank)
     pool = [torch.from_numpy(scenes.scene_for(int(n), seed=5000 + i)).pin_memory() for i, n in enumerate(pool_n)]
-    R = max(20, min(args.steps, 2000))
+    R = int(requests) if requests else max(20, min(args.steps, 2000))
     picks = rng.integers(0, len(pool), size=R)
     choice = rng.integers(0, 3, size=R)
 
@@ -781,7 +804,7 @@ def run_serving(args, world, rank, local):
         plain.close()
     pts_total = int(sum(pool[picks[i]].shape[0] for i in range(R)))
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not sub:
         # the first 48 requests on the host cores, one scene per process
         k = min(R, 48)
         reqs = [(pool[picks[i]].numpy(), [[n // 4, n // 16, min(4096, n)][choice[i]]])
@@ -813,7 +836,10 @@ def run_serving(args, world, rank, local):
             "cpu_baseline": cpu,
             "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
+        if not sub:
+            print(json.dumps(line), flush=True)
+    if sub:
+        return line if rank == 0 else None
     return 0
 
 
@@ -833,6 +859,10 @@ def main():
     ap.add_argument("--search", choices=["bisect", "guided"], default="bisect",
                     help="start of the voxel-size search: bisection over (0, s_hi] (default), or "
                          "guided by the cloud's previous search")
+    ap.add_argument("--no-sub-workloads", action="store_true",
+                    help="default workload only: skip the batch64 and serving objects of the line")
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="requests of the serving object in the default line")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON cache of autotuned knobs (default: always sweep, write nothing)")
     args = ap.parse_args()
@@ -873,7 +903,7 @@ def main():
     stream = torch.cuda.current_stream()
     d_pts = torch.from_numpy(pts).cuda()
     outs = [torch.empty(m, dtype=torch.int32, device="cuda") for m in ml]
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
 
     def step(pp=p):
         hav.hav_sample_levels(ctx, d_pts, ml, pp, outs=outs, stream=stream)
@@ -906,7 +936,7 @@ def main():
         k0 = ctx.launches()
         t0 = time.perf_counter()
         for k in range(steps):
-            flush.zero_()
+            flush.sweep()
             evs[k][0].record(stream)
             step(pp)
             evs[k][1].record(stream)
@@ -939,7 +969,7 @@ def main():
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
     e2e_ms = []
     for k in range(e2e_steps + 3):
-        flush.zero_()
+        flush.sweep()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         d_pts.copy_(h_pts, non_blocking=True)
@@ -1010,7 +1040,7 @@ def main():
             "config": {"workload": args.workload, "desc": w["desc"], "n": n, "levels": ml,
                        "layers": p.layers, "sigma": "5/100", "t_max": p.t_max, "search": args.search,
                        "bisection_steps": int(sum(int(t["iters"]) for t in traces)),
-                       "l2": "flushed before every step (256 MB write)",
+                       "l2": L2_NOTE,
                        "parallelism": "replicas" if world > 1 else "single"},
             "scenes_per_s": world * args.steps / total_s,
             "p50_ms": p50, "p99_ms": p99,
@@ -1026,8 +1056,23 @@ def main():
         }
         if other is not None:
             line["search_guided"] = other
-        print(json.dumps(line), flush=True)
     ctx.close()
+    subs = {}
+    if world == 1 and args.workload == "indoor-1m" and not args.no_sub_workloads:
+        # the batched (C4) and served (C5) forms against the plain per-cloud
+        # path, on the same GPU in the same run, summarised beside the headline
+        b = run_batched(args, world, rank, local, sub=True)
+        subs["batch64"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "scenes_per_s", "p50_ms", "p99_ms",
+                                             "graph", "per_cloud", "speedup_vs_per_cloud", "identical_outputs",
+                                             "tuning", "gpu_launches", "launches_per_step", "clocks")}
+        subs["batch64"]["config"] = b["config"]
+        srv = run_serving(args, world, rank, local, sub=True, requests=args.serve_requests)
+        subs["serving"] = {k: srv[k] for k in ("value", "unit", "scenes_per_s", "plain", "speedup_vs_per_cloud",
+                                               "open_loop", "identical_outputs", "clocks")}
+        subs["serving"]["config"] = srv["config"]
+    if rank == 0:
+        line.update(subs)
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0

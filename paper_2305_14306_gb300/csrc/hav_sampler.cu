@@ -111,6 +111,12 @@ struct Smem {
     unsigned epoch;
     unsigned list_n;
     int set_clean;  // 1 when every slot of the block set is empty
+    // level 0 of one bucketed cloud: the Morton cells [own_lo, own_hi] whose
+    // points all lie in this block's work item (own_on), and per pass the keys
+    // that go to the global table (rest_n) and the owned ones counted here
+    int own_on, own_lo, own_hi;
+    unsigned rest_n;
+    unsigned xcnt[kMaxCand];
     int ntimes;
     int was_clean;
     int cut_seg;
@@ -255,21 +261,54 @@ __device__ __forceinline__ int item_range(const Smem& st, int S, int it, int* a,
 }
 
 // 16^3 Morton cell of a point inside its segment's bounding box (layout only).
-__device__ __forceinline__ unsigned bucket_of(const float p[3], const float mn[3], const float mx[3]) {
-    unsigned c[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float e = mx[a] - mn[a];
-        int q = (e > 0.0f) ? static_cast<int>((p[a] - mn[a]) / e * 16.0f) : 0;
-        q = q < 0 ? 0 : (q > 15 ? 15 : q);
-        c[a] = static_cast<unsigned>(q);
-    }
+// The cell index along an axis is a non-decreasing function of the
+// coordinate (every rounded step is monotone), which the ownership test of
+// the bisection passes relies on.
+__device__ __forceinline__ unsigned bucket_axis(float x, float mn, float mx) {
+    const float e = __fsub_rn(mx, mn);
+    if (!(e > 0.0f)) return 0u;
+    float q = __fmul_rn(__fdiv_rn(__fsub_rn(x, mn), e), 16.0f);
+    q = fminf(fmaxf(q, -1.0f), 16.0f);  // (NaN-free: x, mn, mx finite)
+    const int c = static_cast<int>(q);
+    return static_cast<unsigned>(c < 0 ? 0 : (c > 15 ? 15 : c));
+}
+__device__ __forceinline__ unsigned morton16(unsigned cx, unsigned cy, unsigned cz) {
     unsigned id = 0;
 #pragma unroll
     for (int bit = 0; bit < 4; ++bit)
-        id |= (((c[0] >> bit) & 1u) << (3 * bit)) | (((c[1] >> bit) & 1u) << (3 * bit + 1)) |
-              (((c[2] >> bit) & 1u) << (3 * bit + 2));
+        id |= (((cx >> bit) & 1u) << (3 * bit)) | (((cy >> bit) & 1u) << (3 * bit + 1)) |
+              (((cz >> bit) & 1u) << (3 * bit + 2));
     return id;
+}
+__device__ __forceinline__ unsigned bucket_of(const float p[3], const float mn[3], const float mx[3]) {
+    return morton16(bucket_axis(p[0], mn[0], mx[0]), bucket_axis(p[1], mn[1], mx[1]), bucket_axis(p[2], mn[2], mx[2]));
+}
+
+// Whether every point of the voxel `key` (Eq. 2 cell of grid g) lies in Morton
+// cells [own_lo, own_hi] of the bucketing, all of whose points this block
+// processes: then no other block has a point in the voxel, and the block
+// counts it without the global table.  A point x of the voxel along an axis
+// has f <= RN(x / v) < f + 1, so v (f - ulp(f) / 2) <= x < v (f + 1); the box
+// [v f, v (f + 1)] is widened by 2^-20 (|end| + v) on both sides, which covers
+// that half ulp and the rounding of the products.  Morton order is monotone in
+// each cell coordinate, so the box's cells lie between the codes of its two
+// corner cells.
+__device__ __forceinline__ bool voxel_owned(unsigned long long key, const Grid& g, const float mn[3],
+                                            const float mx[3], int own_lo, int own_hi) {
+    unsigned c0[3], c1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float f = __fadd_rn(static_cast<float>(static_cast<unsigned>((key >> (21 * a)) & 0x1fffffull)), g.fmin[a]);
+        const float v = g.v[a];
+        float lo = __fmul_rn(v, f);
+        float hi = __fmul_rn(v, __fadd_rn(f, 1.0f));
+        lo = __fsub_rn(lo, __fmul_rn(__fadd_rn(fabsf(lo), v), 9.5367431640625e-07f));
+        hi = __fadd_rn(hi, __fmul_rn(__fadd_rn(fabsf(hi), v), 9.5367431640625e-07f));
+        c0[a] = bucket_axis(lo, mn[a], mx[a]);
+        c1[a] = bucket_axis(hi, mn[a], mx[a]);
+    }
+    return static_cast<int>(morton16(c0[0], c0[1], c0[2])) >= own_lo &&
+           static_cast<int>(morton16(c1[0], c1[1], c1[2])) <= own_hi;
 }
 
 // Size evaluated by node c (heap order) of the bisection subtree below
@@ -446,6 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
 
     for (int j = 0; j < P.L; ++j) {
         level_setup(P, j, st);
+        if (tid == 0) st.own_on = 0;
         float4* ord = d.ord[j & 1];
         const int32_t* orig_in = (j == 0) ? nullptr : d.orig[(j - 1) & 1];
         uint32_t* taken = d.taken[j & 1];
@@ -598,6 +638,31 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     before += c4[k];
                 }
                 __syncthreads();
+                // the Morton cells this block's work item holds whole: from the
+                // first cell starting at or after the item's start to the last
+                // one ending at or before its end (cells are laid out in Morton
+                // order; the item is the same in every pass of this level)
+                if (tid == 0 && st.items_total <= static_cast<int>(nb) &&
+                    static_cast<int>(blockIdx.x) < st.items_total) {
+                    int ia, ib;
+                    item_range(st, S, blockIdx.x, &ia, &ib);
+                    int lo = 0, hi = 4096;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (hb[mid] >= static_cast<unsigned>(ia)) hi = mid; else lo = mid + 1;
+                    }
+                    const int c_lo = lo;
+                    lo = 0;
+                    hi = 4096;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        const unsigned end = (mid + 1 < 4096) ? hb[mid + 1] : static_cast<unsigned>(NL);
+                        if (end > static_cast<unsigned>(ib)) hi = mid; else lo = mid + 1;
+                    }
+                    st.own_lo = c_lo;
+                    st.own_hi = lo - 1;
+                    st.own_on = (c_lo <= lo - 1) ? 1 : 0;
+                }
                 for (int b = tid; b < 4096; b += kThreads)
                     if (h[b]) h[b] = hb[b] + atomicAdd(&d.bkt[4096 + b], h[b]);
                 __syncthreads();
@@ -775,7 +840,9 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     if (tid == 0) {
                         st.list_n = 0u;
                         st.rbits = 0u;
+                        st.rest_n = 0u;
                     }
+                    if (tid < kMaxCand) st.xcnt[tid] = 0u;
                     __syncthreads();
                     const int cap = st.cap_log2[s];
                     unsigned long long* Tb = d.tk[X] + st.tab_off[s];
@@ -842,7 +909,32 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     }
                     __syncthreads();
                     const int nl = static_cast<int>(st.list_n);
-                    for (int k0 = tid - lane; k0 < nl; k0 += kProbes * kThreads) {  // warp-uniform
+                    // a voxel whose every point lies in cells this block holds
+                    // whole is counted here; the other keys go to the global table
+                    const unsigned short* gl = list;
+                    int ng = nl;
+                    if (j == 0 && st.own_on && nl <= kSetSlots / 2) {
+                        unsigned short* rest = list + kSetSlots / 2;
+                        for (int k0 = tid - lane; k0 < nl; k0 += kThreads) {  // warp-uniform
+                            const int k = k0 + lane;
+                            bool glob = false;
+                            int c = 0;
+                            if (k < nl) {
+                                const int idx = list[k];
+                                c = idx >> setc_log2;
+                                glob = !voxel_owned(set[idx], st.cgrid[li][c], st.mn[0], st.mx[0], st.own_lo,
+                                                    st.own_hi);
+                            }
+                            const int pos = warp_append(glob, &st.rest_n);
+                            if (pos >= 0) rest[pos] = list[k];
+                            if (ncand == 1) warp_append(k < nl && !glob, &st.xcnt[0]);
+                            else warp_append_keyed(k < nl && !glob, c, st.xcnt);
+                        }
+                        __syncthreads();
+                        gl = rest;
+                        ng = static_cast<int>(st.rest_n);
+                    }
+                    for (int k0 = tid - lane; k0 < ng; k0 += kProbes * kThreads) {  // warp-uniform
                         unsigned long long key[kProbes];
                         unsigned long long* Tp[kProbes];
                         int cc[kProbes];
@@ -851,9 +943,9 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
 #pragma unroll
                         for (int u = 0; u < kProbes; ++u) {
                             const int k = k0 + lane + u * kThreads;
-                            const int idx = (k < nl) ? static_cast<int>(list[k]) : 0;
+                            const int idx = (k < ng) ? static_cast<int>(gl[k]) : 0;
                             cc[u] = idx >> setc_log2;
-                            key[u] = (k < nl) ? set[idx] : kEmptyKey;
+                            key[u] = (k < ng) ? set[idx] : kEmptyKey;
                             Tp[u] = Tb + cc[u] * tstride;
                         }
                         find_or_insert_batch<kProbes>(Tp, cap, key, slot, fr);
@@ -872,12 +964,12 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     __syncthreads();
                     if (fused) {
                         if (tid == 0) {
-                            st.pass_cnt += static_cast<unsigned long long>(st.dcnt[X][li][0]);
+                            st.pass_cnt += static_cast<unsigned long long>(st.dcnt[X][li][0]) + st.xcnt[0];
                             if (st.rbits) st.pass_err = 1;
                         }
                     } else {
-                        if (tid < ncand && st.dcnt[X][li][tid])
-                            atomicAdd(&ls[s].count[p % 3][tid], static_cast<unsigned>(st.dcnt[X][li][tid]));
+                        if (tid < ncand && (st.dcnt[X][li][tid] || st.xcnt[tid]))
+                            atomicAdd(&ls[s].count[p % 3][tid], static_cast<unsigned>(st.dcnt[X][li][tid]) + st.xcnt[tid]);
                         if (tid == 0 && st.rbits) atomicOr(&ls[s].cerr[p % 3], st.rbits);
                     }
                 }

@@ -80,6 +80,7 @@ __device__ __forceinline__ unsigned long long random_draw(unsigned seed, unsigne
 struct Grid {
     float v[3];
     float fmin[3];
+    float r[3];  // RN(1 / v) where it is a normal number, else 0 (floor_div_r)
 };
 
 __device__ __forceinline__ bool floor_div(float x, float v, float* f) {
@@ -90,11 +91,36 @@ __device__ __forceinline__ bool floor_div(float x, float v, float* f) {
     return true;
 }
 
+// floor(RN(x / v)), the Eq. 2 cell, through the reciprocal r = RN(1 / v) (a
+// normal number): q = RN(x * r) equals x / v up to a relative 2^-23 (two
+// roundings), and RN(x / v) is within a relative 2^-24 of x / v, so
+// |RN(x / v) - q| < (|q| + 1) 2^-22.  If q lies farther than
+// b = (|q| + 1) 2^-21 from both integers around it (b < d = q - floor(q) <
+// RN(1 - b)), RN(x / v) lies strictly between them and both floors agree.
+// Near an integer (or with |q| >= 2^21, where b exceeds 1, a quotient below
+// the normal range, which leaves d within b of 0 or 1, r = 0, or x not
+// finite) the quotient is taken correctly rounded and floored.  Either way
+// the result is the floor of the correctly rounded quotient.
+__device__ __forceinline__ bool floor_div_r(float x, const Grid& g, int a, float* f) {
+    const float q = __fmul_rn(x, g.r[a]);
+    const float n = floorf(q);
+    const float d = __fsub_rn(q, n);
+    const float b = __fmul_rn(__fadd_rn(fabsf(q), 1.0f), 4.76837158203125e-07f);  // (|q| + 1) 2^-21
+    if (d > b && d < __fsub_rn(1.0f, b)) {
+        *f = n;
+        return true;
+    }
+    return floor_div(x, g.v[a], f);
+}
+
+// The grid of voxel size v = s * aspect; mn is the bounding box's minimum.
 __device__ inline bool make_grid(float s, const float r[3], const float mn[3], Grid* g) {
     for (int a = 0; a < 3; ++a) {
         const float v = __fmul_rn(s, r[a]);
         if (!(v > 0.0f) || !isfinite(v)) return false;
         g->v[a] = v;
+        const float rv = __fdiv_rn(1.0f, v);
+        g->r[a] = (rv >= 1.17549435e-38f && rv <= 3.40282347e+38f) ? rv : 0.0f;
         if (!floor_div(mn[a], v, &g->fmin[a])) return false;
     }
     return true;
@@ -106,7 +132,7 @@ __device__ __forceinline__ bool cell_key(const float p[3], const Grid& g, unsign
     unsigned long long k = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (!floor_div(p[a], g.v[a], &f[a])) return false;
+        if (!floor_div_r(p[a], g, a, &f[a])) return false;
         const float u = __fsub_rn(f[a], g.fmin[a]);
         if (!(u >= 0.0f && u < 2097152.0f)) return false;
         k |= static_cast<unsigned long long>(static_cast<unsigned>(u)) << (21 * a);

@@ -115,6 +115,7 @@ struct Smem {
     // points all lie in this block's work item (own_on), and per pass the keys
     // that go to the global table (rest_n) and the owned ones counted here
     int own_on, own_lo, own_hi;
+    float own_k[3];
     unsigned rest_n;
     unsigned xcnt[kMaxCand];
     int ntimes;
@@ -287,14 +288,20 @@ __device__ __forceinline__ unsigned bucket_of(const float p[3], const float mn[3
 // Whether every point of the voxel `key` (Eq. 2 cell of grid g) lies in Morton
 // cells [own_lo, own_hi] of the bucketing, all of whose points this block
 // processes: then no other block has a point in the voxel, and the block
-// counts it without the global table.  A point x of the voxel along an axis
-// has f <= RN(x / v) < f + 1, so v (f - ulp(f) / 2) <= x < v (f + 1); the box
-// [v f, v (f + 1)] is widened by 2^-20 (|end| + v) on both sides, which covers
-// that half ulp and the rounding of the products.  Morton order is monotone in
-// each cell coordinate, so the box's cells lie between the codes of its two
-// corner cells.
+// counts it without the global table.  The test may answer no for an owned
+// voxel (the key then goes to the global table), never yes for another one.
+// A point x of the voxel along an axis has f <= RN(x / v) < f + 1, so
+// v (f - ulp(f) / 2) <= x < v (f + 1); the box [v f, v (f + 1)] is widened by
+// 2^-20 (|end| + v) on both sides, which covers that half ulp and the
+// rounding of the products.  Along each axis the box's ends are mapped to
+// cell coordinates by t = (end - mn) * (16 / e): within the box [0, 16] of the
+// points this differs from bucket_axis's rounded (x - mn) / e * 16 by less
+// than 1e-5, so widening the ends by 0.01 cells yields every cell a point of
+// the voxel can fall in (outside [0, 16] the clamp to the end cells decides).
+// Morton order is monotone in each cell coordinate, so those cells lie
+// between the codes of the two corner cells.  k[a] = RN(16 / e_a), 0 if e_a = 0.
 __device__ __forceinline__ bool voxel_owned(unsigned long long key, const Grid& g, const float mn[3],
-                                            const float mx[3], int own_lo, int own_hi) {
+                                            const float k[3], int own_lo, int own_hi) {
     unsigned c0[3], c1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -304,8 +311,12 @@ __device__ __forceinline__ bool voxel_owned(unsigned long long key, const Grid& 
         float hi = __fmul_rn(v, __fadd_rn(f, 1.0f));
         lo = __fsub_rn(lo, __fmul_rn(__fadd_rn(fabsf(lo), v), 9.5367431640625e-07f));
         hi = __fadd_rn(hi, __fmul_rn(__fadd_rn(fabsf(hi), v), 9.5367431640625e-07f));
-        c0[a] = bucket_axis(lo, mn[a], mx[a]);
-        c1[a] = bucket_axis(hi, mn[a], mx[a]);
+        float tl = __fsub_rn(__fmul_rn(__fsub_rn(lo, mn[a]), k[a]), 0.01f);
+        float th = __fadd_rn(__fmul_rn(__fsub_rn(hi, mn[a]), k[a]), 0.01f);
+        tl = fminf(fmaxf(tl, 0.0f), 15.0f);  // NaN-free: finite inputs
+        th = fminf(fmaxf(th, 0.0f), 15.0f);
+        c0[a] = static_cast<unsigned>(tl);
+        c1[a] = static_cast<unsigned>(th);
     }
     return static_cast<int>(morton16(c0[0], c0[1], c0[2])) >= own_lo &&
            static_cast<int>(morton16(c1[0], c1[1], c1[2])) <= own_hi;
@@ -662,6 +673,10 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     st.own_lo = c_lo;
                     st.own_hi = lo - 1;
                     st.own_on = (c_lo <= lo - 1) ? 1 : 0;
+                    for (int a3 = 0; a3 < 3; ++a3) {
+                        const float e = __fsub_rn(st.mx[0][a3], st.mn[0][a3]);
+                        st.own_k[a3] = (e > 0.0f) ? __fdiv_rn(16.0f, e) : 0.0f;
+                    }
                 }
                 for (int b = tid; b < 4096; b += kThreads)
                     if (h[b]) h[b] = hb[b] + atomicAdd(&d.bkt[4096 + b], h[b]);
@@ -915,6 +930,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     int ng = nl;
                     if (j == 0 && st.own_on && nl <= kSetSlots / 2) {
                         unsigned short* rest = list + kSetSlots / 2;
+                        unsigned mine = 0;  // owned keys of this thread (one candidate)
                         for (int k0 = tid - lane; k0 < nl; k0 += kThreads) {  // warp-uniform
                             const int k = k0 + lane;
                             bool glob = false;
@@ -922,13 +938,17 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             if (k < nl) {
                                 const int idx = list[k];
                                 c = idx >> setc_log2;
-                                glob = !voxel_owned(set[idx], st.cgrid[li][c], st.mn[0], st.mx[0], st.own_lo,
+                                glob = !voxel_owned(set[idx], st.cgrid[li][c], st.mn[0], st.own_k, st.own_lo,
                                                     st.own_hi);
                             }
                             const int pos = warp_append(glob, &st.rest_n);
                             if (pos >= 0) rest[pos] = list[k];
-                            if (ncand == 1) warp_append(k < nl && !glob, &st.xcnt[0]);
+                            if (ncand == 1) mine += (k < nl && !glob) ? 1u : 0u;
                             else warp_append_keyed(k < nl && !glob, c, st.xcnt);
+                        }
+                        if (ncand == 1) {
+                            const unsigned w = __reduce_add_sync(0xffffffffu, mine);
+                            if (lane == 0 && w) atomicAdd(&st.xcnt[0], w);
                         }
                         __syncthreads();
                         gl = rest;

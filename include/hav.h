@@ -201,7 +201,7 @@ typedef struct {
                                 the device launches 8-CTA clusters) run on
                                 thread-block clusters, one cluster of 8 SMs per
                                 segment, the voxel table in distributed shared
-                                memory (same results; plain bisection, settled
+                                memory (same results; one size per pass, settled
                                 steps as in the grid kernel; same conditions as
                                 solo_points) */
     int32_t solo_points;     /* levels whose every segment has at most this many
@@ -209,9 +209,8 @@ typedef struct {
                                 single CTAs, one per segment, its points and
                                 voxel table in the CTA's shared memory and each
                                 phase ended by a block barrier (same results;
-                                plain bisection; used when search is BISECT,
-                                select CENTRE_CLOSEST or RANDOM and no flag is
-                                set).  Levels run on the grid-wide kernel until
+                                used when select is CENTRE_CLOSEST or RANDOM
+                                and no flag is set, either search start).  Levels run on the grid-wide kernel until
                                 the first level within small_points, then on
                                 clusters until the first level within
                                 solo_points that has more segments than the

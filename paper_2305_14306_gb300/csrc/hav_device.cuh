@@ -333,6 +333,37 @@ __device__ __forceinline__ int smem_insert_n(unsigned long long* set, int log2, 
     return -1;
 }
 
+// ------------------------------------------------ Section 3.3 search steps
+// The next size of a search with bracket (lo, hi): a pending first guess,
+// 2 lo while doubling up (the guided start), else the bisection midpoint in
+// binary32.
+__device__ __forceinline__ float next_size(float lo, float hi, bool up, float first) {
+    if (first > 0.0f) return first;
+    const float d = __fmul_rn(lo, 2.0f);
+    if (up && d < hi) return d;
+    return __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+}
+
+// Size at node c of the search subtree below the current state (heap order:
+// child 2c + 1 follows a count below m_l, 2c + 2 a count above k_max): the
+// path from the root follows the bits of c + 1 below its leading one (0: too
+// few voxels, hi = s; 1: too many, lo = s), each step as next_size takes it.
+__device__ __forceinline__ float cand_size(float lo, float hi, bool up, float first, int c) {
+    const int x = c + 1;
+    const int depth = 31 - __clz(x);
+    float s = next_size(lo, hi, up, first);
+    for (int b = depth - 1; b >= 0; --b) {
+        if ((x >> b) & 1) {
+            lo = s;
+        } else {
+            hi = s;
+            up = false;
+        }
+        s = next_size(lo, hi, up, 0.0f);
+    }
+    return s;
+}
+
 // Eq. 3 budget of layer l (0-based).
 __device__ __forceinline__ long long layer_budget(long long m, int layers, int ratio, int l) {
     long long S = 0, pw = 1;

@@ -66,7 +66,10 @@ struct SegHdr {
     int32_t status;         // first error of this segment
     int32_t nonfinite;      // set only in the bounding-box phase
     uint32_t bbox[2][6];    // per level parity: ~enc(min xyz) then enc(max xyz), atomicMax'ed
-    uint32_t pad[2];
+    // the segment's last search of the call so far (guided start): its s*
+    // and budget m_l (0: none); handed from the grid kernel to the small-level one
+    float guide_s;
+    int32_t guide_m;
 };
 
 // Per segment, per layer parity: zeroed inside the kernel before use.

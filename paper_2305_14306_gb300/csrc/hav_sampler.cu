@@ -322,37 +322,6 @@ __device__ __forceinline__ bool voxel_owned(unsigned long long key, const Grid& 
            static_cast<int>(morton16(c1[0], c1[1], c1[2])) <= own_hi;
 }
 
-// Size evaluated by node c (heap order) of the bisection subtree below
-// (lo, hi): the path from the root follows the bits of c + 1 below its
-// leading one (0: too few voxels, hi = s; 1: too many, lo = s), with the
-// same binary32 midpoint as the sequential search.
-// The next size of a search with bracket (lo, hi): a pending first guess,
-// 2 lo while doubling up (guided start, F_UP), else the bisection midpoint.
-__device__ __forceinline__ float next_size(float lo, float hi, bool up, float first) {
-    if (first > 0.0f) return first;
-    const float d = __fmul_rn(lo, 2.0f);
-    if (up && d < hi) return d;
-    return __fmul_rn(__fadd_rn(lo, hi), 0.5f);
-}
-
-// Size at node c of the search subtree below the current state (heap order:
-// child 2c + 1 follows a count below m_l, 2c + 2 a count above k_max).
-__device__ __forceinline__ float cand_size(float lo, float hi, bool up, float first, int c) {
-    const int x = c + 1;
-    const int depth = 31 - __clz(x);
-    float s = next_size(lo, hi, up, first);
-    for (int b = depth - 1; b >= 0; --b) {
-        if ((x >> b) & 1) {
-            lo = s;
-        } else {
-            hi = s;
-            up = false;
-        }
-        s = next_size(lo, hi, up, 0.0f);
-    }
-    return s;
-}
-
 // Level layout of every segment, computed identically by every block.
 __device__ void level_setup(const Plan& P, int j, Smem& st) {
     const int S = P.S;
@@ -1121,6 +1090,10 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 !(P.fixed_s > 0.0f) && st.err[tid] == 0) {
                 st.gs[tid] = st.s_star[tid];
                 st.gm[tid] = st.ml[tid];
+                if (blockIdx.x == 0) {  // for a small-level launch that continues the chain
+                    d.sh[tid].guide_s = st.gs[tid];
+                    d.sh[tid].guide_m = st.gm[tid];
+                }
             }
 
             // ------------------------------------- Section 3.2 selection at s*

@@ -12,8 +12,10 @@
 // of an L2 round trip across the chip, and a phase ends with a hardware
 // cluster barrier instead of a grid barrier: on levels of tens of thousands
 // of points the grid-wide kernel pays for that latency, not for work.  The
-// search is the plain bisection (one size per pass), so every evaluated size
-// and count is the paper's.
+// search takes one size per pass (several sizes per pass were measured
+// slower here: a pass is bound by its remote inserts, not by the cluster
+// barrier), from either search start, so every evaluated size and count is
+// the paper's.
 //
 // Inside a cluster, CTA r holds the level's points [n r / Q, n (r + 1) / Q)
 // (level indices, ascending) in shared memory with their taken flags.  The
@@ -194,6 +196,10 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
     for (int seg = cluster_id; seg < S; seg += nclusters) {
         // an error from earlier levels (another kernel) carries on: first m points
         int err = ld_volatile(&sh[seg].status);
+        // the segment's last search of the call so far (guided start), from the
+        // kernel that ran the earlier levels
+        float gs = (first_level > 0) ? sh[seg].guide_s : 0.0f;
+        int gm = (first_level > 0) ? sh[seg].guide_m : 0;
         for (int j = first_level; j < P.L; ++j) {
             const long long n = (j == 0) ? (P.off0[seg + 1] - P.off0[seg]) : P.m[j - 1][seg];
             const long long m = P.m[j][seg];
@@ -308,6 +314,20 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                 float s_star = fixed ? P.fixed_s : sm.s_hi;
                 bool accepted = false;
                 const int steps = fixed ? 0 : P.t_max;
+                const bool guided = (P.search == HAV_SEARCH_GUIDED);
+                // guided start: the first size from the segment's previous search in
+                // this call (or from s_hi), doubling up from it while the counts stay
+                // too high; the same reading as the grid kernel's
+                bool up = false;
+                float first = 0.0f;
+                if (guided && steps > 0) {
+                    const float g = (gm > 0) ? __fmul_rn(gs, __fsqrt_rn(__fdiv_rn(__int2float_rn(gm), __ll2float_rn(ml))))
+                                             : __fdiv_rn(sm.s_hi, __fsqrt_rn(__ll2float_rn(ml)));
+                    if (g > 0.0f && g < sm.s_hi) {
+                        first = g;
+                        up = true;
+                    }
+                }
 
                 // The leading steps settled by an exact bound below m_l are taken
                 // without a pass, as in the grid kernel: the grid cells the
@@ -315,7 +335,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                 // s_hi / 2^(t+1) on a superset of the points; the trace keeps the
                 // smaller bound
                 int t0 = 0;
-                while (t0 < steps) {
+                while (!guided && t0 < steps) {
                     const float sv = __fmul_rn(__fadd_rn(0.0f, hi), 0.5f);
                     long long bd = cell_bound(sv, P.aspect, sm.mn, sm.mx);
                     if (sm.pre[t0] >= 0 && sm.pre[t0] < bd) bd = sm.pre[t0];
@@ -329,11 +349,12 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                     hi = sv;
                     ++t0;
                 }
-                bool pre = true;  // every step so far had too few voxels
+                bool pre = !guided;  // every step so far had too few voxels (plain bisection)
 
-                // Section 3.3 bisection, one size per pass
+                // Section 3.3 search, one size per pass
                 for (int t = t0; t < steps; ++t) {
-                    const float sv = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+                    const float sv = next_size(lo, hi, up, first);
+                    first = 0.0f;
                     Grid G;
                     const bool gok = make_grid(sv, P.aspect, sm.mn, &G);
                     for (int k = tid; k < part; k += kST) keys[k] = kEmptyKey;
@@ -393,6 +414,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                         lo = sv;
                     } else if (K < ml) {
                         hi = sv;
+                        up = false;
                     } else {
                         s_star = sv;
                         accepted = true;
@@ -401,6 +423,10 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                 }
                 if (err) continue;
                 if (!accepted && !fixed && P.t_max > 0) s_star = (lo > 0.0f) ? lo : hi;
+                if (guided && P.t_max > 0 && !fixed) {  // the next search's guided start follows this one
+                    gs = s_star;
+                    gm = static_cast<int>(ml);
+                }
                 Grid G;
                 if (!make_grid(s_star, P.aspect, sm.mn, &G)) {
                     err = HAV_ERR_RANGE;
@@ -588,6 +614,10 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                 }
                 csync<Q>(cl);  // the next level reads orig_out; part_cnt is reused
             }
+        }
+        if (write_tr) {  // for a single-CTA launch that continues the chain
+            sh[seg].guide_s = gs;
+            sh[seg].guide_m = gm;
         }
     }
 }

@@ -355,13 +355,16 @@ def test_coverage_fps_vs_hav(hv, ctx):
     assert c_fps <= c_hav < c_rnd
 
 
-def test_small_level_engines_match_the_grid_kernel(hv):
+@pytest.mark.parametrize("spec", [[0, 4096, 65536], [0, 0, 0], [1 << 31, 1 << 31, 1 << 31]])
+def test_small_level_engines_match_the_grid_kernel(hv, spec):
     # levels within 32,768 points per segment run on clusters of 16 or 8 CTAs
     # and levels within 4,096 on one CTA each by default; every combination,
     # the grid kernel alone included, gives the same indices and traces (the
-    # grid kernel and the small engines settle the same steps by the same bounds)
+    # grid kernel and the small engines settle the same steps by the same
+    # bounds), whatever the grid kernel's speculation depth
     c = hv.Context(1 << 18, 16)
     try:
+        c.set_tuning(spec_points=spec)
         t = c.get_tuning()
         assert t["solo_points"] == 4096 and t["small_points"] in (0, 32768) and t["cluster_ctas"] == 0
         pts = scenes.lidar_min(16384, 7)[0]

@@ -136,12 +136,19 @@ def test_noalloc_guided(hv):
     assert np.array_equal(out, ora[0])
 
 
-def test_cluster_tuning_keeps_the_guided_search_exact(hv):
-    # the cluster engine runs the plain bisection only; a guided call on a
-    # context that enables it stays on the grid kernel and stays exact
+@pytest.mark.parametrize("small,solo,q", [(0, 0, 0), (0, 4096, 0), (32768, 0, 8), (32768, 0, 16),
+                                          (32768, 4096, 0), (32768, 4096, 16)])
+def test_small_level_engines_run_the_guided_search(hv, small, solo, q):
+    # the cluster and single-CTA engines take the guided start too, with the
+    # previous search handed on from the kernel that ran the earlier levels;
+    # every engine combination lands on the oracle's sizes and indices
     c = hv.Context(1 << 18, 16)
     try:
-        c.set_tuning(small_points=32768)
+        if small and c.get_tuning()["small_points"] == 0:
+            pytest.skip("no cluster launch on this device")
+        c.set_tuning(small_points=small, solo_points=solo, cluster_ctas=q)
         check_levels(hv, c, scenes.lidar_min(16384, 6)[0], [16384, 4096, 1024, 512])
+        check_levels(hv, c, scenes.room_scene(60000, 9), [30000, 7500, 1875, 400])
+        check_levels(hv, c, scenes.uniform_box(16384, 4), [4096], {**GUIDED, "layers": 3})
     finally:
         c.close()

@@ -222,14 +222,27 @@ typedef struct {
                                 context's blocks, else 8; or 8, or 16 (a
                                 cluster size above the portable 8; only where
                                 the device schedules it) */
+    int32_t table_log2;      /* load factor of the grid-wide kernel's voxel
+                                tables: a segment's table has nextpow2(2^f n)
+                                slots for its n points, f = table_log2 in 1..3
+                                (default 1: at most half full).  A value above the
+                                context's current workspace makes this call
+                                allocate a larger one (it first waits for the
+                                device); no sampling call allocates */
+    int32_t pass_shape;      /* the grid-wide kernel's instantiation: points each
+                                thread loads ahead in a pass and global probes it
+                                keeps in flight, 0: (2, 1) (default), 1: (1, 1),
+                                2: (2, 2), 3: (4, 1) */
 } hav_tuning;
 
 /* Copy the context's tuning into *out (the defaults after creation:
- * {0, 4096, 65536}, 64, the co-resident maximum, 32768, 4096, 0). */
+ * {0, 4096, 65536}, 64, the co-resident maximum, 32768, 4096, 0, 1, 0). */
 hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out);
 
 /* Replace the context's tuning.  HAV_ERR_INVALID (and no change) on a value
- * outside the ranges above.  Takes effect from the next call. */
+ * outside the ranges above; HAV_ERR_NOMEM (and no change) when a larger
+ * table_log2 needs a workspace that cannot be allocated.  Takes effect from
+ * the next call. */
 hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t);
 
 /* Number of device kernels the context's calls have launched since it was

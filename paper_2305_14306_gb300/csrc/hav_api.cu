@@ -23,6 +23,8 @@ struct hav_ctx {
     int small_points;  // largest level run on clusters (0: never)
     int solo_ok;       // the single-CTA kernel can be launched
     int solo_points;   // largest level run on single CTAs (0: never)
+    int table_log2;    // grid-kernel tables of capacity nextpow2(2^table_log2 n)
+    int pass_shape;    // grid-kernel instantiation (points loaded ahead, probes in flight)
     int fps_nblocks;
     havk::Layout lay;
     unsigned char* ws;
@@ -122,6 +124,8 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
     c->max_blocks = nb;
     c->fps_nblocks = fnb;
     c->chunk_min = havk::kChunkMin;
+    c->table_log2 = 1;
+    c->pass_shape = 0;
     {
         const int snc = havk::small_clusters(dev, 8);
         cudaGetLastError();
@@ -168,6 +172,8 @@ hav_status hav_context_get_tuning(const hav_ctx* ctx, hav_tuning* out) {
     out->small_points = ctx->small_points;
     out->solo_points = ctx->solo_points;
     out->cluster_ctas = ctx->cluster_ctas;
+    out->table_log2 = ctx->table_log2;
+    out->pass_shape = ctx->pass_shape;
     return HAV_OK;
 }
 
@@ -184,6 +190,28 @@ hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t) {
     if (t->small_points > 0 && ctx->small_nc == 0) return HAV_ERR_INVALID;  // no cluster launch on this device
     if (t->cluster_ctas != 0 && t->cluster_ctas != 8 && t->cluster_ctas != 16) return HAV_ERR_INVALID;
     if (t->cluster_ctas == 16 && ctx->big_nc == 0) return HAV_ERR_INVALID;
+    if (t->table_log2 < 1 || t->table_log2 > havk::kMaxTableLog2) return HAV_ERR_INVALID;
+    if (t->pass_shape < 0 || t->pass_shape >= havk::kPassShapes) return HAV_ERR_INVALID;
+    if (t->table_log2 > ctx->lay.table_log2) {
+        // larger tables than the workspace holds: a new workspace (the only
+        // allocation outside hav_context_create); the old one once the device is idle
+        const havk::Layout lay = havk::make_layout(ctx->lay.max_points, ctx->lay.max_segments, true, t->table_log2);
+        unsigned char* ws = nullptr;
+        if (cudaDeviceSynchronize() != cudaSuccess) return HAV_ERR_CUDA;
+        if (cudaMalloc(&ws, lay.total) != cudaSuccess) {
+            cudaGetLastError();
+            return HAV_ERR_NOMEM;
+        }
+        if (cudaMemset(ws, 0, lay.total) != cudaSuccess) {
+            cudaFree(ws);
+            return HAV_ERR_CUDA;
+        }
+        cudaFree(ctx->ws);
+        ctx->ws = ws;
+        ctx->lay = lay;
+    }
+    ctx->table_log2 = t->table_log2;
+    ctx->pass_shape = t->pass_shape;
     ctx->small_points = t->small_points;
     ctx->solo_points = t->solo_points;
     ctx->cluster_ctas = t->cluster_ctas;
@@ -258,6 +286,8 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
         return HAV_ERR_INVALID;
     }
     plan->chunk_min = ctx->chunk_min;
+    plan->table_log2 = ctx->table_log2;
+    plan->pass_shape = ctx->pass_shape;
     for (int k = 0; k < 3; ++k) plan->spec_n[k] = ctx->spec_n[k];
     for (int a = 0; a < 3; ++a) plan->aspect[a] = params->aspect[a];
     plan->select = params->select;

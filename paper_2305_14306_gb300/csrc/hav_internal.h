@@ -40,6 +40,10 @@ constexpr int64_t kSpecN2 = 65536;
 constexpr int kChunkMin = 64;              // default smallest work item (points)
 constexpr int kSmallMax = 32768;           // largest level the cluster kernel takes (points)
 constexpr int kLocalItems = 8;             // work items one block can own in a level
+// Pass shapes of the grid kernel (template instantiations): points each thread
+// loads ahead in a bisection or selection pass, and first probes of the
+// global flush it keeps in flight.  Shape 0 is the default.
+constexpr int kPassShapes = 4;
 
 constexpr unsigned long long kEmptyKey = ~0ull;  // valid keys use 63 bits
 constexpr unsigned long long kEmptyVal = ~0ull;  // packed (d^2 bits, index) never reaches it
@@ -93,7 +97,7 @@ struct Cand {
 struct Layout {
     int64_t max_points;
     int32_t max_segments;
-    int32_t pad;
+    int32_t table_log2;    // key tables sized for capacities nextpow2(2^table_log2 n)
     int64_t tab_slots;     // slots of one key-table array (all segments, all candidates of a pass)
     int64_t cand_slots;
     int64_t taken_words;
@@ -110,16 +114,21 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr int kMaxItems = kMaxBlocks + kMaxSegments;  // work items of one level
 
-inline Layout make_layout(int64_t N, int32_t S, bool spec_room = true) {
+// Largest table load factor setting: capacity nextpow2(2^3 n), at most 1/8 full.
+constexpr int kMaxTableLog2 = 3;
+
+inline Layout make_layout(int64_t N, int32_t S, bool spec_room = true, int table_log2 = 1) {
     Layout L{};
     L.max_points = N;
     L.max_segments = S;
-    // Per-segment capacity C = max(nextpow2(2 n), 64) < max(4 n, 128); small
-    // levels (at most 32,768 points) also get room for kMaxCand tables per pass.
-    const int64_t plain = 4 * N + 128 * static_cast<int64_t>(S);
+    L.table_log2 = table_log2;
+    // Per-segment capacity C = max(nextpow2(2^f n), 64) < max(2^(f+1) n, 128)
+    // for f = table_log2; small levels (at most 32,768 points) also get room
+    // for kMaxCand tables per pass.
+    const int64_t plain = (2ll << table_log2) * N + 128 * static_cast<int64_t>(S);
     const int64_t spec = spec_room ? static_cast<int64_t>(kMaxCand) * (65536 + 128 * static_cast<int64_t>(S)) : 0;
     L.tab_slots = plain > spec ? plain : spec;
-    L.cand_slots = (4 * N + 128 * static_cast<int64_t>(S)) / 2;
+    L.cand_slots = plain / 2;
     const int64_t dspec = spec_room ? static_cast<int64_t>(kMaxCand) * 32768 : 0;
     L.dirty_slots = N > dspec ? N : dspec;
     L.taken_words = N / 32 + 2;
@@ -178,6 +187,8 @@ struct Plan {
     int32_t search;              // HAV_SEARCH_*
     int32_t test_timeout;        // HAV_FLAG_TEST_TIMEOUT: the first barrier waits for a missing block
     int32_t test_table_full;     // HAV_FLAG_TEST_TABLE_FULL: segment 0's tables keep 64 slots
+    int32_t table_log2;          // per-segment table capacity nextpow2(2^table_log2 n) (<= lay.table_log2)
+    int32_t pass_shape;          // points loaded ahead / probes in flight per thread: kPassShapes[pass_shape]
     int64_t off0[kMaxSegments + 1];       // level-0 segment offsets
     int32_t m[kMaxLevels][kMaxSegments];  // budgets per level and segment
 };

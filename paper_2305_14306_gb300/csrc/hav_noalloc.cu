@@ -127,6 +127,8 @@ extern "C" hav_status hav_sample_noalloc(const float* points, int64_t n, int64_t
         plan.sigma_den = params->sigma_den;
         plan.nblocks = nblocks;
         plan.chunk_min = havk::kChunkMin;
+        plan.table_log2 = 1;
+        plan.pass_shape = 0;
         for (int a = 0; a < 3; ++a) plan.aspect[a] = params->aspect[a];
         plan.select = params->select;
         plan.seed = params->seed;

@@ -54,13 +54,18 @@ constexpr int kSelSlots = 8192;    // block-local argmin table of the selection 
 constexpr size_t kSelSmem = static_cast<size_t>(kSelSlots) * 18;
 constexpr size_t kDynSmem = kPassSmem > kSelSmem ? kPassSmem : kSelSmem;
 constexpr int kBucketMin = 1 << 17;
-// Loads and probes in flight per thread: with 64 registers a thread (one
+// Loads and probes in flight per thread (the kernel's template arguments,
+// one instantiation per pass shape): with 64 registers a thread (one
 // 1024-thread block per SM), deeper batches spill more than they hide
-// (measured on GB300: 4 and 2 made the 1M-point chain 5 % slower).
-constexpr int kInFlight = 2;       // points loaded ahead per thread
-constexpr int kProbes = 1;         // global first probes issued together per thread
-static_assert(kSetSlots % (kProbes * kThreads) == 0 && kSelSlots % (kProbes * kThreads) == 0,
-              "flush loops take kProbes slots per thread per step");
+// (measured on GB300: 4 and 2 made the 1M-point chain 5 % slower than the
+// default 2 and 1).
+template <int IF, int PR>
+struct PassShape {
+    static constexpr int kInFlight = IF;  // points loaded ahead per thread
+    static constexpr int kProbes = PR;    // global first probes issued together per thread
+    static_assert(kSetSlots % (PR * kThreads) == 0 && kSelSlots % (PR * kThreads) == 0,
+                  "flush loops take kProbes slots per thread per step");
+};
 
 enum : int { F_ACTIVE = 1, F_SEARCH = 2, F_ACCEPT = 4, F_UP = 8, F_PRE = 16 };
 
@@ -332,8 +337,10 @@ __device__ void level_setup(const Plan& P, int j, Smem& st) {
         n = (j == 0) ? (P.off0[s + 1] - P.off0[s]) : P.m[j - 1][s];
         mm = P.m[j][s];
         // (test hook: segment 0's tables keep the smallest capacity)
+        // (the load factor: capacity nextpow2(2^f n), f = table_log2, at least 1)
+        const int tl = P.table_log2 > 0 ? P.table_log2 : 1;
         if (!(P.test_table_full && s == 0))
-            while ((1ll << lg) < 2 * n) ++lg;
+            while ((1ll << lg) < (n << tl)) ++lg;
         C = 1ll << lg;
         st.n[s] = static_cast<int>(n);
         st.m[s] = static_cast<int>(mm);
@@ -408,7 +415,10 @@ __device__ void level_setup(const Plan& P, int j, Smem& st) {
 
 }  // namespace
 
+template <int IF, int PR>
 __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_constant__ Plan P) {
+    constexpr int kInFlight = PassShape<IF, PR>::kInFlight;
+    constexpr int kProbes = PassShape<IF, PR>::kProbes;
     __shared__ Smem st;
     extern __shared__ __align__(16) unsigned char dyn[];
     const int S = P.S;
@@ -1645,20 +1655,31 @@ __global__ void fill_u64(unsigned long long* p, long long n, unsigned long long 
 
 }  // namespace
 
+namespace {
+// The instantiations, by pass shape: (points loaded ahead, probes in flight).
+using ChainFn = void (*)(const Plan);
+const ChainFn kChain[kPassShapes] = {hav_chain_kernel<2, 1>, hav_chain_kernel<1, 1>, hav_chain_kernel<2, 2>,
+                                     hav_chain_kernel<4, 1>};
+}  // namespace
+
 int max_coresident_blocks(int device) {
-    int sms = 0, per_sm = 0;
+    int sms = 0, per_sm = 0, least = 1 << 30;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(hav_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kDynSmem)) != cudaSuccess)
-        return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hav_chain_kernel, kThreads, kDynSmem) != cudaSuccess)
-        return -1;
-    long long nb = static_cast<long long>(sms) * per_sm;
+    for (int k = 0; k < kPassShapes; ++k) {  // every shape must fit the same grid
+        if (cudaFuncSetAttribute(kChain[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kDynSmem)) != cudaSuccess)
+            return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kChain[k], kThreads, kDynSmem) != cudaSuccess)
+            return -1;
+        if (per_sm < least) least = per_sm;
+    }
+    long long nb = static_cast<long long>(sms) * least;
     if (nb > kMaxBlocks) nb = kMaxBlocks;
     return static_cast<int>(nb);
 }
 
 int launch_chain(const Plan& plan, cudaStream_t stream) {
+    if (plan.pass_shape < 0 || plan.pass_shape >= kPassShapes) return -1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(plan.nblocks));
     cfg.blockDim = dim3(kThreads);
@@ -1669,7 +1690,7 @@ int launch_chain(const Plan& plan, cudaStream_t stream) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, hav_chain_kernel, plan) == cudaSuccess ? 1 : -1;
+    return cudaLaunchKernelEx(&cfg, kChain[plan.pass_shape], plan) == cudaSuccess ? 1 : -1;
 }
 
 int count_voxels(const float* points, int64_t n, float s, const float aspect[3], unsigned char* ws,

@@ -73,6 +73,8 @@ class hav_tuning(C.Structure):
         ("small_points", C.c_int32),
         ("solo_points", C.c_int32),
         ("cluster_ctas", C.c_int32),
+        ("table_log2", C.c_int32),
+        ("pass_shape", C.c_int32),
     ]
 
 
@@ -229,10 +231,11 @@ class Context:
         t = hav_tuning()
         _check(load().hav_context_get_tuning(self.handle, C.byref(t)), "hav_context_get_tuning")
         return {"spec_points": list(t.spec_points), "chunk_min": t.chunk_min, "nblocks": t.nblocks,
-                "small_points": t.small_points, "solo_points": t.solo_points, "cluster_ctas": t.cluster_ctas}
+                "small_points": t.small_points, "solo_points": t.solo_points, "cluster_ctas": t.cluster_ctas,
+                "table_log2": t.table_log2, "pass_shape": t.pass_shape}
 
     def set_tuning(self, spec_points=None, chunk_min=None, nblocks=None, small_points=None, solo_points=None,
-                   cluster_ctas=None):
+                   cluster_ctas=None, table_log2=None, pass_shape=None):
         """Change some of the knobs; the others keep their values."""
         cur = self.get_tuning()
         t = hav_tuning()
@@ -244,6 +247,8 @@ class Context:
         t.small_points = int(cur["small_points"] if small_points is None else small_points)
         t.solo_points = int(cur["solo_points"] if solo_points is None else solo_points)
         t.cluster_ctas = int(cur["cluster_ctas"] if cluster_ctas is None else cluster_ctas)
+        t.table_log2 = int(cur["table_log2"] if table_log2 is None else table_log2)
+        t.pass_shape = int(cur["pass_shape"] if pass_shape is None else pass_shape)
         _check(load().hav_context_set_tuning(self.handle, C.byref(t)), "hav_context_set_tuning")
 
     def launches(self) -> int:

@@ -265,6 +265,12 @@ TUNINGS = [
     {"spec_points": [65536, 262144, 524288], "chunk_min": 1024},
     {"spec_points": [32768, 131072, 262144], "chunk_min": 64, "nblocks": 5},
     {"spec_points": [0, 16384, 262144], "chunk_min": 128, "nblocks": 17},
+    # emptier tables (the workspace grows on the first of these) and the other
+    # pass shapes of the grid kernel
+    {"table_log2": 2},
+    {"table_log2": 3, "pass_shape": 2},
+    {"pass_shape": 1, "spec_points": [0, 0, 0]},
+    {"pass_shape": 3, "nblocks": 40},
 ]
 
 
@@ -292,12 +298,15 @@ def test_tuning_never_changes_results(hv):
             assert len(got_b[3]) == len(ref_b[3]) and len(got_c[2]) == len(ref_c[2])
             for x, y in zip(got_b[3] + got_c[2], ref_b[3] + ref_c[2]):
                 assert G.traces_equal(x, y) is None, (t, G.traces_equal(x, y))
-            c.set_tuning(spec_points=[0, 4096, 65536], chunk_min=64, nblocks=0)
-        assert c.get_tuning()["chunk_min"] == 64
+            c.set_tuning(spec_points=[0, 4096, 65536], chunk_min=64, nblocks=0, table_log2=1, pass_shape=0)
+        assert c.get_tuning()["chunk_min"] == 64 and c.get_tuning()["table_log2"] == 1
         with pytest.raises(hv.HavError):
             c.set_tuning(spec_points=[3, 2, 1])
         with pytest.raises(hv.HavError):
             c.set_tuning(chunk_min=0)
+        for bad in ({"table_log2": 0}, {"table_log2": 4}, {"pass_shape": 4}, {"pass_shape": -1}):
+            with pytest.raises(hv.HavError):
+                c.set_tuning(**bad)
     finally:
         c.close()
 

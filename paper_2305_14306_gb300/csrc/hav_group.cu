@@ -7,8 +7,8 @@
 //
 // A uniform grid with cells of at least the radius (so every ball lies in the
 // 3 x 3 x 3 cells around its centre's cell) is built by a counting sort of the
-// points by cell; one thread per centre then scans those cells and keeps the
-// nsample smallest qualifying indices in a sorted array.  The result does not
+// points by cell; one warp per centre then scans those cells and keeps the
+// nsample smallest qualifying indices in a sorted list.  The result does not
 // depend on the grid, only the work does.  Kernels, on the caller's stream:
 // bounding box, grid set-up, cell counts, a three-stage exclusive scan,
 // scatter, query.
@@ -167,28 +167,40 @@ __global__ void grp_scatter(const float* pts, long long n, const GroupGrid* g, u
     }
 }
 
-__global__ void grp_query(const float* pts, long long n, const int32_t* centres, long long m, float radius,
-                          int nsample, const GroupGrid* g, const uint32_t* end, const int32_t* list,
-                          int32_t* out_idx, float* out_xyz, int32_t* status) {
+// One warp per centre: the lanes test 32 candidates of the 27 cells at a
+// time, and the warp keeps the nsample smallest qualifying indices so far in
+// an ascending list in shared memory (a candidate at or above the list's last
+// entry is skipped once the list is full).  The list's contents do not depend
+// on the order in which the candidates arrive.
+constexpr int kQueryWarps = 4;  // warps per block of the query
+
+__global__ void __launch_bounds__(32 * kQueryWarps)
+    grp_query(const float* pts, long long n, const int32_t* centres, long long m, float radius, int nsample,
+              const GroupGrid* g, const uint32_t* end, const int32_t* list, int32_t* out_idx, float* out_xyz,
+              int32_t* status) {
+    __shared__ int32_t sbest[kQueryWarps][kGrpMaxSample];
     const GroupGrid G = *g;
     const float r2 = __fmul_rn(radius, radius);
-    int32_t best[kGrpMaxSample];
-    for (long long j = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; j < m;
-         j += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int32_t* best = sbest[wib];
+    const long long warps = static_cast<long long>(gridDim.x) * kQueryWarps;
+    for (long long j = blockIdx.x * static_cast<long long>(kQueryWarps) + wib; j < m; j += warps) {
         const int32_t ci = centres[j];
         int32_t* row = out_idx + j * nsample;
         if (ci < 0 || ci >= n) {
-            atomicCAS(status, 0, static_cast<int>(HAV_ERR_INVALID));
-            for (int s = 0; s < nsample; ++s) row[s] = 0;
+            if (lane == 0) atomicCAS(status, 0, static_cast<int>(HAV_ERR_INVALID));
+            for (int s = lane; s < nsample; s += 32) row[s] = 0;
             if (out_xyz)
-                for (int s = 0; s < 3 * nsample; ++s) out_xyz[j * 3 * nsample + s] = 0.0f;
+                for (int s = lane; s < 3 * nsample; s += 32) out_xyz[j * 3 * nsample + s] = 0.0f;
             continue;
         }
         const float cx = pts[3ll * ci], cy = pts[3ll * ci + 1], cz = pts[3ll * ci + 2];
         int c[3];
         const float cp[3] = {cx, cy, cz};
         cell_of(cp, G, c);
-        int cnt = 0;
+        int cnt = 0;           // entries in best (warp-uniform)
+        int32_t top = 0x7fffffff;  // best[nsample - 1] once the list is full
         for (int dz = -1; dz <= 1; ++dz) {
             const int z = c[2] + dz;
             if (z < 0 || z >= G.dims[2]) continue;
@@ -200,28 +212,61 @@ __global__ void grp_query(const float* pts, long long n, const int32_t* centres,
                     if (x < 0 || x >= G.dims[0]) continue;
                     const long long cell = (static_cast<long long>(z) * G.dims[1] + y) * G.dims[0] + x;
                     const uint32_t a = (cell > 0) ? end[cell - 1] : 0u;
-                    const uint32_t b = end[cell];
-                    for (uint32_t q = a; q < b && q < static_cast<uint32_t>(n); ++q) {
-                        const int32_t k = list[q];
-                        if (cnt == nsample && k >= best[nsample - 1]) continue;
-                        const float ex = __fsub_rn(pts[3ll * k], cx), ey = __fsub_rn(pts[3ll * k + 1], cy),
-                                    ez = __fsub_rn(pts[3ll * k + 2], cz);
-                        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-                        if (!(d2 < r2)) continue;
-                        // insert k into the sorted best[0..cnt), keeping at most nsample
-                        int at = (cnt < nsample) ? cnt : nsample - 1;
-                        while (at > 0 && best[at - 1] > k) {
-                            best[at] = best[at - 1];
-                            --at;
+                    uint32_t b = end[cell];
+                    if (b > static_cast<uint32_t>(n)) b = static_cast<uint32_t>(n);
+                    for (uint32_t q0 = a; q0 < b; q0 += 32) {  // warp-uniform
+                        const uint32_t q = q0 + lane;
+                        int32_t k = 0;
+                        bool ok = false;
+                        if (q < b) {
+                            k = list[q];
+                            if (k < top) {
+                                const float ex = __fsub_rn(pts[3ll * k], cx), ey = __fsub_rn(pts[3ll * k + 1], cy),
+                                            ez = __fsub_rn(pts[3ll * k + 2], cz);
+                                const float d2 =
+                                    __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+                                ok = d2 < r2;
+                            }
                         }
-                        best[at] = k;
-                        if (cnt < nsample) ++cnt;
+                        unsigned mask = __ballot_sync(0xffffffffu, ok);
+                        while (mask) {  // insert the qualifying candidates one by one
+                            const int src = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const int32_t kk = __shfl_sync(0xffffffffu, k, src);
+                            if (kk >= top) continue;  // (top only falls)
+                            // its position: the entries below it
+                            int below = 0;
+                            for (int e = lane; e < cnt; e += 32) below += (best[e] < kk) ? 1 : 0;
+                            const int pos = __reduce_add_sync(0xffffffffu, below);
+                            // entries [pos, last) move up one place; the last one drops out when full
+                            const int last = (cnt < nsample) ? cnt : nsample - 1;
+                            int32_t v[kGrpMaxSample / 32];
+#pragma unroll
+                            for (int r = 0; r < kGrpMaxSample / 32; ++r) {
+                                const int e = pos + lane + 32 * r;
+                                v[r] = (e < last) ? best[e] : 0;
+                            }
+                            __syncwarp();
+#pragma unroll
+                            for (int r = 0; r < kGrpMaxSample / 32; ++r) {
+                                const int e = pos + lane + 32 * r;
+                                if (e < last) best[e + 1] = v[r];
+                            }
+                            if (lane == 0) best[pos] = kk;
+                            __syncwarp();
+                            if (cnt < nsample) ++cnt;
+                            if (cnt == nsample) top = best[nsample - 1];
+                        }
                     }
                 }
             }
         }
-        if (cnt == 0) best[cnt++] = ci;  // unreachable: the centre is at distance 0
-        for (int s = 0; s < nsample; ++s) {
+        if (cnt == 0) {  // unreachable: the centre is at distance 0
+            if (lane == 0) best[0] = ci;
+            __syncwarp();
+            cnt = 1;
+        }
+        for (int s = lane; s < nsample; s += 32) {
             const int32_t k = (s < cnt) ? best[s] : best[0];
             row[s] = k;
             if (out_xyz) {
@@ -231,6 +276,7 @@ __global__ void grp_query(const float* pts, long long n, const int32_t* centres,
                 o[2] = __fsub_rn(pts[3ll * k + 2], cz);
             }
         }
+        __syncwarp();  // the list is rewritten for the next centre
     }
 }
 
@@ -267,8 +313,10 @@ int launch_ball_query(const float* points, long long n, const int32_t* centres, 
     grp_scan_sums<<<1, 1024, 0, stream>>>(block_sums, g);
     grp_scan_add<<<blocks(budget), t, 0, stream>>>(counts, g, block_sums);
     grp_scatter<<<blocks(n), t, 0, stream>>>(points, n, g, counts, list);
-    grp_query<<<blocks(m), 128, 0, stream>>>(points, n, centres, m, radius, nsample, g, counts, list, out_idx,
-                                             out_xyz, status);
+    long long qb = (m + kQueryWarps - 1) / kQueryWarps;
+    if (qb > 65536) qb = 65536;
+    grp_query<<<static_cast<unsigned>(qb < 1 ? 1 : qb), 32 * kQueryWarps, 0, stream>>>(
+        points, n, centres, m, radius, nsample, g, counts, list, out_idx, out_xyz, status);
     return cudaGetLastError() == cudaSuccess ? 8 : -1;
 }
 

@@ -248,8 +248,8 @@ hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t);
 /* Number of device kernels the context's calls have launched since it was
  * created (memsets and copies excluded), in *out (HOST).  A level chain
  * launches one to three kernels (hav_tuning), hav_sample_xyz one more, the
- * spacing, ball-query and farthest-point calls one each.  HAV_ERR_INVALID on
- * a NULL argument. */
+ * spacing and farthest-point calls one each, the ball query two.
+ * HAV_ERR_INVALID on a NULL argument. */
 hav_status hav_context_launches(const hav_ctx* ctx, uint64_t* out);
 
 /* Release the context and its device memory.  Waits for the device.  NULL is ignored. */
@@ -370,8 +370,12 @@ hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32
  * m int32 (e.g. the indices hav_sample returned); out_idx: device,
  * m*nsample int32; out_xyz: device, m*nsample*3 floats or NULL.
  * radius finite and > 0; 1 <= nsample <= 256.  A centre outside [0, n) gets
- * zeros and HAV_ERR_INVALID in hav_status_get.  Uses the context's workspace
- * (the phase-timer records of an earlier call are overwritten). */
+ * zeros and HAV_ERR_INVALID in hav_status_get.  Two launches on `stream`:
+ * a cooperative one that builds a uniform grid of cells at least the radius
+ * wide over the points (grid barriers with bounded waits; a wait that gives
+ * up is read as HAV_ERR_TIMEOUT), and the query, one warp per centre.  Uses
+ * the context's workspace (the phase-timer records of an earlier call are
+ * overwritten). */
 hav_status hav_ball_query(hav_ctx* ctx, const float* points, int64_t n, const int32_t* centres, int64_t m,
                           float radius, int32_t nsample, int32_t* out_idx, float* out_xyz, hav_stream stream);
 

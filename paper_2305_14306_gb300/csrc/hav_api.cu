@@ -26,6 +26,7 @@ struct hav_ctx {
     int table_log2;    // grid-kernel tables of capacity nextpow2(2^table_log2 n)
     int pass_shape;    // grid-kernel instantiation (points loaded ahead, probes in flight)
     int fps_nblocks;
+    int group_nblocks;  // co-resident blocks of the ball query's cooperative grid build
     havk::Layout lay;
     unsigned char* ws;
     int32_t last_S;
@@ -123,6 +124,11 @@ hav_status hav_context_create(hav_ctx** out, int64_t max_points, int32_t max_seg
     c->nblocks = nb;
     c->max_blocks = nb;
     c->fps_nblocks = fnb;
+    c->group_nblocks = havk::group_coresident_blocks(dev);
+    if (c->group_nblocks < 1) {
+        delete c;
+        return HAV_ERR_CUDA;
+    }
     c->chunk_min = havk::kChunkMin;
     c->table_log2 = 1;
     c->pass_shape = 0;
@@ -434,7 +440,7 @@ hav_status hav_ball_query(hav_ctx* ctx, const float* points, int64_t n, const in
     if (m == 0) return HAV_OK;
     havk::GlobalHdr* gh = reinterpret_cast<havk::GlobalHdr*>(ctx->ws + ctx->lay.ghdr);
     if (!counted(ctx, havk::launch_ball_query(points, n, centres, m, radius, nsample, out_idx, out_xyz, ctx->ws,
-                                              ctx->lay, &gh->status, strm)))
+                                              ctx->lay, &gh->status, ctx->group_nblocks, strm)))
         return HAV_ERR_CUDA;
     return HAV_OK;
 }

@@ -9,9 +9,8 @@
 // 3 x 3 x 3 cells around its centre's cell) is built by a counting sort of the
 // points by cell; one warp per centre then scans those cells and keeps the
 // nsample smallest qualifying indices in a sorted list.  The result does not
-// depend on the grid, only the work does.  Kernels, on the caller's stream:
-// bounding box, grid set-up, cell counts, a three-stage exclusive scan,
-// scatter, query.
+// depend on the grid, only the work does.  Two kernels on the caller's
+// stream: the grid build (one cooperative launch) and the query.
 
 #include <cuda_runtime.h>
 
@@ -47,35 +46,12 @@ __device__ __forceinline__ long long cell_of(const float* p, const GroupGrid& g,
     return (static_cast<long long>(c[2]) * g.dims[1] + c[1]) * g.dims[0] + c[0];
 }
 
-__global__ void grp_bbox(const float* pts, long long n, GroupGrid* g) {
-    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x)
-        for (int a = 0; a < 3; ++a) {
-            const float x = pts[3 * i + a];
-            if (isfinite(x)) {
-                mn[a] = fminf(mn[a], x);
-                mx[a] = fmaxf(mx[a], x);
-            }
-        }
-    for (int a = 0; a < 3; ++a)
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
-        }
-    if ((threadIdx.x & 31) == 0)
-        for (int a = 0; a < 3; ++a) {
-            if (isfinite(mn[a])) atomicMax(&g->box[a], ~enc_f(mn[a]));
-            if (isfinite(mx[a])) atomicMax(&g->box[3 + a], enc_f(mx[a]));
-        }
-}
-
 // Cell size h >= radius (1 + 2^-10) and at least 1/256 of the largest
 // extent, grown by 2^(1/3) until the grid has at most `budget` cells.  With
 // at most 257 cells per axis the cell map t = (x - mn) * RN(1/h) is off by
 // under 2^-12 cells, so two points closer than the radius (under 1 - 2^-10
 // cells apart) never land more than one cell apart.
-__global__ void grp_setup(GroupGrid* g, float radius, long long budget) {
+__device__ void setup_grid(GroupGrid* g, float radius, long long budget) {
     float ext = 0.0f, e[3];
     for (int a = 0; a < 3; ++a) {
         g->mn[a] = dec_f(~g->box[a]);
@@ -100,69 +76,102 @@ __global__ void grp_setup(GroupGrid* g, float radius, long long budget) {
     g->cells = cells;
 }
 
-__global__ void grp_count(const float* pts, long long n, const GroupGrid* g, uint32_t* counts) {
-    const GroupGrid G = *g;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        int c[3];
-        atomicAdd(&counts[cell_of(pts + 3 * i, G, c)], 1u);
-    }
-}
-
-// exclusive scan of counts[0..cells): block sums, a scan of those, then the offsets
-__global__ void grp_scan_local(uint32_t* v, const GroupGrid* g, uint32_t* block_sums) {
+// The grid in one cooperative launch, its phases separated by grid barriers
+// (bounded waits; a wait that gives up sets the abort flag, which the query
+// honours): bounding box and cleared counts; set-up (every block alike) and
+// cell counts; a scan of each block's share of the cells; the shares'
+// offsets; the scatter.  Afterwards end[c] holds the end of cell c in list
+// (its start is end[c - 1]).
+__global__ void __launch_bounds__(kThreads, 1)
+    grp_build(const float* pts, long long n, float radius, long long budget, GroupGrid* g, uint32_t* end,
+              uint32_t* block_sums, int32_t* list, Barrier* bar, GlobalHdr* gh) {
+    __shared__ GroupGrid sg;
+    __shared__ unsigned epoch;
+    __shared__ int flag;
     __shared__ uint32_t scratch[32];
-    const long long cells = g->cells;
-    const long long base = static_cast<long long>(blockIdx.x) * kScanBlock;
-    if (base >= cells) return;
-    uint32_t x[kScanItems], sum = 0;
-    for (int k = 0; k < kScanItems; ++k) {
-        const long long i = base + threadIdx.x * kScanItems + k;
-        x[k] = (i < cells) ? v[i] : 0u;
-        sum += x[k];
+    __shared__ float redf[6][32];
+    const int tid = threadIdx.x;
+    const unsigned nb = gridDim.x;
+    const long long gtid = blockIdx.x * static_cast<long long>(kThreads) + tid;
+    const long long gstride = static_cast<long long>(nb) * kThreads;
+    if (tid == 0) epoch = 0u;
+    for (long long i = gtid; i < budget; i += gstride) end[i] = 0u;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (long long i = gtid; i < n; i += gstride)
+        for (int a = 0; a < 3; ++a) {
+            const float x = pts[3 * i + a];
+            if (isfinite(x)) {
+                mn[a] = fminf(mn[a], x);
+                mx[a] = fmaxf(mx[a], x);
+            }
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if ((tid & 31) == 0)
+        for (int a = 0; a < 3; ++a) {
+            redf[a][tid >> 5] = mn[a];
+            redf[3 + a][tid >> 5] = mx[a];
+        }
+    __syncthreads();
+    if (tid < 6) {
+        float r = redf[tid][0];
+        for (int w = 1; w < kThreads / 32; ++w) r = (tid < 3) ? fminf(r, redf[tid][w]) : fmaxf(r, redf[tid][w]);
+        if (isfinite(r)) atomicMax(&g->box[tid], (tid < 3) ? ~enc_f(r) : enc_f(r));
     }
-    uint32_t tot;
-    uint32_t before = block_excl_scan<uint32_t>(sum, &tot, scratch);
-    for (int k = 0; k < kScanItems; ++k) {
-        const long long i = base + threadIdx.x * kScanItems + k;
-        if (i < cells) v[i] = before;
-        before += x[k];
-    }
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
-}
+    if (!grid_sync_impl(bar, gh, nb, &epoch, &flag)) return;
 
-__global__ void grp_scan_sums(uint32_t* block_sums, const GroupGrid* g) {
-    __shared__ uint32_t scratch[32];
-    const long long nb = (g->cells + kScanBlock - 1) / kScanBlock;  // <= kMaxCells / kScanBlock = 4096
-    uint32_t x[kScanItems], sum = 0;
-    for (int k = 0; k < kScanItems; ++k) {
-        const long long i = threadIdx.x * kScanItems + k;
-        x[k] = (i < nb) ? block_sums[i] : 0u;
-        sum += x[k];
+    if (tid == 0) {
+        for (int a = 0; a < 6; ++a) sg.box[a] = ld_volatile_u(&g->box[a]);
+        setup_grid(&sg, radius, budget);
+        if (blockIdx.x == 0) *g = sg;  // for the query
     }
-    uint32_t tot;
-    uint32_t before = block_excl_scan<uint32_t>(sum, &tot, scratch);
-    for (int k = 0; k < kScanItems; ++k) {
-        const long long i = threadIdx.x * kScanItems + k;
-        if (i < nb) block_sums[i] = before;
-        before += x[k];
-    }
-}
-
-__global__ void grp_scan_add(uint32_t* v, const GroupGrid* g, const uint32_t* block_sums) {
-    const long long cells = g->cells;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < cells;
-         i += static_cast<long long>(gridDim.x) * blockDim.x)
-        v[i] += block_sums[i / kScanBlock];
-}
-
-// after this, start[c] holds the end of cell c (its start is end[c - 1])
-__global__ void grp_scatter(const float* pts, long long n, const GroupGrid* g, uint32_t* start, int32_t* list) {
-    const GroupGrid G = *g;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    __syncthreads();
+    for (long long i = gtid; i < n; i += gstride) {
         int c[3];
-        const uint32_t pos = atomicAdd(&start[cell_of(pts + 3 * i, G, c)], 1u);
+        atomicAdd(&end[cell_of(pts + 3 * i, sg, c)], 1u);
+    }
+    if (!grid_sync_impl(bar, gh, nb, &epoch, &flag)) return;
+
+    // this block's share of the cells: an exclusive scan in place, the share's total aside
+    const long long cells = sg.cells;
+    const long long share = (cells + nb - 1) / nb;
+    const long long cb = share * blockIdx.x;
+    const long long ce = (cb + share < cells) ? cb + share : cells;
+    uint32_t run = 0;
+    for (long long t0 = cb; t0 < ce; t0 += static_cast<long long>(kThreads) * kScanItems) {
+        uint32_t x[kScanItems], sum = 0;
+        for (int k = 0; k < kScanItems; ++k) {
+            const long long i = t0 + static_cast<long long>(tid) * kScanItems + k;
+            x[k] = (i < ce) ? end[i] : 0u;
+            sum += x[k];
+        }
+        uint32_t tot;
+        uint32_t before = block_excl_scan<uint32_t>(sum, &tot, scratch);
+        for (int k = 0; k < kScanItems; ++k) {
+            const long long i = t0 + static_cast<long long>(tid) * kScanItems + k;
+            if (i < ce) end[i] = run + before;
+            before += x[k];
+        }
+        run += tot;
+    }
+    if (tid == 0) block_sums[blockIdx.x] = run;
+    if (!grid_sync_impl(bar, gh, nb, &epoch, &flag)) return;
+
+    // the shares before this one, then the offsets
+    uint32_t pre = 0;
+    for (unsigned b = tid; b < blockIdx.x; b += kThreads) pre += ld_volatile_u(&block_sums[b]);
+    uint32_t tot;
+    pre = block_excl_scan<uint32_t>(pre, &tot, scratch);  // (only the total matters)
+    const uint32_t off = tot;
+    for (long long i = cb + tid; i < ce; i += kThreads) end[i] += off;
+    if (!grid_sync_impl(bar, gh, nb, &epoch, &flag)) return;
+
+    for (long long i = gtid; i < n; i += gstride) {
+        int c[3];
+        const uint32_t pos = atomicAdd(&end[cell_of(pts + 3 * i, sg, c)], 1u);
         if (pos < static_cast<uint32_t>(n)) list[pos] = static_cast<int32_t>(i);
     }
 }
@@ -177,8 +186,9 @@ constexpr int kQueryWarps = 4;  // warps per block of the query
 __global__ void __launch_bounds__(32 * kQueryWarps)
     grp_query(const float* pts, long long n, const int32_t* centres, long long m, float radius, int nsample,
               const GroupGrid* g, const uint32_t* end, const int32_t* list, int32_t* out_idx, float* out_xyz,
-              int32_t* status) {
+              int32_t* status, const GlobalHdr* gh) {
     __shared__ int32_t sbest[kQueryWarps][kGrpMaxSample];
+    if (ld_volatile(&gh->abort)) return;  // the build gave up (its status says so)
     const GroupGrid G = *g;
     const float r2 = __fmul_rn(radius, radius);
     const int lane = threadIdx.x & 31;
@@ -220,7 +230,7 @@ __global__ void __launch_bounds__(32 * kQueryWarps)
                         bool ok = false;
                         if (q < b) {
                             k = list[q];
-                            if (k < top) {
+                            if (k >= 0 && k < n && k < top) {
                                 const float ex = __fsub_rn(pts[3ll * k], cx), ey = __fsub_rn(pts[3ll * k + 1], cy),
                                             ez = __fsub_rn(pts[3ll * k + 2], cz);
                                 const float d2 =
@@ -282,9 +292,17 @@ __global__ void __launch_bounds__(32 * kQueryWarps)
 
 }  // namespace
 
+int group_coresident_blocks(int device) {
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grp_build, kThreads, 0) != cudaSuccess) return -1;
+    if (per_sm < 1) return -1;
+    return sms < kMaxBlocks ? sms : kMaxBlocks;  // one block per SM
+}
+
 int launch_ball_query(const float* points, long long n, const int32_t* centres, long long m, float radius,
                       int nsample, int32_t* out_idx, float* out_xyz, unsigned char* ws, const Layout& lay,
-                      int32_t* status, cudaStream_t stream) {
+                      int32_t* status, int nblocks, cudaStream_t stream) {
     if (nsample < 1 || nsample > kGrpMaxSample) return -1;
     // scratch: grid parameters and scan block sums in the phase-timer area,
     // cell counts in the candidate area, the sorted point list in staged points
@@ -303,21 +321,25 @@ int launch_ball_query(const float* points, long long n, const int32_t* centres, 
         return static_cast<unsigned>(b < 1 ? 1 : b);
     };
     if (cudaMemsetAsync(g, 0, sizeof(GroupGrid), stream) != cudaSuccess) return -1;
-    grp_bbox<<<blocks(n), t, 0, stream>>>(points, n, g);
-    grp_setup<<<1, 1, 0, stream>>>(g, radius, budget);
-    // the grid size is known on the device only: size the cell work by the budget
-    if (cudaMemsetAsync(counts, 0, 4 * budget, stream) != cudaSuccess) return -1;
-    grp_count<<<blocks(n), t, 0, stream>>>(points, n, g, counts);
-    grp_scan_local<<<static_cast<unsigned>((budget + kScanBlock - 1) / kScanBlock), 1024, 0, stream>>>(counts, g,
-                                                                                                       block_sums);
-    grp_scan_sums<<<1, 1024, 0, stream>>>(block_sums, g);
-    grp_scan_add<<<blocks(budget), t, 0, stream>>>(counts, g, block_sums);
-    grp_scatter<<<blocks(n), t, 0, stream>>>(points, n, g, counts, list);
+    Barrier* bar = reinterpret_cast<Barrier*>(ws + lay.barrier);  // zeroed by the caller
+    GlobalHdr* gh = reinterpret_cast<GlobalHdr*>(ws + lay.ghdr);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(nblocks));
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, grp_build, points, static_cast<long long>(n), radius, budget, g, counts, block_sums,
+                           list, bar, gh) != cudaSuccess)
+        return -1;
     long long qb = (m + kQueryWarps - 1) / kQueryWarps;
     if (qb > 65536) qb = 65536;
     grp_query<<<static_cast<unsigned>(qb < 1 ? 1 : qb), 32 * kQueryWarps, 0, stream>>>(
-        points, n, centres, m, radius, nsample, g, counts, list, out_idx, out_xyz, status);
-    return cudaGetLastError() == cudaSuccess ? 8 : -1;
+        points, n, centres, m, radius, nsample, g, counts, list, out_idx, out_xyz, status, gh);
+    return cudaGetLastError() == cudaSuccess ? 2 : -1;
 }
 
 }  // namespace havk

@@ -224,10 +224,11 @@ int launch_small(const Plan& plan, int first_level, int q, int nclusters, cudaSt
 constexpr int kSoloMax = 4096;
 constexpr int kSoloAlone = 1024;  // a single segment this small goes to one CTA, not a cluster
 int launch_solo(const Plan& plan, int first_level, int nblocks, cudaStream_t stream);
-// Grouping around centres (hav_group.cu).
+// Grouping around centres (hav_group.cu); the blocks of its cooperative grid build.
+int group_coresident_blocks(int device);
 int launch_ball_query(const float* points, long long n, const int32_t* centres, long long m, float radius,
                       int nsample, int32_t* out_idx, float* out_xyz, unsigned char* ws, const Layout& lay,
-                      int32_t* status, cudaStream_t stream);
+                      int32_t* status, int nblocks, cudaStream_t stream);
 // Subset point spacing (hav_spacing.cu).
 int launch_spacing(const float* points, long long n, const int32_t* idx, long long m, float* out_d2,
                    int32_t* status, int sms, cudaStream_t stream);

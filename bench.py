@@ -675,12 +675,16 @@ def run_spacing(args, world, rank, local):
             sp = np.sqrt(d2.cpu().numpy().astype(np.float64))
             if fps_min is None:
                 fps_min = float(sp.min())
-            edges = np.linspace(0.0, 3.0, 25) * fps_min  # bins in units of FPS's minimum spacing
-            hist, _ = np.histogram(np.minimum(sp, edges[-1]), bins=edges)
+            # Fig. 3 as integer counts on the GPU: 24 bins of 1/8 of FPS's
+            # minimum spacing (edges as binary32 squared distances)
+            edges = (np.linspace(0.0, 3.0, 25) * fps_min) ** 2
+            _, counts = hav.hav_spacing_histogram(ctx, d, idx, edges.astype(np.float32))
+            counts = counts.cpu().numpy()
             res[name] = {"min": float(sp.min()), "p10": float(np.percentile(sp, 10)),
                          "median": float(np.median(sp)), "mean": float(sp.mean()),
                          "below_fps_min": float((sp < fps_min).mean()),
-                         "hist_fps_min_units_0_to_3": hist.tolist(), "spacing_ms": a.elapsed_time(b)}
+                         "hist_fps_min_units_0_to_3": counts[1:-1].tolist(), "above_3_fps_min": int(counts[-1]),
+                         "spacing_ms": a.elapsed_time(b)}
         st, _ = hav.hav_status_get(ctx, 1)
         ctx.close()
         cases.append({"case": case, "n": n, "m": m, "fps_min_spacing": fps_min, "samplers": res, "status": st})

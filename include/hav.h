@@ -359,6 +359,20 @@ hav_status hav_fps(hav_ctx* ctx, const float* points, int64_t n, int64_t m, int3
 hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32_t* idx, int64_t m,
                        float* out_d2, hav_stream stream);
 
+/* hav_spacing plus the histogram of the spacings that Fig. 3 (Section 3.1)
+ * plots, over bin edges the caller chooses.  edges: HOST, nbins + 1 finite
+ * binary32 squared distances, strictly ascending; 1 <= nbins <=
+ * HAV_SPACING_MAX_BINS.  out_d2: device, m floats (as hav_spacing writes
+ * them).  out_counts: device, nbins + 2 uint64: out_counts[0] counts the
+ * spacings below edges[0], out_counts[nbins + 1] those above edges[nbins],
+ * and out_counts[1 + i] those with edges[i] <= d2 < edges[i + 1], the last
+ * bin also taking d2 == edges[nbins] (the bins of numpy.histogram).  Integer
+ * counts, exact.  Three launches on `stream`. */
+#define HAV_SPACING_MAX_BINS 1024
+hav_status hav_spacing_histogram(hav_ctx* ctx, const float* points, int64_t n, const int32_t* idx, int64_t m,
+                                 const float* edges, int32_t nbins, float* out_d2, uint64_t* out_counts,
+                                 hav_stream stream);
+
 /* Grouping around sampled centres, the step that follows sampling in the
  * sample-group-aggregate block of point networks (Section 3.1; the ball query
  * of PointNet++): for centre j (the point centres[j]), the nsample smallest

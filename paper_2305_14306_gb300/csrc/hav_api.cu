@@ -428,6 +428,28 @@ hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32
     return HAV_OK;
 }
 
+hav_status hav_spacing_histogram(hav_ctx* ctx, const float* points, int64_t n, const int32_t* idx, int64_t m,
+                                 const float* edges, int32_t nbins, float* out_d2, uint64_t* out_counts,
+                                 hav_stream stream) {
+    if (!ctx || !edges || !out_counts || nbins < 1 || nbins > HAV_SPACING_MAX_BINS) return HAV_ERR_INVALID;
+    havk::HistEdges E;
+    std::memset(&E, 0, sizeof E);
+    for (int i = 0; i <= nbins; ++i) {
+        if (!std::isfinite(edges[i]) || (i > 0 && !(edges[i] > edges[i - 1]))) return HAV_ERR_INVALID;
+        E.e[i] = edges[i];
+    }
+    E.nbins = nbins;
+    hav_status st = hav_spacing(ctx, points, n, idx, m, out_d2, stream);
+    if (st != HAV_OK) return st;
+    cudaStream_t strm = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(out_counts, 0, sizeof(uint64_t) * (nbins + 2), strm) != cudaSuccess) return HAV_ERR_CUDA;
+    if (m == 0) return HAV_OK;
+    if (!counted(ctx, havk::launch_spacing_hist(out_d2, m, E, reinterpret_cast<unsigned long long*>(out_counts),
+                                                strm)))
+        return HAV_ERR_CUDA;
+    return HAV_OK;
+}
+
 hav_status hav_ball_query(hav_ctx* ctx, const float* points, int64_t n, const int32_t* centres, int64_t m,
                           float radius, int32_t nsample, int32_t* out_idx, float* out_xyz, hav_stream stream) {
     if (!ctx || n < 0 || m < 0 || n > ctx->lay.max_points || m >= (1ll << 31)) return HAV_ERR_INVALID;

@@ -229,9 +229,16 @@ int group_coresident_blocks(int device);
 int launch_ball_query(const float* points, long long n, const int32_t* centres, long long m, float radius,
                       int nsample, int32_t* out_idx, float* out_xyz, unsigned char* ws, const Layout& lay,
                       int32_t* status, int nblocks, cudaStream_t stream);
-// Subset point spacing (hav_spacing.cu).
+// Subset point spacing (hav_spacing.cu), and its histogram over bin edges.
 int launch_spacing(const float* points, long long n, const int32_t* idx, long long m, float* out_d2,
                    int32_t* status, int sms, cudaStream_t stream);
+constexpr int kHistEdgesMax = HAV_SPACING_MAX_BINS + 1;
+struct HistEdges {
+    float e[kHistEdgesMax];
+    int32_t nbins;
+};
+int launch_spacing_hist(const float* d2, long long m, const HistEdges& edges, unsigned long long* counts,
+                        cudaStream_t stream);
 // Representative coordinates after a one-layer call (hav_repr.cu).
 int launch_repr(const float* points, long long n, long long m, const int32_t* idx, float* xyz, int select,
                 const float aspect[3], unsigned char* ws, const Layout& lay, cudaStream_t stream);

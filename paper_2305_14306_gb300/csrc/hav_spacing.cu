@@ -89,7 +89,54 @@ __global__ void __launch_bounds__(kSpThreads) spacing_kernel(const float* pts, l
         if (qpos[u] >= 0 && best[u] < INFINITY) atomicMin(out + qpos[u], __float_as_uint(best[u]));
 }
 
+// Histogram of the spacings over caller-given bin edges e[0] < ... < e[B]
+// (binary32 squared distances): bin i holds e[i] <= d2 < e[i + 1], the last
+// bin also d2 == e[B] (numpy's convention); counts[0] holds the values below
+// e[0] (or not ordered against it), counts[B + 1] those above e[B], bins at
+// counts[1..B].  Integer counts, so the order of the additions does not matter.
+__global__ void __launch_bounds__(kSpThreads) spacing_hist(const unsigned* d2bits, long long m, const HistEdges E,
+                                                           unsigned long long* counts) {
+    __shared__ float se[kHistEdgesMax];
+    __shared__ unsigned sc[kHistEdgesMax + 1];
+    const int nb = E.nbins;
+    for (int k = threadIdx.x; k <= nb; k += kSpThreads) se[k] = E.e[k];
+    for (int k = threadIdx.x; k <= nb + 1; k += kSpThreads) sc[k] = 0u;
+    __syncthreads();
+    for (long long r = blockIdx.x * static_cast<long long>(kSpThreads) + threadIdx.x; r < m;
+         r += static_cast<long long>(gridDim.x) * kSpThreads) {
+        const float x = __uint_as_float(d2bits[r]);
+        int slot;
+        if (!(x >= se[0])) {
+            slot = 0;
+        } else if (x > se[nb]) {
+            slot = nb + 1;
+        } else if (x == se[nb]) {
+            slot = nb;
+        } else {
+            int lo = 0, hi = nb;  // largest i < nb with se[i] <= x
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (se[mid] <= x) lo = mid; else hi = mid;
+            }
+            slot = lo + 1;
+        }
+        atomicAdd(&sc[slot], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k <= nb + 1; k += kSpThreads)
+        if (sc[k]) atomicAdd(counts + k, static_cast<unsigned long long>(sc[k]));
+}
+
 }  // namespace
+
+int launch_spacing_hist(const float* d2, long long m, const HistEdges& edges, unsigned long long* counts,
+                        cudaStream_t stream) {
+    long long b = (m + kSpThreads - 1) / kSpThreads;
+    if (b > 1024) b = 1024;
+    spacing_hist<<<static_cast<unsigned>(b < 1 ? 1 : b), kSpThreads, 0, stream>>>(
+        reinterpret_cast<const unsigned*>(d2), m, edges, counts);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_spacing(const float* points, long long n, const int32_t* idx, long long m, float* out_d2,
                    int32_t* status, int sms, cudaStream_t stream) {

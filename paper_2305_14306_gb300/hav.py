@@ -93,7 +93,7 @@ EXPORTS = [
     "hav_sample", "hav_sample_levels", "hav_sample_batched", "hav_status_get", "hav_trace_get",
     "hav_count", "hav_status_string", "hav_sample_noalloc", "hav_phase_times_get", "hav_fps",
     "hav_context_set_blocks", "hav_context_get_tuning", "hav_context_set_tuning", "hav_sample_xyz",
-    "hav_spacing", "hav_ball_query", "hav_context_launches",
+    "hav_spacing", "hav_spacing_histogram", "hav_ball_query", "hav_context_launches",
 ]
 HAV_FLAG_PHASE_TIMES = 1
 HAV_FLAG_TEST_TIMEOUT = 2
@@ -129,6 +129,8 @@ def load(path: str = LIB_PATH):
         L.hav_ball_query.restype = C.c_int
         L.hav_spacing.argtypes = [vp, vp, i64, vp, i64, vp, vp]
         L.hav_spacing.restype = C.c_int
+        L.hav_spacing_histogram.argtypes = [vp, vp, i64, vp, i64, P(C.c_float), C.c_int32, vp, vp, vp]
+        L.hav_spacing_histogram.restype = C.c_int
         L.hav_sample_xyz.argtypes = [vp, vp, i64, i64, P(hav_params), vp, vp, vp]
         L.hav_sample_xyz.restype = C.c_int
         L.hav_sample_levels.argtypes = [vp, vp, i64, P(C.c_int64), i32, P(hav_params), P(vp), vp]
@@ -401,6 +403,34 @@ def hav_spacing(ctx: Context, points, idx, out=None, stream=None):
                             C.c_void_p(idx.data_ptr()), m, C.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(st, "hav_spacing")
     return out
+
+
+SPACING_MAX_BINS = 1024
+
+
+def hav_spacing_histogram(ctx: Context, points, idx, edges_d2, out=None, counts=None, stream=None):
+    """hav_spacing and the histogram of the spacings over the given bin edges
+    (squared distances, binary32, ascending): returns (d2, counts) with counts
+    an int64 CUDA tensor of len(edges_d2) + 1 entries: below the first edge,
+    the bins (numpy.histogram's), above the last edge."""
+    import torch
+    points = _points(points)
+    if idx.dim() != 1:
+        raise ValueError("idx must be one-dimensional")
+    idx = idx.to(dtype=torch.int32, device=points.device).contiguous()
+    e = np.ascontiguousarray(edges_d2, dtype=np.float32)
+    if e.ndim != 1 or not (2 <= e.shape[0] <= SPACING_MAX_BINS + 1):
+        raise ValueError("edges_d2 must hold 2 .. 1025 edges")
+    nb = e.shape[0] - 1
+    m = idx.shape[0]
+    out = _out(out, m, torch.float32, points, "out")
+    counts = _out(counts, nb + 2, torch.int64, points, "counts")
+    st = load().hav_spacing_histogram(ctx.handle, C.c_void_p(points.data_ptr()), points.shape[0],
+                                      C.c_void_p(idx.data_ptr()), m,
+                                      e.ctypes.data_as(C.POINTER(C.c_float)), nb, C.c_void_p(out.data_ptr()),
+                                      C.c_void_p(counts.data_ptr()), _stream_handle(stream))
+    _check(st, "hav_spacing_histogram")
+    return out, counts
 
 
 def hav_ball_query(ctx: Context, points, centres, radius: float, nsample: int, out=None, xyz=True, stream=None):

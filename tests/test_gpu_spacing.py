@@ -86,3 +86,57 @@ def test_spacing_rejects_bad_indices(hv, ctx):
     hv.hav_spacing(ctx, pts, torch.tensor([0, 5, 7], dtype=torch.int32, device="cuda"))
     st, _ = hv.hav_status_get(ctx, 1)
     assert st == 0
+
+
+def numpy_counts(d2, edges):
+    """below, numpy.histogram's bins, above: the layout hav_spacing_histogram writes."""
+    d2 = np.asarray(d2, dtype=np.float32)
+    e = np.asarray(edges, dtype=np.float32)
+    hist, _ = np.histogram(d2, bins=e)
+    return np.concatenate([[int((d2 < e[0]).sum())], hist, [int((d2 > e[-1]).sum())]]).astype(np.int64)
+
+
+@pytest.mark.parametrize("sampler", ["hav", "random", "fps"])
+def test_spacing_histogram_matches_numpy_on_the_oracle_spacings(hv, ctx, oracle_mod, sampler):
+    # Fig. 3's distributions as integer counts: the GPU histogram of the
+    # spacings equals numpy.histogram of the oracle's spacings, with edges that
+    # include some spacings exactly (the half-open bins and the closed last bin)
+    pts = scenes.uniform_box(16384, 3)
+    rng = np.random.default_rng(8)
+    if sampler == "hav":
+        idx = oracle_mod.sample(pts, 4096)
+    elif sampler == "fps":
+        idx = oracle_mod.fps(pts, 4096)
+    else:
+        idx = np.sort(rng.choice(16384, size=4096, replace=False))
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    d2 = oracle_mod.spacing(pts, idx)
+    geo = np.geomspace(max(float(d2.min()), 1e-6) * 0.5, float(d2.max()) * 0.9, 30)
+    exact = rng.choice(d2, size=6, replace=False)
+    edges = np.unique(np.concatenate([geo.astype(np.float32), exact, [d2.max()]]).astype(np.float32))
+    got_d2, counts = hv.hav_spacing_histogram(ctx, dev(pts), torch.from_numpy(idx).cuda(), edges)
+    st, _ = hv.hav_status_get(ctx, 1)
+    assert st == 0
+    assert np.array_equal(got_d2.cpu().numpy().view(np.uint32), d2.view(np.uint32))
+    want = numpy_counts(d2, edges)
+    assert np.array_equal(counts.cpu().numpy(), want)
+    assert int(want.sum()) == 4096 and want[-1] == 0  # the largest spacing is the closed last edge
+
+
+def test_spacing_histogram_edge_cases(hv, ctx, oracle_mod):
+    pts = scenes.uniform_box(2000, 4)
+    idx = np.arange(0, 2000, 7, dtype=np.int32)
+    d2 = oracle_mod.spacing(pts, idx)
+    # every value below the first edge, every value above the last one, one bin
+    for edges in ([float(d2.max()) * 2, float(d2.max()) * 3], [0.0, float(d2.min()) * 0.5], [0.0, 1e9]):
+        e = np.asarray(edges, dtype=np.float32)
+        _, counts = hv.hav_spacing_histogram(ctx, dev(pts), torch.from_numpy(idx).cuda(), e)
+        assert np.array_equal(counts.cpu().numpy(), numpy_counts(d2, e))
+    # a subset of one point: +inf spacing, counted above the last edge
+    _, counts = hv.hav_spacing_histogram(ctx, dev(pts), torch.from_numpy(idx[:1].copy()).cuda(),
+                                         np.array([0.0, 1.0], np.float32))
+    assert counts.cpu().numpy().tolist() == [0, 0, 1]
+    # edges must be finite and strictly ascending
+    for bad in ([1.0, 1.0], [2.0, 1.0], [0.0, np.inf]):
+        with pytest.raises(hv.HavError):
+            hv.hav_spacing_histogram(ctx, dev(pts), torch.from_numpy(idx).cuda(), np.array(bad, np.float32))

@@ -857,7 +857,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="indoor-1m")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-slots", type=int, default=2)
+    ap.add_argument("--serve-slots", type=int, default=3,
+                    help="co-resident serving slots (measured on GB300: 3 beat 1, 2 and 4)")
     ap.add_argument("--no-search-compare", action="store_true",
                     help="skip timing the guided search start beside the default one")
     ap.add_argument("--search", choices=["bisect", "guided"], default="bisect",
@@ -865,7 +866,7 @@ def main():
                          "guided by the cloud's previous search")
     ap.add_argument("--no-sub-workloads", action="store_true",
                     help="default workload only: skip the batch64 and serving objects of the line")
-    ap.add_argument("--serve-requests", type=int, default=400,
+    ap.add_argument("--serve-requests", type=int, default=800,
                     help="requests of the serving object in the default line")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON cache of autotuned knobs (default: always sweep, write nothing)")

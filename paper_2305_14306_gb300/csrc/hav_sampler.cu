@@ -51,7 +51,7 @@ static_assert(kHistBins % kThreads == 0, "the cut-off scan gives each thread who
 constexpr int kSetSlots = 16384;   // block-local dedupe set of a bisection pass (128 KB + 32 KB list)
 constexpr size_t kPassSmem = static_cast<size_t>(kSetSlots) * 10;
 constexpr int kSelSlots = 8192;    // block-local argmin table of the selection (128 KB + 16 KB list)
-constexpr size_t kSelSmem = static_cast<size_t>(kSelSlots) * 18;
+constexpr size_t kSelSmem = static_cast<size_t>(kSelSlots) * 20;  // + the list of keys that go global
 constexpr size_t kDynSmem = kPassSmem > kSelSmem ? kPassSmem : kSelSmem;
 constexpr int kBucketMin = 1 << 17;
 // Loads and probes in flight per thread (the kernel's template arguments,
@@ -123,6 +123,9 @@ struct Smem {
     float own_k[3];
     unsigned rest_n;
     unsigned xcnt[kMaxCand];
+    int ocnt[kLocalItems];  // owned voxels the selection listed for the classification, per item
+    unsigned gl_n;          // keys of the selection that go to the global table
+    unsigned bh[kHistBins]; // this block's cut-off histogram of a selection (added to the global one once)
     int ntimes;
     int was_clean;
     int cut_seg;
@@ -1121,9 +1124,20 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         skey[k] = kEmptyKey;
                         sval[k] = kEmptyVal;
                     }
-                    if (tid == 0) st.list_n = 0u;
+                    for (int k = tid; k < kHistBins; k += kThreads) st.bh[k] = 0u;
+                    if (tid == 0) {
+                        st.list_n = 0u;
+                        st.rest_n = 0u;
+                        st.gl_n = 0u;
+                    }
                     __syncthreads();
                     const Grid& G = st.grid[s];
+                    // level 0 of a bucketed cloud: a voxel the block owns whole has its
+                    // representative in the block's own minimum; it skips the global
+                    // table and is listed for the classification (in the next level's
+                    // staged-point array, not written before this level's compaction)
+                    const bool owning = (j == 0 && st.own_on);
+                    Cand* olist = reinterpret_cast<Cand*>(d.ord[1]) + a;
                     const int sel = st.sel[s];
                     const int sc = st.sel_cand[s];
                     unsigned long long* T = d.tk[sel] + sc * tstride + st.tab_off[s];
@@ -1139,8 +1153,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         }
                         if (atomicMin(V + slot, packed) == kEmptyVal) {
                             ++first;
-                            atomicAdd(&hist[static_cast<long long>(s) * kHistBins + (priority(key) >> (64 - kHistBits))],
-                                      1u);
+                            atomicAdd(&st.bh[priority(key) >> (64 - kHistBits)], 1u);
                         }
                     };
                     const int lane = tid & 31;
@@ -1191,7 +1204,34 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     }
                     __syncthreads();
                     const int nl = static_cast<int>(st.list_n);
-                    for (int k0 = tid; k0 < nl; k0 += kProbes * kThreads) {
+                    // owned voxels first: listed for the classification, counted here;
+                    // the other keys are packed into a second list for the global table
+                    const unsigned short* gl = list;
+                    int ng = nl;
+                    if (owning) {
+                        unsigned short* glist = list + kSelSlots;
+                        for (int k0 = tid - lane; k0 < nl; k0 += kThreads) {  // warp-uniform
+                            const int k = k0 + lane;
+                            const int si = (k < nl) ? static_cast<int>(list[k]) : 0;
+                            const unsigned long long key = (k < nl) ? skey[si] : kEmptyKey;
+                            const bool own = key != kEmptyKey &&
+                                             voxel_owned(key, G, st.mn[0], st.own_k, st.own_lo, st.own_hi);
+                            const int opos = warp_append(own, &st.rest_n);
+                            if (opos >= 0) {
+                                const unsigned long long h = priority(key);
+                                olist[opos].h = h;
+                                olist[opos].g = static_cast<uint32_t>(sval[si] & 0xffffffffull);
+                                ++first;
+                                atomicAdd(&st.bh[h >> (64 - kHistBits)], 1u);
+                            }
+                            const int gpos = warp_append(key != kEmptyKey && !own, &st.gl_n);
+                            if (gpos >= 0) glist[gpos] = static_cast<unsigned short>(si);
+                        }
+                        __syncthreads();
+                        gl = glist;
+                        ng = static_cast<int>(st.gl_n);
+                    }
+                    for (int k0 = tid - lane; k0 < ng; k0 += kProbes * kThreads) {  // warp-uniform
                         unsigned long long key[kProbes];
                         unsigned long long* Tp[kProbes];
                         long long slot[kProbes];
@@ -1199,24 +1239,30 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         int sidx[kProbes];
 #pragma unroll
                         for (int u = 0; u < kProbes; ++u) {
-                            const int k = k0 + u * kThreads;
-                            sidx[u] = (k < nl) ? static_cast<int>(list[k]) : 0;
-                            key[u] = (k < nl) ? skey[sidx[u]] : kEmptyKey;
+                            const int k = k0 + lane + u * kThreads;
+                            sidx[u] = (k < ng) ? static_cast<int>(gl[k]) : 0;
+                            key[u] = (k < ng) ? skey[sidx[u]] : kEmptyKey;
                             Tp[u] = T;
                         }
                         find_or_insert_batch<kProbes>(Tp, cap, key, slot, fr);
 #pragma unroll
                         for (int u = 0; u < kProbes; ++u) {
-                            if (key[u] == kEmptyKey) continue;
-                            if (slot[u] < 0) {
-                                bad = HAV_ERR_TABLE_FULL;
-                                continue;
-                            }
-                            global_min(key[u], slot[u], fr[u], sval[sidx[u]]);
+                            const bool ok = key[u] != kEmptyKey && slot[u] >= 0;
+                            if (key[u] != kEmptyKey && slot[u] < 0) bad = HAV_ERR_TABLE_FULL;
+                            // a fresh insert (a voxel no count pass put in this table) is
+                            // logged, warp-aggregated
+                            const int pos = warp_append(ok && fr[u], &st.dcnt[sel][li][sc]);
+                            if (pos >= 0)
+                                d.dirty[sel][sc * dstride + a + pos] =
+                                    static_cast<uint32_t>(sc * tstride + st.tab_off[s] + slot[u]);
+                            if (ok) global_min(key[u], slot[u], false, sval[sidx[u]]);
                         }
                     }
                     if (bad) seg_error(d, s, bad);
-                    const unsigned total = block_sum(first, st.scan_u);
+                    const unsigned total = block_sum(first, st.scan_u);  // (its barriers order bh)
+                    for (int k = tid; k < kHistBins; k += kThreads)
+                        if (st.bh[k]) atomicAdd(&hist[static_cast<long long>(s) * kHistBins + k], st.bh[k]);
+                    if (tid == 0) st.ocnt[li] = owning ? static_cast<int>(st.rest_n) : 0;
                     if (tid == 0 && total) atomicAdd(&ls[s].kstar, total);
                 }
             }
@@ -1290,6 +1336,26 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         const unsigned long long h = priority(d.tk[sel][gs]);
                         const int hb = static_cast<int>(h >> (64 - kHistBits));
                         if (hb < bin) {
+                            mark_taken(taken, ord, d.posof, g);
+                        } else if (hb == bin) {
+                            const uint32_t ci = atomicAdd(&ls[s].cand, 1u);
+                            if (static_cast<long long>(ci) < (C >> 1)) {
+                                Cand* cd = d.cand + st.cand_off[s] + ci;
+                                cd->h = h;
+                                cd->g = static_cast<uint32_t>(g);
+                            } else {
+                                seg_error(d, s, HAV_ERR_TABLE_FULL);
+                            }
+                        }
+                    }
+                    // the voxels the selection kept out of the table (owned whole)
+                    const int oc = st.ocnt[li];
+                    const Cand* ol = reinterpret_cast<const Cand*>(d.ord[1]) + a;
+                    for (int k = tid; k < oc; k += kThreads) {
+                        const unsigned long long h = ol[k].h;
+                        const int g = static_cast<int>(ol[k].g);
+                        const int hb = static_cast<int>(h >> (64 - kHistBits));
+                        if (!cut || hb < bin) {
                             mark_taken(taken, ord, d.posof, g);
                         } else if (hb == bin) {
                             const uint32_t ci = atomicAdd(&ls[s].cand, 1u);

@@ -314,12 +314,6 @@ int launch_ball_query(const float* points, long long n, const int32_t* centres, 
     if (budget > kMaxCells) budget = kMaxCells;
     if (n > lay.max_points) return -1;
     static_assert(256 + 4 * (kMaxCells / kScanBlock) <= 2 * 8 * kPhaseTimes, "scan scratch fits");
-    const int t = 256;
-    auto blocks = [&](long long work) {
-        long long b = (work + t - 1) / t;
-        if (b > 4096) b = 4096;
-        return static_cast<unsigned>(b < 1 ? 1 : b);
-    };
     if (cudaMemsetAsync(g, 0, sizeof(GroupGrid), stream) != cudaSuccess) return -1;
     Barrier* bar = reinterpret_cast<Barrier*>(ws + lay.barrier);  // zeroed by the caller
     GlobalHdr* gh = reinterpret_cast<GlobalHdr*>(ws + lay.ghdr);

@@ -116,11 +116,13 @@ struct Smem {
     unsigned epoch;
     unsigned list_n;
     int set_clean;  // 1 when every slot of the block set is empty
-    // level 0 of one bucketed cloud: the Morton cells [own_lo, own_hi] whose
-    // points all lie in this block's work item (own_on), and per pass the keys
-    // that go to the global table (rest_n) and the owned ones counted here
-    int own_on, own_lo, own_hi;
-    float own_k[3];
+    // a bucketed cloud (level 0 and the levels that keep its order): the
+    // Morton cells [own_lo, own_hi] of the level-0 bucketing (its box own_mn,
+    // own_mx, own_k[a] = 16 / extent) whose points all lie in this block's work
+    // item (own_on), and per pass the keys that go to the global table
+    // (rest_n) and the owned ones counted here
+    int own_on, own_lo, own_hi, bucketed;
+    float own_k[3], own_mn[3], own_mx[3];
     unsigned rest_n;
     unsigned xcnt[kMaxCand];
     int ocnt[kLocalItems];  // owned voxels the selection listed for the classification, per item
@@ -460,6 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
     d.ptimes = P.ptimes;
     d.ptimes_cap = P.ptimes_cap;
     for (int k = tid; k < P.S; k += kThreads) st.gm[k] = 0;  // no previous search yet
+    if (tid == 0) st.bucketed = 0;
     if (tid == 0) {
         st.fused_uses[0] = st.fused_uses[1] = 0u;
         st.fused_last[0] = st.fused_last[1] = 0ull;
@@ -593,6 +596,32 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
         }
         __syncthreads();
 
+        // A later level of a bucketed cloud keeps the bucketing's order (each
+        // level's points are a subsequence of the previous level's, in order),
+        // so its points are sorted by their level-0 Morton cell: the cells this
+        // block's item holds whole run from the first cell starting in it to
+        // the last cell ending in it, read off the cells of the points at and
+        // beside the item's two ends.
+        if (j > 0 && st.bucketed && S == 1 && tid == 0 && st.items_total <= static_cast<int>(nb) &&
+            static_cast<int>(blockIdx.x) < st.items_total) {
+            int ia, ib;
+            item_range(st, S, blockIdx.x, &ia, &ib);
+            auto cell = [&](int i) {
+                const float4 q = ord[i];
+                const float p3[3] = {q.x, q.y, q.z};
+                return static_cast<int>(bucket_of(p3, st.own_mn, st.own_mx));
+            };
+            if (ib > ia) {
+                const int cf = cell(ia), cl = cell(ib - 1);
+                const int lo = (ia == 0 || cell(ia - 1) < cf) ? cf : cf + 1;
+                const int hi = (ib == NL || cell(ib) > cl) ? cl : cl - 1;
+                st.own_lo = lo;
+                st.own_hi = hi;
+                st.own_on = (lo <= hi) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+
         // ---------------------------------------- bucketing (one large cloud)
         if (bucketing) {
             if (tid == 0) st.set_clean = 0;
@@ -655,7 +684,13 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     st.own_lo = c_lo;
                     st.own_hi = lo - 1;
                     st.own_on = (c_lo <= lo - 1) ? 1 : 0;
+                }
+                if (tid == 0) {
+                    // the bucketing's box, kept for the levels that inherit its order
+                    st.bucketed = 1;
                     for (int a3 = 0; a3 < 3; ++a3) {
+                        st.own_mn[a3] = st.mn[0][a3];
+                        st.own_mx[a3] = st.mx[0][a3];
                         const float e = __fsub_rn(st.mx[0][a3], st.mn[0][a3]);
                         st.own_k[a3] = (e > 0.0f) ? __fdiv_rn(16.0f, e) : 0.0f;
                     }
@@ -910,7 +945,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     // whole is counted here; the other keys go to the global table
                     const unsigned short* gl = list;
                     int ng = nl;
-                    if (j == 0 && st.own_on && nl <= kSetSlots / 2) {
+                    // (below 256 listed keys the test costs about what it saves)
+                    if (st.own_on && nl >= 256 && nl <= kSetSlots / 2) {
                         unsigned short* rest = list + kSetSlots / 2;
                         unsigned mine = 0;  // owned keys of this thread (one candidate)
                         for (int k0 = tid - lane; k0 < nl; k0 += kThreads) {  // warp-uniform
@@ -920,7 +956,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             if (k < nl) {
                                 const int idx = list[k];
                                 c = idx >> setc_log2;
-                                glob = !voxel_owned(set[idx], st.cgrid[li][c], st.mn[0], st.own_k, st.own_lo,
+                                glob = !voxel_owned(set[idx], st.cgrid[li][c], st.own_mn, st.own_k, st.own_lo,
                                                     st.own_hi);
                             }
                             const int pos = warp_append(glob, &st.rest_n);
@@ -1136,8 +1172,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     // representative in the block's own minimum; it skips the global
                     // table and is listed for the classification (in the next level's
                     // staged-point array, not written before this level's compaction)
-                    const bool owning = (j == 0 && st.own_on);
-                    Cand* olist = reinterpret_cast<Cand*>(d.ord[1]) + a;
+                    const bool owning = st.own_on != 0;
+                    Cand* olist = reinterpret_cast<Cand*>(d.ord[(j + 1) & 1]) + a;
                     const int sel = st.sel[s];
                     const int sc = st.sel_cand[s];
                     unsigned long long* T = d.tk[sel] + sc * tstride + st.tab_off[s];
@@ -1215,7 +1251,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             const int si = (k < nl) ? static_cast<int>(list[k]) : 0;
                             const unsigned long long key = (k < nl) ? skey[si] : kEmptyKey;
                             const bool own = key != kEmptyKey &&
-                                             voxel_owned(key, G, st.mn[0], st.own_k, st.own_lo, st.own_hi);
+                                             voxel_owned(key, G, st.own_mn, st.own_k, st.own_lo, st.own_hi);
                             const int opos = warp_append(own, &st.rest_n);
                             if (opos >= 0) {
                                 const unsigned long long h = priority(key);
@@ -1350,7 +1386,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     }
                     // the voxels the selection kept out of the table (owned whole)
                     const int oc = st.ocnt[li];
-                    const Cand* ol = reinterpret_cast<const Cand*>(d.ord[1]) + a;
+                    const Cand* ol = reinterpret_cast<const Cand*>(d.ord[(j + 1) & 1]) + a;
                     for (int k = tid; k < oc; k += kThreads) {
                         const unsigned long long h = ol[k].h;
                         const int g = static_cast<int>(ol[k].g);

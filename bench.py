@@ -770,7 +770,7 @@ def run_serving(args, world, rank, local, sub=False, requests=None):
             out.append(serving.Request(i, float(arrivals[i]), pts, int(m)))
         return out
 
-    slot_points = int(pool_n.max()) * 2
+    slot_points = int(pool_n.max()) * args.serve_slot_scale
     sp = hav.params(search=args.search)
     served = serving.Server(slots=args.serve_slots, slot_points=slot_points, max_segments=64, params=sp)
     plain = serving.Server(slots=1, slot_points=int(pool_n.max()), max_segments=1, share_sms=False, params=sp)
@@ -857,8 +857,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="indoor-1m")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-slots", type=int, default=3,
-                    help="co-resident serving slots (measured on GB300: 3 beat 1, 2 and 4)")
+    ap.add_argument("--serve-slots", type=int, default=2,
+                    help="co-resident serving slots (GB300 sweep at 800 requests: 2 slots of 4x the largest "
+                         "scene 3.08x the plain path, 3 of 2x 3.02x, larger slots slower)")
     ap.add_argument("--no-search-compare", action="store_true",
                     help="skip timing the guided search start beside the default one")
     ap.add_argument("--search", choices=["bisect", "guided"], default="bisect",
@@ -866,6 +867,8 @@ def main():
                          "guided by the cloud's previous search")
     ap.add_argument("--no-sub-workloads", action="store_true",
                     help="default workload only: skip the batch64 and serving objects of the line")
+    ap.add_argument("--serve-slot-scale", type=int, default=4,
+                    help="points a serving slot holds, in units of the largest scene of the pool")
     ap.add_argument("--serve-requests", type=int, default=800,
                     help="requests of the serving object in the default line")
     ap.add_argument("--tuning-cache", default=None,

@@ -324,7 +324,11 @@ int32_t hav_trace_get(hav_ctx* ctx, hav_stream stream, hav_layer_trace* out, int
  * HAV_FLAG_PHASE_TIMES: t_ns[k] is the device %globaltimer (ns) when phase k
  * ended, tag[k] = phase << 24 | level << 16 | layer << 8 | pass, with phase
  * 0 kernel start, 1 bbox, 2 bisection pass, 3 selection, 4 cut-off classify,
- * 5 cut-off resolve, 6 shortfall, 7 compaction count, 8 compaction scatter.
+ * 5 cut-off resolve, 6 shortfall, 7 compaction count, 8 compaction scatter,
+ * 9 / 10 Morton bucketing count / scatter.  The grid kernel records block 0's
+ * phases, and the small-level kernels that continue the call append those of
+ * their first cluster (or CTA); the timer does not change which kernel runs
+ * a level.
  * HOST buffers of max_records entries; returns the number written, or -1.
  * Records of an earlier call may follow the last valid one if this call
  * recorded fewer. */

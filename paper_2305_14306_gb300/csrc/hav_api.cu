@@ -326,11 +326,11 @@ hav_status hav_sample_batched(hav_ctx* ctx, const float* points, const int64_t* 
     } else if (any_m > 0) {
         // levels from j0 on, where every segment has at most small_points points,
         // run on thread-block clusters, or else, where every segment has at most
-        // solo_points points, on single CTAs (either search start); the phase
-        // timer and the test hooks stay with the grid kernel, and so do the
+        // solo_points points, on single CTAs (either search start, phase timer
+        // on or off); the test hooks stay with the grid kernel, and so do the
         // calls whose representatives need the grid kernel's tables.
         const bool small_ok =
-            params->flags == 0 &&
+            (params->flags & ~static_cast<uint32_t>(HAV_FLAG_PHASE_TIMES)) == 0 &&
             (params->select == HAV_SELECT_CENTRE_CLOSEST || params->select == HAV_SELECT_RANDOM);
         // grid kernel for [0, j0), clusters for [j0, j1), single CTAs for [j1, L).
         // A level goes to single CTAs when it also has more segments than

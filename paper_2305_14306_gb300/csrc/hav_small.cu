@@ -40,6 +40,8 @@ namespace {
 constexpr int kST = 1024;         // threads per CTA
 constexpr int kPtsPerCta = 4096;  // level points one CTA holds
 constexpr int kPartMax = 2 * kPtsPerCta;  // table slots per CTA at most
+constexpr int kPartMaxLog2 = 13;
+static_assert(kPartMax == 1 << kPartMaxLog2, "kPartMaxLog2");
 static_assert(kSmallMax == 8 * kPtsPerCta, "the 8-CTA cluster takes kSmallMax points");
 constexpr int kMaxQ = 16;  // largest cluster
 template <int Q>
@@ -51,9 +53,11 @@ constexpr size_t kSmallDyn = static_cast<size_t>(kPartMax) * 16 + static_cast<si
 static_assert(kHistBins == kST, "one histogram bin per thread");
 
 struct SmallSmem {
+    // pass counts, three-way rotation, and pass errors (1: range, 2: table
+    // full), same rotation: every CTA's own copy, which every CTA adds into
+    unsigned long long cnt[3];
+    unsigned perr[3];
     // CTA 0's copy is the cluster's: written by every CTA through distributed shared memory
-    unsigned long long cnt[3];  // pass counts, three-way rotation
-    unsigned perr[3];           // pass errors (1: range, 2: table full), same rotation
     unsigned long long kstar;   // occupied voxels at s*
     unsigned errbits;           // selection errors
     unsigned ncand;             // boundary-bin candidates appended
@@ -68,6 +72,11 @@ struct SmallSmem {
     int red_i[32];
     float redf[6][32];
     int flag;
+    // the search's two possible next sizes and grids (0: the count was above
+    // K_max, 1: below m_l), prepared while the cluster barrier completes
+    float nx_s[2];
+    int nx_ok[2];
+    Grid nx_g[2];
 };
 
 template <int Q>
@@ -106,6 +115,20 @@ __device__ __forceinline__ void csync(cg::cluster_group& cl) {
     }
 }
 
+// The cluster barrier in two halves (arrival releases this thread's earlier
+// writes, the wait acquires everyone's); with Q = 1 the block barrier that
+// the caller places between them stands for it.
+template <int Q>
+__device__ __forceinline__ void carrive(cg::cluster_group& cl) {
+    if constexpr (Q > 1) (void)cl.barrier_arrive();
+    (void)cl;
+}
+template <int Q>
+__device__ __forceinline__ void cwait(cg::cluster_group& cl) {
+    if constexpr (Q > 1) cl.barrier_wait();
+    (void)cl;
+}
+
 // Insert `key` into the cluster table: the slot inside the owner's part, or
 // -1 when the part is full; *fresh when this call inserted it.
 template <int Q>
@@ -131,15 +154,17 @@ __device__ __forceinline__ int dsm_insert(cg::cluster_group& cl, unsigned long l
 }
 
 // 64-bit minimum in another CTA's shared memory with compare-and-swap (the
-// operation the table inserts use): every failed attempt saw a smaller
-// value, so the loop ends after at most as many attempts as writers.  In
-// the CTA's own shared memory (Q = 1) the atomic minimum itself.
+// operation the table inserts use).  The first attempt expects the empty
+// value (v is always below it), so a slot nobody has written yet takes one
+// round trip; every failed attempt returns the slot's current value, and
+// the next one expects it, so the loop ends after at most as many attempts
+// as writers.  In the CTA's own shared memory (Q = 1) the atomic minimum.
 template <int Q>
 __device__ __forceinline__ void dsm_min(unsigned long long* p, unsigned long long v) {
-    unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(p);
     if constexpr (Q == 1) {
-        if (v < cur) atomicMin(p, v);
+        if (v < *reinterpret_cast<volatile unsigned long long*>(p)) atomicMin(p, v);
     } else {
+        unsigned long long cur = kEmptyVal;
         while (v < cur) {
             const unsigned long long prev = atomicCAS(p, cur, v);
             if (prev == cur) break;
@@ -164,6 +189,42 @@ __device__ __forceinline__ void seg_fail(SegHdr* sh, GlobalHdr* gh, int seg, int
     atomicCAS(&sh[seg].status, 0, code);
     atomicCAS(&gh->status, 0, code);
 }
+
+// Phase timer (HAV_FLAG_PHASE_TIMES): thread 0 of the first cluster's CTA 0
+// appends (time, tag) records after the grid kernel's, tag = phase << 24 |
+// level << 16 | layer << 8 | pass with the grid kernel's phase numbers.  The
+// records of a call are a prefix of the zeroed buffer, so the first free one
+// is found by bisection.
+struct SmallTimer {
+    unsigned long long* rec;
+    int cap, n;
+    __device__ void open(const Plan& P, bool on) {
+        rec = on ? P.ptimes : nullptr;
+        cap = P.ptimes_cap;
+        n = 0;
+        if (!rec) return;
+        int lo = 0, hi = cap;  // rec[2k] != 0 exactly for k < n
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (rec[2 * mid] != 0ull) lo = mid + 1;
+            else hi = mid;
+        }
+        n = lo;
+        if (n == 0) mark(0u);  // no earlier kernel in this call: the start record
+    }
+    __device__ __forceinline__ void mark(unsigned tag) {
+        if (rec && n < cap) {
+            rec[2 * n] = globaltimer();
+            rec[2 * n + 1] = tag;
+            ++n;
+        }
+    }
+    __device__ __forceinline__ void mark(int phase, int level, int layer, int pass) {
+        if (rec)
+            mark((static_cast<unsigned>(phase) << 24) | (static_cast<unsigned>(level) << 16) |
+                 (static_cast<unsigned>(layer) << 8) | static_cast<unsigned>(pass));
+    }
+};
 
 // Levels [first_level, P.L) of every segment; level first_level > 0 reads its
 // input through orig[(first_level - 1) & 1].
@@ -192,6 +253,8 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
     Cand* cand_all = reinterpret_cast<Cand*>(ws + P.lay.cand);
     const int S = P.S;
     const bool write_tr = (rank == 0 && tid == 0);
+    SmallTimer tm;
+    tm.open(P, write_tr && cluster_id == 0);
 
     for (int seg = cluster_id; seg < S; seg += nclusters) {
         // an error from earlier levels (another kernel) carries on: first m points
@@ -253,6 +316,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
             }
             if (tid == 0 && bad) atomicExch(&sm0->nonfinite, 1);
             csync<Q>(cl);
+            tm.mark(1, j, 0, 0);
             // the bracket (0, s_hi] of Section 3.3 from CTA 0's box, in every CTA
             if (tid == 0) {
                 const int nf = sm0->nonfinite;
@@ -351,23 +415,50 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                 }
                 bool pre = !guided;  // every step so far had too few voxels (plain bisection)
 
-                // Section 3.3 search, one size per pass
-                for (int t = t0; t < steps; ++t) {
-                    const float sv = next_size(lo, hi, up, first);
-                    first = 0.0f;
-                    Grid G;
-                    const bool gok = make_grid(sv, P.aspect, sm.mn, &G);
-                    for (int k = tid; k < part; k += kST) keys[k] = kEmptyKey;
-                    // slot pass_no % 3 was last read three passes ago
-                    if (rank == 0 && tid == 0) {
-                        sm.cnt[pass_no % 3] = 0ull;
-                        sm.perr[pass_no % 3] = 0u;
+                // Section 3.3 search, one size per pass.  Two key tables alternate
+                // (the value array holds keys during the search), each with up to
+                // four times the selection's slots (emptier tables, shorter probe
+                // chains): pass p inserts into table p & 1 while every CTA empties
+                // its part of the other, whose inserts ended at the previous
+                // pass's barrier.  Every CTA adds its totals into every CTA's copy
+                // of the pass's count slot, so each reads the count locally; the
+                // slots rotate over three, and slot (p + 1) % 3, emptied during
+                // pass p, was last read right after the barrier of pass p - 2.
+                // The barrier is split: between its arrival and its wait two
+                // threads prepare the grids of both possible next sizes.
+                int pass_log2 = part_log2 + 2;
+                if (pass_log2 > kPartMaxLog2) pass_log2 = kPartMaxLog2;
+                const int pass_part = 1 << pass_log2;
+                unsigned long long* const tabs[2] = {keys, vals};
+                float sv = 0.0f;
+                Grid Gp;
+                bool gok = false;
+                if (t0 < steps) {
+                    for (int k = tid; k < pass_part; k += kST) {
+                        keys[k] = kEmptyKey;
+                        vals[k] = kEmptyKey;
+                    }
+                    if (tid < 3) {
+                        sm.cnt[tid] = 0ull;
+                        sm.perr[tid] = 0u;
                     }
                     if (tid == 0) {
                         sm.acc_cnt = 0u;
                         sm.acc_err = 0u;
                     }
+                    sv = next_size(lo, hi, up, first);
+                    first = 0.0f;
+                    gok = make_grid(sv, P.aspect, sm.mn, &Gp);
                     csync<Q>(cl);
+                }
+                for (int t = t0; t < steps; ++t) {
+                    unsigned long long* const tab = tabs[pass_no & 1];
+                    unsigned long long* const other = tabs[(pass_no + 1) & 1];
+                    for (int k = tid; k < pass_part; k += kST) other[k] = kEmptyKey;
+                    if (tid == 0) {
+                        sm.cnt[(pass_no + 1) % 3] = 0ull;
+                        sm.perr[(pass_no + 1) % 3] = 0u;
+                    }
                     unsigned local = 0;
                     unsigned ebits = gok ? 0u : 1u;
                     if (gok) {
@@ -377,24 +468,41 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                             const float p3[3] = {q.x, q.y, q.z};
                             unsigned long long key;
                             float f[3];
-                            if (!cell_key(p3, G, &key, f)) {
+                            if (!cell_key(p3, Gp, &key, f)) {
                                 ebits |= 1u;
                                 continue;
                             }
                             int owner;
                             bool fr;
-                            if (dsm_insert<Q>(cl, keys, part_log2, key, &owner, &fr) < 0) ebits |= 2u;
+                            if (dsm_insert<Q>(cl, tab, pass_log2, key, &owner, &fr) < 0) ebits |= 2u;
                             else if (fr) ++local;
                         }
                     }
                     block_count(local, ebits, &sm.acc_cnt, &sm.acc_err);
-                    if (tid == 0) {
-                        if (sm.acc_cnt) atomicAdd(&sm0->cnt[pass_no % 3], static_cast<unsigned long long>(sm.acc_cnt));
-                        if (sm.acc_err) atomicOr(&sm0->perr[pass_no % 3], sm.acc_err);
+                    if (tid < 32) {  // this CTA's totals into every CTA's copy; emptied for the next pass
+                        const unsigned c = sm.acc_cnt, e = sm.acc_err;
+                        __syncwarp();
+                        if (tid == 0) {
+                            sm.acc_cnt = 0u;
+                            sm.acc_err = 0u;
+                        }
+                        if (tid < Q) {
+                            if (c) atomicAdd(at_rank<Q>(cl, &sm.cnt[pass_no % 3], tid), static_cast<unsigned long long>(c));
+                            if (e) atomicOr(at_rank<Q>(cl, &sm.perr[pass_no % 3], tid), e);
+                        }
                     }
-                    csync<Q>(cl);
-                    const long long K = static_cast<long long>(sm0->cnt[pass_no % 3]);
-                    const unsigned eb = sm0->perr[pass_no % 3];
+                    carrive<Q>(cl);
+                    if (tid == 0 || tid == 32) {
+                        const int w = tid >> 5;
+                        const float nsv = (w == 0) ? next_size(sv, hi, up, 0.0f) : next_size(lo, sv, false, 0.0f);
+                        sm.nx_s[w] = nsv;
+                        sm.nx_ok[w] = make_grid(nsv, P.aspect, sm.mn, &sm.nx_g[w]) ? 1 : 0;
+                    }
+                    __syncthreads();
+                    cwait<Q>(cl);
+                    tm.mark(2, j, l, t);
+                    const long long K = static_cast<long long>(sm.cnt[pass_no % 3]);
+                    const unsigned eb = sm.perr[pass_no % 3];
                     ++pass_no;
                     if (write_tr) {
                         tr->s[t] = sv;
@@ -410,11 +518,17 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                         if (write_tr) seg_fail(sh, gh, seg, err);
                         break;
                     }
-                    if (K > kmax) {
+                    if (K > kmax) {  // the next pass takes the grid prepared for this outcome
                         lo = sv;
+                        sv = sm.nx_s[0];
+                        gok = sm.nx_ok[0] != 0;
+                        Gp = sm.nx_g[0];
                     } else if (K < ml) {
                         hi = sv;
                         up = false;
+                        sv = sm.nx_s[1];
+                        gok = sm.nx_ok[1] != 0;
+                        Gp = sm.nx_g[1];
                     } else {
                         s_star = sv;
                         accepted = true;
@@ -491,6 +605,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                     }
                 }
                 csync<Q>(cl);
+                tm.mark(3, j, l, 0);
                 const long long kstar = static_cast<long long>(sm0->kstar);
                 {
                     const unsigned eb = sm0->errbits;
@@ -544,6 +659,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                     }
                 }
                 csync<Q>(cl);
+                tm.mark(4, j, l, 0);
                 if (cut) {
                     // the boundary bin's candidates ranked exactly; the r smallest priorities are taken
                     const int c = static_cast<int>(sm0->ncand);
@@ -559,6 +675,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                         }
                     }
                     csync<Q>(cl);
+                    tm.mark(5, j, l, 0);
                 } else if (kstar < ml) {
                     // shortfall: untaken points in ascending level index until m_l
                     int cnt = 0;
@@ -579,6 +696,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                         budget -= chunk;
                     }
                     csync<Q>(cl);
+                    tm.mark(6, j, l, 0);
                 }
             }
 
@@ -591,6 +709,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                 block_excl_scan<int>(cnt, &tot, sm.red_i);
                 if (tid == 0) sm0->part_cnt[rank] = tot;
                 csync<Q>(cl);
+                tm.mark(7, j, 0, 0);
                 long long pos = obase;
                 for (int r2 = 0; r2 < rank; ++r2) pos += sm0->part_cnt[r2];
                 int32_t* out = P.out[j];
@@ -613,6 +732,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                     pos += chunk;
                 }
                 csync<Q>(cl);  // the next level reads orig_out; part_cnt is reused
+                tm.mark(8, j, 0, 0);
             }
         }
         if (write_tr) {  // for a single-CTA launch that continues the chain

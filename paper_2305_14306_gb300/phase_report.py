@@ -1,9 +1,11 @@
 """Per-phase device time of one sampler call, from the kernel's phase timer.
 
-With HAV_FLAG_PHASE_TIMES, block 0 of the persistent kernel records a device
-timestamp after every grid-wide phase (bounding box, Morton bucketing, each
-bisection pass, selection, classification, cut-off resolution, shortfall
-fill, compaction).  This tool runs a workload a few times and prints the
+With HAV_FLAG_PHASE_TIMES, block 0 of the persistent grid kernel records a
+device timestamp after every grid-wide phase (bounding box, Morton
+bucketing, each bisection pass, selection, classification, cut-off
+resolution, shortfall fill, compaction), and the first cluster of the
+small-level kernel that continues the chain appends its own after every
+cluster-wide phase.  This tool runs a workload a few times and prints the
 median time per phase and level, and the bisection passes per level.
 
     python -m paper_2305_14306_gb300.phase_report [--workload indoor-1m] [--runs 20]

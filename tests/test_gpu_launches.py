@@ -52,9 +52,9 @@ def test_level_chains_launch_one_kernel_per_engine(hv):
         assert launched(ctx, lambda: hv.hav_sample(ctx, mid, 700, p)) == 1
         tiny = dev(scenes.uniform_box(800, seed=3))
         assert launched(ctx, lambda: hv.hav_sample(ctx, tiny, 200, p)) == 1
-        # the phase timer keeps every level on the grid kernel
+        # the phase timer does not change which kernel runs a level
         pt = hv.params(flags=hv.HAV_FLAG_PHASE_TIMES)
-        assert launched(ctx, lambda: hv.hav_sample_levels(ctx, big, [25_000, 4_000, 1_000, 250], pt)) == 1
+        assert launched(ctx, lambda: hv.hav_sample_levels(ctx, big, [25_000, 4_000, 1_000, 250], pt)) == 3
         # nothing to select: nothing launched
         assert launched(ctx, lambda: hv.hav_sample(ctx, big, 0, p)) == 0
         st, _ = hv.hav_status_get(ctx, 1)
@@ -81,3 +81,42 @@ def test_other_calls_count_their_kernels(hv):
         assert st == hv.HAV_OK
     finally:
         ctx.close()
+
+
+def test_phase_timer_spans_every_kernel_of_a_chain(hv):
+    """The grid kernel's records, then those of the cluster and single-CTA
+    kernels that continue the chain: one start record, times in order, one
+    record per evaluated bisection step on the small levels (the trace's
+    steps less those settled by bounds), the bbox, selection and compaction
+    records of each small level, and the same indices as without the timer."""
+    ctx = hv.Context(1 << 17, 1)
+    try:
+        big = dev(scenes.uniform_box(100_000, seed=1))
+        ml = [25_000, 4_000, 1_000, 250]
+        ref = [o.cpu().numpy() for o in hv.hav_sample_levels(ctx, big, ml, hv.params())]
+        pt = hv.params(flags=hv.HAV_FLAG_PHASE_TIMES)
+        k0 = ctx.launches()
+        out = [o.cpu().numpy() for o in hv.hav_sample_levels(ctx, big, ml, pt)]
+        assert ctx.launches() - k0 == 3
+        assert all(np.array_equal(a, b) for a, b in zip(out, ref))
+        rec = hv.hav_phase_times_get(ctx)
+        trace = hv.hav_trace_get(ctx, len(ml) * 2)
+        st, _ = hv.hav_status_get(ctx, 1)
+        assert st == hv.HAV_OK
+    finally:
+        ctx.close()
+    assert rec[0][1] == 0 and sum(1 for _, g in rec if g == 0) == 1
+    times = [t for t, _ in rec]
+    assert times == sorted(times)
+    tags = [((g >> 24), (g >> 16) & 255, (g >> 8) & 255) for _, g in rec]
+    assert any(ph == 2 and lv == 0 for ph, lv, _ in tags)  # the grid kernel's passes come first
+    first_small = next(k for k, (ph, lv, _) in enumerate(tags) if lv == 1)
+    assert all(lv == 0 for _, lv, _ in tags[1:first_small])
+    for j in (1, 2, 3):  # levels of at most 32,768 points: the small-level kernels
+        for ph in (1, 3, 7, 8):  # bbox, and per layer selection; compaction count and write
+            want = 2 if ph == 3 else 1
+            assert sum(1 for p2, lv, _ in tags if p2 == ph and lv == j) == want, (j, ph)
+        for l in range(2):
+            tr = trace[j * 2 + l]
+            steps = tr["iters"] - bin(tr["bounded"]).count("1")
+            assert sum(1 for ph, lv, ly in tags if ph == 2 and lv == j and ly == l) == steps

@@ -27,6 +27,23 @@ def test_take_batch_is_first_come_first_served_within_the_limits():
     assert [r.rid for r in w] == [3]
 
 
+def test_large_clouds_are_served_alone_in_arrival_order():
+    w = collections.deque([_req(0, 10), _req(1, 20), _req(2, 500), _req(3, 30), _req(4, 600), _req(5, 5)])
+    take = lambda: [r.rid for r in serving.take_batch(w, max_segments=8, slot_points=1000, solo_points=400)]
+    assert take() == [0, 1]  # a large cloud ends the batch of small ones before it
+    assert take() == [2]     # and is a call of its own when it is first in line
+    assert take() == [3]
+    assert take() == [4]
+    assert take() == [5]
+    assert take() == [] and not w
+    # a large cloud the slot cannot hold is not taken (the server rejects it up front)
+    w = collections.deque([_req(0, 2000)])
+    assert serving.take_batch(w, max_segments=8, slot_points=1000, solo_points=400) == [] and len(w) == 1
+    # without solo_points the same queue packs as before
+    w = collections.deque([_req(0, 10), _req(1, 20), _req(2, 500), _req(3, 30)])
+    assert [r.rid for r in serving.take_batch(w, max_segments=8, slot_points=1000)] == [0, 1, 2, 3]
+
+
 def test_expired_requests_are_dropped_before_launch():
     w = collections.deque([_req(0, 10, 0.0, deadline=0.5), _req(1, 10, 0.2), _req(2, 10, 0.4, deadline=0.5),
                            _req(3, 10, 0.1, deadline=0.95)])

@@ -158,7 +158,7 @@ inline Layout make_layout(int64_t N, int32_t S, bool spec_room = true, int table
     for (int b = 0; b < kTableSets; ++b) L.dirty[b] = take(sizeof(uint32_t) * L.dirty_slots + 16);
     L.wpre = take(sizeof(uint32_t) * L.taken_words);
     L.posof = take(sizeof(int32_t) * N + 16);
-    L.bkt = take(sizeof(uint32_t) * 2 * 4096);
+    L.bkt = take(sizeof(uint32_t) * 2 * 4096 * static_cast<size_t>(S));  // counts and cursors per segment
     L.prefix = take(sizeof(int32_t) * HAV_MAX_ITERS * S);
     for (int b = 0; b < kTableSets; ++b) L.tabk[b] = take(sizeof(unsigned long long) * L.tab_slots);
     L.tabv = take(sizeof(unsigned long long) * L.tab_slots);

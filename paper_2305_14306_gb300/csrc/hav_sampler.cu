@@ -486,7 +486,12 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
         const int32_t* orig_in = (j == 0) ? nullptr : d.orig[(j - 1) & 1];
         uint32_t* taken = d.taken[j & 1];
         const long long NL = st.n_level;
-        const bool bucketing = (j == 0 && S == 1 && NL >= kBucketMin);
+        // level 0: every segment of at least kBucketMin points is sorted by
+        // Morton cell (one cloud: the whole level; a batch: each such segment
+        // within its own range)
+        bool bucketing = false;
+        if (j == 0)
+            for (int s2 = 0; s2 < S; ++s2) bucketing = bucketing || st.n[s2] >= kBucketMin;
 
         // ------------------------------------------------ bbox, layout, clears
         // (a later level's box, masks and states were prepared by the previous
@@ -505,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         p[0] = q[0];
                         p[1] = q[1];
                         p[2] = q[2];
-                        if (!bucketing) {
+                        if (st.n[s] < kBucketMin) {  // (a bucketed segment is placed by its scatter)
                             ord[i] = make_float4(p[0], p[1], p[2], __int_as_float(static_cast<int>(i)));
                             d.posof[i] = static_cast<int32_t>(i);
                         }
@@ -561,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     fill<unsigned long long>(d.tk[b], P.lay.tab_slots, kEmptyKey, gtid, gstride);
                 fill<unsigned long long>(d.tv, P.lay.tab_slots, kEmptyVal, gtid, gstride);
             }
-            if (bucketing) fill<uint32_t>(d.bkt, 2 * 4096, 0u, gtid, gstride);
+            if (bucketing) fill<uint32_t>(d.bkt, 2 * 4096ll * S, 0u, gtid, gstride);
             // (test hook: one arrival more than the launch has blocks never comes,
             // so every block's bounded wait gives up and the call reports a timeout)
             if (!grid_sync(d, nb + ((j == 0 && P.test_timeout) ? 1u : 0u), st, TAG(1, j, 0, 0))) return;
@@ -623,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
         __syncthreads();
 
         // ---------------------------------------- bucketing (one large cloud)
-        if (bucketing) {
+        if (bucketing && S == 1) {
             if (tid == 0) st.set_clean = 0;
             uint32_t* h = reinterpret_cast<uint32_t*>(dyn);          // this block's counts
             uint32_t* hb = reinterpret_cast<uint32_t*>(dyn) + 4096;  // global bucket bases
@@ -711,6 +716,93 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         }
                     }
                 }
+            }
+            if (!grid_sync(d, nb, st, TAG(10, j, 0, 0))) return;
+        } else if (bucketing) {
+            // ------------------------------- bucketing (large clouds of a batch)
+            // The same counting sort per segment of at least kBucketMin points,
+            // within the segment's range: counts [S][4096] and cursors [S][4096]
+            // in the workspace.  A block's items may belong to several
+            // segments: the counts are gathered per run of items of one
+            // segment, and every item counts its points again before it takes
+            // its places.  The other segments keep their order (bbox phase).
+            if (tid == 0) st.set_clean = 0;
+            uint32_t* h = reinterpret_cast<uint32_t*>(dyn);          // counts of one segment's items
+            uint32_t* hb = reinterpret_cast<uint32_t*>(dyn) + 4096;  // bases of one segment's buckets
+            uint32_t* bcnt = d.bkt;
+            uint32_t* bcur = d.bkt + 4096ll * S;
+            int hs = -1;  // the segment whose counts h holds
+            for (int b = tid; b < 4096; b += kThreads) h[b] = 0u;
+            __syncthreads();
+            for (int it = blockIdx.x; it < st.items_total; it += nb) {  // (block-uniform)
+                int a, b;
+                const int s = item_range(st, S, it, &a, &b);
+                if (st.n[s] < kBucketMin) continue;
+                if (hs >= 0 && hs != s) {
+                    for (int k = tid; k < 4096; k += kThreads)
+                        if (h[k]) {
+                            atomicAdd(&bcnt[4096ll * hs + k], h[k]);
+                            h[k] = 0u;
+                        }
+                    __syncthreads();
+                }
+                hs = s;
+                for (int i = a + tid; i < b; i += kThreads) {
+                    const float* q = P.points + 3 * i;
+                    const float p3[3] = {q[0], q[1], q[2]};
+                    atomicAdd(&h[bucket_of(p3, st.mn[s], st.mx[s])], 1u);
+                }
+                __syncthreads();
+            }
+            if (hs >= 0)
+                for (int k = tid; k < 4096; k += kThreads)
+                    if (h[k]) atomicAdd(&bcnt[4096ll * hs + k], h[k]);
+            if (!grid_sync(d, nb, st, TAG(9, j, 0, 0))) return;
+            int bs = -1;  // the segment whose bases hb holds
+            for (int it = blockIdx.x; it < st.items_total; it += nb) {  // (block-uniform)
+                int a, b;
+                const int s = item_range(st, S, it, &a, &b);
+                if (st.n[s] < kBucketMin) continue;
+                if (bs != s) {
+                    // exclusive prefix of the segment's 4096 counts, from its first position
+                    constexpr int kPerT = 4096 / kThreads;
+                    uint32_t c4[kPerT], sum = 0;
+#pragma unroll
+                    for (int k = 0; k < kPerT; ++k) {
+                        c4[k] = bcnt[4096ll * s + kPerT * tid + k];
+                        sum += c4[k];
+                    }
+                    unsigned tot;
+                    unsigned before = static_cast<unsigned>(st.off[s]) + block_excl_scan<unsigned>(sum, &tot, st.scan_u);
+#pragma unroll
+                    for (int k = 0; k < kPerT; ++k) {
+                        hb[kPerT * tid + k] = before;
+                        before += c4[k];
+                    }
+                    bs = s;
+                }
+                for (int k = tid; k < 4096; k += kThreads) h[k] = 0u;
+                __syncthreads();
+                for (int i = a + tid; i < b; i += kThreads) {
+                    const float* q = P.points + 3 * i;
+                    const float p3[3] = {q[0], q[1], q[2]};
+                    atomicAdd(&h[bucket_of(p3, st.mn[s], st.mx[s])], 1u);
+                }
+                __syncthreads();
+                for (int k = tid; k < 4096; k += kThreads)
+                    if (h[k]) h[k] = hb[k] + atomicAdd(&bcur[4096ll * s + k], h[k]);
+                __syncthreads();
+                const unsigned end = static_cast<unsigned>(st.off[s + 1]);
+                for (int i = a + tid; i < b; i += kThreads) {
+                    const float* q = P.points + 3 * i;
+                    const float p3[3] = {q[0], q[1], q[2]};
+                    const unsigned r = atomicAdd(&h[bucket_of(p3, st.mn[s], st.mx[s])], 1u);
+                    if (r < end) {
+                        ord[r] = make_float4(p3[0], p3[1], p3[2], __int_as_float(static_cast<int>(i)));
+                        d.posof[i] = static_cast<int32_t>(r);
+                    }
+                }
+                __syncthreads();
             }
             if (!grid_sync(d, nb, st, TAG(10, j, 0, 0))) return;
         }

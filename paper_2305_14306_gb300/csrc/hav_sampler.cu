@@ -116,13 +116,15 @@ struct Smem {
     unsigned epoch;
     unsigned list_n;
     int set_clean;  // 1 when every slot of the block set is empty
-    // a bucketed cloud (level 0 and the levels that keep its order): the
-    // Morton cells [own_lo, own_hi] of the level-0 bucketing (its box own_mn,
-    // own_mx, own_k[a] = 16 / extent) whose points all lie in this block's work
-    // item (own_on), and per pass the keys that go to the global table
-    // (rest_n) and the owned ones counted here
-    int own_on, own_lo, own_hi, bucketed;
-    float own_k[3], own_mn[3], own_mx[3];
+    // a bucketed segment (level 0, and for one cloud the levels that keep its
+    // order): per work item of the block, the Morton cells [own_lo, own_hi]
+    // of the level-0 bucketing (its box own_mn, own_k[a] = 16 / extent) whose
+    // points all lie in the item (own_on); per pass the keys that go to the
+    // global table (rest_n) and the owned ones counted here.  b0_*: one
+    // bucketed cloud's level-0 box, kept for its later levels.
+    int own_on[kLocalItems], own_lo[kLocalItems], own_hi[kLocalItems], bucketed;
+    float own_k[kLocalItems][3], own_mn[kLocalItems][3];
+    float b0_mn[3], b0_mx[3], b0_k[3];
     unsigned rest_n;
     unsigned xcnt[kMaxCand];
     int ocnt[kLocalItems];  // owned voxels the selection listed for the classification, per item
@@ -297,9 +299,9 @@ __device__ __forceinline__ unsigned bucket_of(const float p[3], const float mn[3
 }
 
 // Whether every point of the voxel `key` (Eq. 2 cell of grid g) lies in Morton
-// cells [own_lo, own_hi] of the bucketing, all of whose points this block
-// processes: then no other block has a point in the voxel, and the block
-// counts it without the global table.  The test may answer no for an owned
+// cells [own_lo, own_hi] of its segment's bucketing, all of whose points one
+// work item of this block processes: then no other item has a point in the
+// voxel, and the item counts it without the global table.  The test may answer no for an owned
 // voxel (the key then goes to the global table), never yes for another one.
 // A point x of the voxel along an axis has f <= RN(x / v) < f + 1, so
 // v (f - ulp(f) / 2) <= x < v (f + 1); the box [v f, v (f + 1)] is widened by
@@ -331,6 +333,35 @@ __device__ __forceinline__ bool voxel_owned(unsigned long long key, const Grid& 
     }
     return static_cast<int>(morton16(c0[0], c0[1], c0[2])) >= own_lo &&
            static_cast<int>(morton16(c1[0], c1[1], c1[2])) <= own_hi;
+}
+
+// The Morton cells a work item [ia, ib) of a bucketed segment holds whole,
+// from the bucket bases hb (position of each cell's first point; the
+// segment's points end at `end`): from the first cell starting at or after
+// ia to the last one ending at or before ib.  Stored as item li's owned
+// range with the bucketing's box mn and k = RN(16 / extent).
+__device__ void own_cells(const uint32_t* hb, int ia, int ib, unsigned end, const float mn[3], const float k[3],
+                          Smem& st, int li) {
+    int lo = 0, hi = 4096;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (hb[mid] >= static_cast<unsigned>(ia)) hi = mid; else lo = mid + 1;
+    }
+    const int c_lo = lo;
+    lo = 0;
+    hi = 4096;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const unsigned e = (mid + 1 < 4096) ? hb[mid + 1] : end;
+        if (e > static_cast<unsigned>(ib)) hi = mid; else lo = mid + 1;
+    }
+    st.own_lo[li] = c_lo;
+    st.own_hi[li] = lo - 1;
+    st.own_on[li] = (c_lo <= lo - 1) ? 1 : 0;
+    for (int a3 = 0; a3 < 3; ++a3) {
+        st.own_mn[li][a3] = mn[a3];
+        st.own_k[li][a3] = k[a3];
+    }
 }
 
 // Level layout of every segment, computed identically by every block.
@@ -482,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
 
     for (int j = 0; j < P.L; ++j) {
         level_setup(P, j, st);
-        if (tid == 0) st.own_on = 0;
+        if (tid < kLocalItems) st.own_on[tid] = 0;
         float4* ord = d.ord[j & 1];
         const int32_t* orig_in = (j == 0) ? nullptr : d.orig[(j - 1) & 1];
         uint32_t* taken = d.taken[j & 1];
@@ -608,22 +639,27 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
         // block's item holds whole run from the first cell starting in it to
         // the last cell ending in it, read off the cells of the points at and
         // beside the item's two ends.
-        if (j > 0 && st.bucketed && S == 1 && tid == 0 && st.items_total <= static_cast<int>(nb) &&
-            static_cast<int>(blockIdx.x) < st.items_total) {
+        if (j > 0 && st.bucketed && S == 1 && tid < kLocalItems &&
+            static_cast<long long>(blockIdx.x) + static_cast<long long>(tid) * nb < st.items_total) {
+            const int li = tid;  // one thread per item of the block
             int ia, ib;
-            item_range(st, S, blockIdx.x, &ia, &ib);
+            item_range(st, S, static_cast<int>(blockIdx.x + tid * nb), &ia, &ib);
             auto cell = [&](int i) {
                 const float4 q = ord[i];
                 const float p3[3] = {q.x, q.y, q.z};
-                return static_cast<int>(bucket_of(p3, st.own_mn, st.own_mx));
+                return static_cast<int>(bucket_of(p3, st.b0_mn, st.b0_mx));
             };
             if (ib > ia) {
                 const int cf = cell(ia), cl = cell(ib - 1);
                 const int lo = (ia == 0 || cell(ia - 1) < cf) ? cf : cf + 1;
                 const int hi = (ib == NL || cell(ib) > cl) ? cl : cl - 1;
-                st.own_lo = lo;
-                st.own_hi = hi;
-                st.own_on = (lo <= hi) ? 1 : 0;
+                st.own_lo[li] = lo;
+                st.own_hi[li] = hi;
+                st.own_on[li] = (lo <= hi) ? 1 : 0;
+                for (int a3 = 0; a3 < 3; ++a3) {
+                    st.own_mn[li][a3] = st.b0_mn[a3];
+                    st.own_k[li][a3] = st.b0_k[a3];
+                }
             }
         }
         __syncthreads();
@@ -666,40 +702,25 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     before += c4[k];
                 }
                 __syncthreads();
-                // the Morton cells this block's work item holds whole: from the
-                // first cell starting at or after the item's start to the last
-                // one ending at or before its end (cells are laid out in Morton
-                // order; the item is the same in every pass of this level)
-                if (tid == 0 && st.items_total <= static_cast<int>(nb) &&
-                    static_cast<int>(blockIdx.x) < st.items_total) {
-                    int ia, ib;
-                    item_range(st, S, blockIdx.x, &ia, &ib);
-                    int lo = 0, hi = 4096;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (hb[mid] >= static_cast<unsigned>(ia)) hi = mid; else lo = mid + 1;
-                    }
-                    const int c_lo = lo;
-                    lo = 0;
-                    hi = 4096;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        const unsigned end = (mid + 1 < 4096) ? hb[mid + 1] : static_cast<unsigned>(NL);
-                        if (end > static_cast<unsigned>(ib)) hi = mid; else lo = mid + 1;
-                    }
-                    st.own_lo = c_lo;
-                    st.own_hi = lo - 1;
-                    st.own_on = (c_lo <= lo - 1) ? 1 : 0;
-                }
+                // the Morton cells each of this block's work items holds whole
+                // (one thread per item; the items are the same in every pass of
+                // this level), and the bucketing's box, kept for the levels
+                // that inherit its order
                 if (tid == 0) {
-                    // the bucketing's box, kept for the levels that inherit its order
                     st.bucketed = 1;
                     for (int a3 = 0; a3 < 3; ++a3) {
-                        st.own_mn[a3] = st.mn[0][a3];
-                        st.own_mx[a3] = st.mx[0][a3];
+                        st.b0_mn[a3] = st.mn[0][a3];
+                        st.b0_mx[a3] = st.mx[0][a3];
                         const float e = __fsub_rn(st.mx[0][a3], st.mn[0][a3]);
-                        st.own_k[a3] = (e > 0.0f) ? __fdiv_rn(16.0f, e) : 0.0f;
+                        st.b0_k[a3] = (e > 0.0f) ? __fdiv_rn(16.0f, e) : 0.0f;
                     }
+                }
+                __syncthreads();
+                if (tid < kLocalItems &&
+                    static_cast<long long>(blockIdx.x) + static_cast<long long>(tid) * nb < st.items_total) {
+                    int ia, ib;
+                    item_range(st, S, static_cast<int>(blockIdx.x + tid * nb), &ia, &ib);
+                    own_cells(hb, ia, ib, static_cast<unsigned>(NL), st.b0_mn, st.b0_k, st, tid);
                 }
                 for (int b = tid; b < 4096; b += kThreads)
                     if (h[b]) h[b] = hb[b] + atomicAdd(&d.bkt[4096 + b], h[b]);
@@ -799,6 +820,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 int a, b;
                 const int s = item_range(st, S, it, &a, &b);
                 if (!st.bseg[s]) continue;
+                const int li = static_cast<int>((it - static_cast<int>(blockIdx.x)) / static_cast<int>(nb));
                 if (bs != s) {
                     // exclusive prefix of the segment's 4096 counts, from its first position
                     constexpr int kPerT = 4096 / kThreads;
@@ -819,6 +841,14 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                 }
                 for (int k = tid; k < 4096; k += kThreads) h[k] = 0u;
                 __syncthreads();
+                if (tid == 0) {  // the cells this item holds whole, in its segment's box
+                    float k3[3];
+                    for (int a3 = 0; a3 < 3; ++a3) {
+                        const float e = __fsub_rn(st.mx[s][a3], st.mn[s][a3]);
+                        k3[a3] = (e > 0.0f) ? __fdiv_rn(16.0f, e) : 0.0f;
+                    }
+                    own_cells(hb, a, b, static_cast<unsigned>(st.off[s + 1]), st.mn[s], k3, st, li);
+                }
                 for (int i = a + tid; i < b; i += kThreads) {
                     const float* q = P.points + 3 * i;
                     const float p3[3] = {q[0], q[1], q[2]};
@@ -1074,7 +1104,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     const unsigned short* gl = list;
                     int ng = nl;
                     // (below 256 listed keys the test costs about what it saves)
-                    if (st.own_on && nl >= 256 && nl <= kSetSlots / 2) {
+                    if (st.own_on[li] && nl >= 256 && nl <= kSetSlots / 2) {
                         unsigned short* rest = list + kSetSlots / 2;
                         unsigned mine = 0;  // owned keys of this thread (one candidate)
                         for (int k0 = tid - lane; k0 < nl; k0 += kThreads) {  // warp-uniform
@@ -1084,8 +1114,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             if (k < nl) {
                                 const int idx = list[k];
                                 c = idx >> setc_log2;
-                                glob = !voxel_owned(set[idx], st.cgrid[li][c], st.own_mn, st.own_k, st.own_lo,
-                                                    st.own_hi);
+                                glob = !voxel_owned(set[idx], st.cgrid[li][c], st.own_mn[li], st.own_k[li],
+                                                    st.own_lo[li], st.own_hi[li]);
                             }
                             const int pos = warp_append(glob, &st.rest_n);
                             if (pos >= 0) rest[pos] = list[k];
@@ -1300,7 +1330,7 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     // representative in the block's own minimum; it skips the global
                     // table and is listed for the classification (in the next level's
                     // staged-point array, not written before this level's compaction)
-                    const bool owning = st.own_on != 0;
+                    const bool owning = st.own_on[li] != 0;
                     Cand* olist = reinterpret_cast<Cand*>(d.ord[(j + 1) & 1]) + a;
                     const int sel = st.sel[s];
                     const int sc = st.sel_cand[s];
@@ -1379,7 +1409,8 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                             const int si = (k < nl) ? static_cast<int>(list[k]) : 0;
                             const unsigned long long key = (k < nl) ? skey[si] : kEmptyKey;
                             const bool own = key != kEmptyKey &&
-                                             voxel_owned(key, G, st.own_mn, st.own_k, st.own_lo, st.own_hi);
+                                             voxel_owned(key, G, st.own_mn[li], st.own_k[li], st.own_lo[li],
+                                                         st.own_hi[li]);
                             const int opos = warp_append(own, &st.rest_n);
                             if (opos >= 0) {
                                 const unsigned long long h = priority(key);

@@ -244,6 +244,31 @@ def test_batched_mixed_segments(hv, ctx):
     check_batched(hv, ctx, clouds, [m1, m2])
 
 
+@pytest.mark.parametrize("knobs", [{}, {"nblocks": 17}])
+def test_batched_bucketed_segments_on_cell_boundaries(hv, ctx, knobs):
+    # large shuffled segments of a batch are sorted by Morton cell and counted
+    # with the ownership test item by item: two lattices whose planes lie on
+    # their 16^3 cell faces (boxes [0, 16] and [-8, 8]), a shuffled room, and
+    # between them a scan-ordered LiDAR cloud and small clouds that keep their
+    # order; 17 blocks give each block several items
+    g = np.arange(65, dtype=np.float32) * np.float32(0.25)
+    zz = np.arange(33, dtype=np.float32) * np.float32(0.5)
+    x, y, z = np.meshgrid(g, g, zz, indexing="ij")
+    lat = np.stack([x.ravel(), y.ravel(), z.ravel()], 1).astype(np.float32)
+    lat = np.concatenate([lat, lat[::7]])
+    rng = np.random.default_rng(5)
+    clouds = [lat[rng.permutation(lat.shape[0])], scenes.uniform_box(3000, 1),
+              scenes.lidar_exact(140000, 2), lat[rng.permutation(lat.shape[0])] - np.float32(8.0),
+              scenes.room_scene(150000, 3), scenes.uniform_box(20000, 4)]
+    sizes = [c.shape[0] for c in clouds]
+    old = ctx.get_tuning()
+    try:
+        ctx.set_tuning(**knobs)
+        check_batched(hv, ctx, clouds, [[n // 4 for n in sizes], [n // 16 for n in sizes]])
+    finally:
+        ctx.set_tuning(**old)
+
+
 def test_batched_error_is_contained(hv, ctx):
     clouds = [scenes.uniform_box(3000, i) for i in range(4)]
     clouds[2] = clouds[2].copy()

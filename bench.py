@@ -779,12 +779,16 @@ def run_serving(args, world, rank, local, sub=False, requests=None):
         zero = np.zeros(R)
         plain.serve(make(zero[:min(R, 8)]))  # warm-up
         served.serve(make(zero[:min(R, 8)]))
-        t0 = time.perf_counter()
-        res_p = plain.serve(make(zero))
-        cap_plain = R / (time.perf_counter() - t0)
-        t0 = time.perf_counter()
-        res_s = served.serve(make(zero))
-        cap_served = R / (time.perf_counter() - t0)
+        # closed-loop capacity: the better of two runs of each path (a host
+        # hiccup in one run would otherwise move the ratio)
+        cap_plain = cap_served = 0.0
+        for _ in range(2):
+            t0 = time.perf_counter()
+            res_p = plain.serve(make(zero))
+            cap_plain = max(cap_plain, R / (time.perf_counter() - t0))
+            t0 = time.perf_counter()
+            res_s = served.serve(make(zero))
+            cap_served = max(cap_served, R / (time.perf_counter() - t0))
         same = all(np.array_equal(res_p[i].indices, res_s[i].indices) for i in range(R))
         clk = Clocks(local)
         open_loop = []

@@ -248,8 +248,8 @@ def test_batched_mixed_segments(hv, ctx):
 def test_batched_bucketed_segments_on_cell_boundaries(hv, ctx, knobs):
     # large shuffled segments of a batch are sorted by Morton cell and counted
     # with the ownership test item by item: two lattices whose planes lie on
-    # their 16^3 cell faces (boxes [0, 16] and [-8, 8]), a shuffled room, and
-    # between them a scan-ordered LiDAR cloud and small clouds that keep their
+    # their 16^3 cell faces (boxes [0, 16] and [-8, 8]), a shuffled room and a
+    # scan-ordered LiDAR cloud, and between them small clouds that keep their
     # order; 17 blocks give each block several items
     g = np.arange(65, dtype=np.float32) * np.float32(0.25)
     zz = np.arange(33, dtype=np.float32) * np.float32(0.5)

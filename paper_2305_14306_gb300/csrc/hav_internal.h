@@ -74,6 +74,11 @@ struct SegHdr {
     // and budget m_l (0: none); handed from the grid kernel to the small-level one
     float guide_s;
     int32_t guide_m;
+    // a batch segment sorted by Morton cell at level 0: that level's box (min
+    // xyz, max xyz), for the ownership test of its later levels (b0_on = 1)
+    float b0[6];
+    int32_t b0_on;
+    int32_t pad;
 };
 
 // Per segment, per layer parity: zeroed inside the kernel before use.

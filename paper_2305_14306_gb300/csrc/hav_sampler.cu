@@ -638,6 +638,39 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
         // block's item holds whole run from the first cell starting in it to
         // the last cell ending in it, read off the cells of the points at and
         // beside the item's two ends.
+        // The same for a batch's segments sorted at level 0 (their level-0
+        // boxes are in the segment headers), item by item within the segment.
+        if (j > 0 && S > 1 && tid < kLocalItems &&
+            static_cast<long long>(blockIdx.x) + static_cast<long long>(tid) * nb < st.items_total) {
+            const int li = tid;
+            int ia, ib;
+            const int s = item_range(st, S, static_cast<int>(blockIdx.x + tid * nb), &ia, &ib);
+            if (ld_volatile(&d.sh[s].b0_on) && ib > ia) {
+                float mn3[3], mx3[3], k3[3];
+                for (int a3 = 0; a3 < 3; ++a3) {
+                    mn3[a3] = d.sh[s].b0[a3];
+                    mx3[a3] = d.sh[s].b0[3 + a3];
+                    const float e = __fsub_rn(mx3[a3], mn3[a3]);
+                    k3[a3] = (e > 0.0f) ? __fdiv_rn(16.0f, e) : 0.0f;
+                }
+                auto cell = [&](int i) {
+                    const float4 q = ord[i];
+                    const float p3[3] = {q.x, q.y, q.z};
+                    return static_cast<int>(bucket_of(p3, mn3, mx3));
+                };
+                const int sa = static_cast<int>(st.off[s]), se = static_cast<int>(st.off[s + 1]);
+                const int cf = cell(ia), cl = cell(ib - 1);
+                const int lo = (ia == sa || cell(ia - 1) < cf) ? cf : cf + 1;
+                const int hi = (ib == se || cell(ib) > cl) ? cl : cl - 1;
+                st.own_lo[li] = lo;
+                st.own_hi[li] = hi;
+                st.own_on[li] = (lo <= hi) ? 1 : 0;
+                for (int a3 = 0; a3 < 3; ++a3) {
+                    st.own_mn[li][a3] = mn3[a3];
+                    st.own_k[li][a3] = k3[a3];
+                }
+            }
+        }
         if (j > 0 && st.bucketed && S == 1 && tid < kLocalItems &&
             static_cast<long long>(blockIdx.x) + static_cast<long long>(tid) * nb < st.items_total) {
             const int li = tid;  // one thread per item of the block
@@ -755,6 +788,15 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
             uint32_t* hb = reinterpret_cast<uint32_t*>(dyn) + 4096;  // bases of one segment's buckets
             uint32_t* bcnt = d.bkt;
             uint32_t* bcur = d.bkt + 4096ll * S;
+            if (blockIdx.x == 0)  // the boxes of the sorted segments, for their later levels
+                for (int s2 = tid; s2 < S; s2 += kThreads)
+                    if (st.n[s2] >= kBucketMin) {
+                        for (int a3 = 0; a3 < 3; ++a3) {
+                            d.sh[s2].b0[a3] = st.mn[s2][a3];
+                            d.sh[s2].b0[3 + a3] = st.mx[s2][a3];
+                        }
+                        d.sh[s2].b0_on = 1;
+                    }
             int hs = -1;  // the segment whose counts h holds
             for (int b = tid; b < 4096; b += kThreads) h[b] = 0u;
             __syncthreads();

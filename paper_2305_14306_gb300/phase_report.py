@@ -8,7 +8,7 @@ small-level kernel that continues the chain appends its own after every
 cluster-wide phase.  This tool runs a workload a few times and prints the
 median time per phase and level, and the bisection passes per level.
 
-    python -m paper_2305_14306_gb300.phase_report [--workload indoor-1m] [--runs 20]
+    python -m paper_2305_14306_gb300.phase_report [--workload indoor-1m|lidar-chain|uniform-16k|batch64] [--runs 20]
 
 Timestamps come from %globaltimer; the recording itself adds well under a
 microsecond per phase.
@@ -30,6 +30,8 @@ WORKLOADS = {
     "indoor-1m": (lambda: scenes.room_scene(1 << 20, seed=0), [1 << 18, 1 << 16, 1 << 14, 1 << 12]),
     "lidar-chain": (lambda: scenes.lidar_min(16384, seed=0)[0], [16384, 4096, 1024, 512]),
     "uniform-16k": (lambda: scenes.uniform_box(16384, seed=0), [4096]),
+    # 64 LiDAR clouds in one segmented call, each to N/4 then N/16
+    "batch64": (lambda: scenes.lidar_batch(64, seed=0), None),
 }
 
 
@@ -55,19 +57,35 @@ def main(argv=None):
     build.build()
     hav.load()
     make, ml = WORKLOADS[args.workload]
-    pts = make()
-    ctx = hav.Context(pts.shape[0], 1)
-    d = torch.from_numpy(np.ascontiguousarray(pts, dtype=np.float32)).cuda()
     p = hav.params(flags=hav.HAV_FLAG_PHASE_TIMES)
-    outs = [torch.empty(m, dtype=torch.int32, device="cuda") for m in ml]
+    if ml is None:  # a batch: one segmented call
+        clouds = make()
+        pts, offs = scenes.concat(clouds)
+        sizes = np.diff(offs)
+        seg_m = np.stack([sizes // 4, sizes // 16]).astype(np.int64)
+        ml = [int(x) for x in seg_m.sum(axis=1)]
+        ctx = hav.Context(pts.shape[0], len(clouds))
+        d = torch.from_numpy(np.ascontiguousarray(pts, dtype=np.float32)).cuda()
+        outs = [torch.empty(m, dtype=torch.int32, device="cuda") for m in ml]
+
+        def call():
+            hav.hav_sample_batched(ctx, d, offs, seg_m, p, outs=outs)
+    else:
+        pts = make()
+        ctx = hav.Context(pts.shape[0], 1)
+        d = torch.from_numpy(np.ascontiguousarray(pts, dtype=np.float32)).cuda()
+        outs = [torch.empty(m, dtype=torch.int32, device="cuda") for m in ml]
+
+        def call():
+            hav.hav_sample_levels(ctx, d, ml, p, outs=outs)
     for _ in range(5):
-        hav.hav_sample_levels(ctx, d, ml, p, outs=outs)
+        call()
     per = collections.defaultdict(list)
     counts = None
     totals = []
     for _ in range(args.runs):
         torch.cuda.synchronize()
-        hav.hav_sample_levels(ctx, d, ml, p, outs=outs)
+        call()
         rec = hav.hav_phase_times_get(ctx)
         dur, counts = phase_durations(rec)
         for k, v in dur.items():

@@ -126,6 +126,17 @@ __device__ inline bool make_grid(float s, const float r[3], const float mn[3], G
     return true;
 }
 
+// One axis of make_grid (its three axes may be computed by three threads;
+// the grid is valid when every axis is).
+__device__ __forceinline__ bool make_grid_axis(float s, float r, float mn, Grid* g, int a) {
+    const float v = __fmul_rn(s, r);
+    if (!(v > 0.0f) || !isfinite(v)) return false;
+    g->v[a] = v;
+    const float rv = __fdiv_rn(1.0f, v);
+    g->r[a] = (rv >= 1.17549435e-38f && rv <= 3.40282347e+38f) ? rv : 0.0f;
+    return floor_div(mn, v, &g->fmin[a]);
+}
+
 // key = u_x | u_y << 21 | u_z << 42 with u = floor(x / v) - floor(min / v).
 __device__ __forceinline__ bool cell_key(const float p[3], const Grid& g, unsigned long long* key,
                                          float f[3]) {

@@ -75,7 +75,7 @@ struct SmallSmem {
     // the search's two possible next sizes and grids (0: the count was above
     // K_max, 1: below m_l), prepared while the cluster barrier completes
     float nx_s[2];
-    int nx_ok[2];
+    int nx_ok[2][3];  // per axis
     Grid nx_g[2];
 };
 
@@ -492,11 +492,11 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                         }
                     }
                     carrive<Q>(cl);
-                    if (tid == 0 || tid == 32) {
-                        const int w = tid >> 5;
+                    if (tid < 64 && (tid & 31) < 3) {  // one axis of one outcome's grid per thread
+                        const int w = tid >> 5, ax = tid & 31;
                         const float nsv = (w == 0) ? next_size(sv, hi, up, 0.0f) : next_size(lo, sv, false, 0.0f);
-                        sm.nx_s[w] = nsv;
-                        sm.nx_ok[w] = make_grid(nsv, P.aspect, sm.mn, &sm.nx_g[w]) ? 1 : 0;
+                        if (ax == 0) sm.nx_s[w] = nsv;
+                        sm.nx_ok[w][ax] = make_grid_axis(nsv, P.aspect[ax], sm.mn[ax], &sm.nx_g[w], ax) ? 1 : 0;
                     }
                     __syncthreads();
                     cwait<Q>(cl);
@@ -521,13 +521,13 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                     if (K > kmax) {  // the next pass takes the grid prepared for this outcome
                         lo = sv;
                         sv = sm.nx_s[0];
-                        gok = sm.nx_ok[0] != 0;
+                        gok = sm.nx_ok[0][0] && sm.nx_ok[0][1] && sm.nx_ok[0][2];
                         Gp = sm.nx_g[0];
                     } else if (K < ml) {
                         hi = sv;
                         up = false;
                         sv = sm.nx_s[1];
-                        gok = sm.nx_ok[1] != 0;
+                        gok = sm.nx_ok[1][0] && sm.nx_ok[1][1] && sm.nx_ok[1][2];
                         Gp = sm.nx_g[1];
                     } else {
                         s_star = sv;

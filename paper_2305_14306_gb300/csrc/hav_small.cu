@@ -448,8 +448,14 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                     }
                     sv = next_size(lo, hi, up, first);
                     first = 0.0f;
-                    gok = make_grid(sv, P.aspect, sm.mn, &Gp);
-                    csync<Q>(cl);
+                    if constexpr (Q > 1) {  // the first grid while the barrier completes
+                        carrive<Q>(cl);
+                        gok = make_grid(sv, P.aspect, sm.mn, &Gp);
+                        cwait<Q>(cl);
+                    } else {
+                        gok = make_grid(sv, P.aspect, sm.mn, &Gp);
+                        __syncthreads();
+                    }
                 }
                 for (int t = t0; t < steps; ++t) {
                     unsigned long long* const tab = tabs[pass_no & 1];
@@ -541,8 +547,8 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                     gs = s_star;
                     gm = static_cast<int>(ml);
                 }
-                Grid G;
-                if (!make_grid(s_star, P.aspect, sm.mn, &G)) {
+                Grid G = Gp;  // an accepted s* is the last pass's size: its grid is Gp
+                if (!(accepted && gok) && !make_grid(s_star, P.aspect, sm.mn, &G)) {
                     err = HAV_ERR_RANGE;
                     if (write_tr) seg_fail(sh, gh, seg, err);
                     continue;

@@ -67,6 +67,8 @@ struct SmallSmem {
     // this CTA's
     float mn[3], mx[3], s_hi;
     int pre[kMaxIters];         // counts at s_hi / 2^(k+1) of this level's earlier layers (-1: none)
+    float st_s[kMaxIters];      // a layer's sizes s_hi / 2^(k+1) and their bounds (settled steps)
+    long long st_b[kMaxIters];
     unsigned acc_cnt, acc_err;  // this CTA's pass totals
     int cut_bin, cut_below;
     int red_i[32];
@@ -398,20 +400,32 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kST, 1)
                 // bounding box spans, or an earlier layer's count at the same size
                 // s_hi / 2^(t+1) on a superset of the points; the trace keeps the
                 // smaller bound
+                // (the sizes s_hi / 2^(k+1) are known in advance: lane k of warp 0
+                // takes step k by the same k + 1 halvings, and every thread then
+                // walks the bounds in order)
                 int t0 = 0;
-                while (!guided && t0 < steps) {
-                    const float sv = __fmul_rn(__fadd_rn(0.0f, hi), 0.5f);
-                    long long bd = cell_bound(sv, P.aspect, sm.mn, sm.mx);
-                    if (sm.pre[t0] >= 0 && sm.pre[t0] < bd) bd = sm.pre[t0];
-                    if (!(bd < ml)) break;
-                    if (write_tr) {
-                        tr->s[t0] = sv;
-                        tr->K[t0] = bd;
-                        tr->iters = t0 + 1;
-                        tr->bounded |= 1u << t0;
+                if (!guided && steps > 0) {
+                    for (int k = tid; k < steps; k += kST) {  // (warp 0 for steps <= 32)
+                        float sv = hi;
+                        for (int h = 0; h <= k; ++h) sv = __fmul_rn(__fadd_rn(0.0f, sv), 0.5f);
+                        long long bd = cell_bound(sv, P.aspect, sm.mn, sm.mx);
+                        if (sm.pre[k] >= 0 && sm.pre[k] < bd) bd = sm.pre[k];
+                        sm.st_s[k] = sv;
+                        sm.st_b[k] = bd;
                     }
-                    hi = sv;
-                    ++t0;
+                    __syncthreads();
+                    while (t0 < steps && sm.st_b[t0] < ml) {
+                        const float sv = sm.st_s[t0];
+                        if (write_tr) {
+                            tr->s[t0] = sv;
+                            tr->K[t0] = sm.st_b[t0];
+                            tr->iters = t0 + 1;
+                            tr->bounded |= 1u << t0;
+                        }
+                        hi = sv;
+                        ++t0;
+                    }
+                    __syncthreads();  // (st_s, st_b are rewritten by the next layer)
                 }
                 bool pre = !guided;  // every step so far had too few voxels (plain bisection)
 

@@ -921,40 +921,6 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                         fl |= F_UP;
                     }
                 }
-                // bisection: the leading steps whose outcome is already settled are
-                // taken without a pass: at the size s_hi / 2^(k+1) either an earlier
-                // layer of this level counted fewer than m_l voxels on a superset of
-                // this layer's points, or the bounding box spans fewer than m_l grid
-                // cells.  The trace keeps the smaller bound
-                int nskip = 0;
-                float hi_ff = st.s_hi[tid];
-                int32_t bnd[kMaxIters];
-                if ((fl & F_SEARCH) && P.search == HAV_SEARCH_BISECT) {
-                    fl |= F_PRE;
-                    const int* pre = d.prefix + tid * kMaxIters;
-#pragma unroll
-                    for (int k = 0; k < kMaxIters; ++k) bnd[k] = (k < P.t_max) ? ld_volatile(pre + k) : -1;
-                    while (nskip < P.t_max) {
-                        const float sv = __fmul_rn(__fadd_rn(0.0f, hi_ff), 0.5f);
-                        long long b = cell_bound(sv, P.aspect, st.mn[tid], st.mx[tid]);
-                        if (bnd[nskip] >= 0 && bnd[nskip] < b) b = bnd[nskip];
-                        if (!(b < ml)) break;
-                        bnd[nskip] = static_cast<int32_t>(b);
-                        hi_ff = sv;
-                        ++nskip;
-                    }
-                    st.hi[tid] = hi_ff;
-                    st.iters[tid] = nskip;
-                    if (nskip >= P.t_max) {  // every step settled: no acceptance, s* = hi
-                        fl = F_ACTIVE;
-                        st.s_star[tid] = hi_ff;
-                        if (!make_grid(hi_ff, P.aspect, st.mn[tid], &st.grid[tid])) {
-                            seg_error(d, tid, HAV_ERR_RANGE);
-                            st.err[tid] = HAV_ERR_RANGE;
-                            fl = 0;
-                        }
-                    }
-                }
                 if (active && (P.t_max == 0 || fixed)) {
                     st.s_star[tid] = fixed ? P.fixed_s : st.s_hi[tid];
                     if (!make_grid(st.s_star[tid], P.aspect, st.mn[tid], &st.grid[tid])) {
@@ -970,21 +936,69 @@ __global__ void __launch_bounds__(kThreads, 1) hav_chain_kernel(const __grid_con
                     tr->k_max = kmax;
                     tr->k_star = 0;
                     tr->n_in = st.n[tid] - taken_before;
-                    tr->iters = nskip;
+                    tr->iters = 0;
                     tr->accepted = 0;
                     tr->s_hi = st.s_hi[tid];
-                    tr->s_star = (nskip >= P.t_max && (fl & F_ACTIVE)) ? hi_ff : 0.0f;
-                    tr->bounded = nskip ? (0xffffffffu >> (32 - nskip)) : 0u;
-                    float h = st.s_hi[tid];
-                    for (int k = 0; k < nskip; ++k) {
-                        h = __fmul_rn(__fadd_rn(0.0f, h), 0.5f);
-                        tr->s[k] = h;
-                        tr->K[k] = bnd[k];
-                    }
+                    tr->s_star = (P.t_max == 0 && (fl & F_ACTIVE)) ? st.s_hi[tid] : 0.0f;
+                    tr->bounded = 0u;
                 }
                 taken_before += ml;
             }
             __syncthreads();
+            // bisection: the leading steps whose outcome is already settled are
+            // taken without a pass: at the size s_hi / 2^(k+1) either an earlier
+            // layer of this level counted fewer than m_l voxels on a superset of
+            // this layer's points, or the bounding box spans fewer than m_l grid
+            // cells.  The trace keeps the smaller bound.  One warp per searching
+            // segment, lane k the step k (the same k + 1 halvings of s_hi).
+            if (P.search == HAV_SEARCH_BISECT && P.t_max > 0) {
+                static_assert(kMaxIters <= 32, "one lane per step");
+                const int lane = tid & 31;
+                for (int s = tid >> 5; s < S; s += kThreads / 32) {  // (warp-uniform)
+                    if (!(st.flags[s] & F_SEARCH)) continue;
+                    const long long ml = st.ml[s];
+                    float sv = st.s_hi[s];
+                    for (int h = 0; h <= lane; ++h) sv = __fmul_rn(__fadd_rn(0.0f, sv), 0.5f);
+                    long long bd = LLONG_MAX;
+                    if (lane < P.t_max) {
+                        bd = cell_bound(sv, P.aspect, st.mn[s], st.mx[s]);
+                        const int pk = ld_volatile(d.prefix + s * kMaxIters + lane);
+                        if (pk >= 0 && pk < bd) bd = pk;
+                    }
+                    const unsigned settled = __ballot_sync(0xffffffffu, lane < P.t_max && bd < ml);
+                    const int nskip = __ffs(~settled) - 1;  // leading settled steps
+                    const float hi_ff = __shfl_sync(0xffffffffu, sv, nskip > 0 ? nskip - 1 : 0);
+                    int fl = st.flags[s] | F_PRE;
+                    const float hi_s = nskip > 0 ? hi_ff : st.s_hi[s];
+                    if (nskip >= P.t_max) fl = F_ACTIVE;  // every step settled: no acceptance, s* = hi
+                    if (lane == 0) {
+                        st.hi[s] = hi_s;
+                        st.iters[s] = nskip;
+                        if (nskip >= P.t_max) {
+                            st.s_star[s] = hi_s;
+                            if (!make_grid(hi_s, P.aspect, st.mn[s], &st.grid[s])) {
+                                seg_error(d, s, HAV_ERR_RANGE);
+                                st.err[s] = HAV_ERR_RANGE;
+                                fl = 0;
+                            }
+                        }
+                        st.flags[s] = fl;
+                    }
+                    if (blockIdx.x == 0) {
+                        hav_layer_trace* tr = d.tr + (static_cast<long long>(j) * S + s) * kMaxLayers + l;
+                        if (lane < nskip) {
+                            tr->s[lane] = sv;
+                            tr->K[lane] = bd;
+                        }
+                        if (lane == 0) {
+                            tr->iters = nskip;
+                            tr->s_star = (nskip >= P.t_max && (fl & F_ACTIVE)) ? hi_s : 0.0f;
+                            tr->bounded = nskip ? (0xffffffffu >> (32 - nskip)) : 0u;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
 
             // --------------------------------------- Section 3.3 bisection
             // One pass evaluates the whole depth-D subtree of the bisection below

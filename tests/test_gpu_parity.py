@@ -149,6 +149,26 @@ def test_parameter_variants(hv, ctx, pkw):
     assert_parity(res, tr, K, ora, tr_o)
 
 
+@pytest.mark.parametrize("n", [1000, 20000, 150000])  # one CTA, a cluster, the grid kernel
+@pytest.mark.parametrize("scale", [2.0 ** -23, 1e-30])
+def test_range_error_matches_the_oracle(hv, ctx, oracle_mod, n, scale):
+    # a fixed voxel size (Table 6 "Fix") far below the cloud's extent: the cell
+    # indices need more than 21 bits (extent / 2^23), or the quotient of the
+    # box's minimum is no usable integer (1e-30 times the extent); the library
+    # reports HAV_ERR_RANGE where the oracle does, and the segment takes its
+    # first m points
+    pts = scenes.uniform_box(n, 11)
+    ext = float(np.max(pts.max(axis=0) - pts.min(axis=0)))
+    pkw = {"fixed_s": float(np.float32(ext * scale)), "layers": 1}
+    m = n // 4
+    with pytest.raises(oracle_mod.OracleError) as e:
+        oracle_mod.sample_levels(pts, [m], oracle_mod.params(**pkw))
+    assert e.value.status == hv.HAV_ERR_RANGE
+    res, st, tr, K = run_levels(hv, ctx, pts, [m], pkw)
+    assert st == hv.HAV_ERR_RANGE
+    assert np.array_equal(res[0], np.arange(m, dtype=np.int32))
+
+
 def test_duplicates_and_lattice(hv, ctx):
     rng = np.random.default_rng(0)
     base = rng.uniform(0, 4, size=(300, 3)).astype(np.float32)

@@ -304,6 +304,32 @@ def test_batched_error_is_contained(hv, ctx):
     assert list(parts[2]) == list(range(700))
 
 
+def test_batched_error_in_a_sorted_segment_is_contained(hv, ctx):
+    # a NaN in a segment large enough to be sorted by Morton cell: that segment
+    # reports HAV_ERR_NONFINITE and takes its first m points, the others stay
+    # exact; segments of 2^17 - 1 and 2^17 points sit on either side of the
+    # sorting threshold
+    bad = scenes.room_scene(140000, 12)
+    bad[70000, 1] = np.nan
+    clouds = [scenes.uniform_box((1 << 17) - 1, 13), bad, scenes.uniform_box(1 << 17, 14),
+              scenes.uniform_box(5000, 15)]
+    sizes = [c.shape[0] for c in clouds]
+    outs, st, per, tr, seg_m, layers = _batched(hv, ctx, clouds, [[n // 4 for n in sizes], [n // 16 for n in sizes]])
+    assert st == hv.HAV_ERR_NONFINITE
+    assert per == [0, hv.HAV_ERR_NONFINITE, 0, 0]
+    keep = (0, 2, 3)
+    ora = G.oracle_many([clouds[s] for s in keep], [[sizes[s] // 4, sizes[s] // 16] for s in keep])
+    for j in range(2):
+        parts = _split(outs[j], seg_m[j])
+        for k, s in enumerate(keep):
+            assert np.array_equal(parts[s], ora[k][0][j]), (j, s)
+        assert list(parts[1]) == list(range(int(seg_m[j][1]))), j
+    # one sorted cloud alone with the same NaN
+    res, st1, _, _ = run_levels(hv, ctx, bad, [35000])
+    assert st1 == hv.HAV_ERR_NONFINITE
+    assert list(res[0]) == list(range(35000))
+
+
 TUNINGS = [
     {"spec_points": [0, 0, 0], "chunk_min": 64},                       # plain bisection
     {"spec_points": [1 << 31, 1 << 31, 1 << 31], "chunk_min": 32},     # depth 4 wherever it fits

@@ -7,8 +7,10 @@
 //
 // A uniform grid with cells of at least the radius (so every ball lies in the
 // 3 x 3 x 3 cells around its centre's cell) is built by a counting sort of the
-// points by cell; one warp per centre then scans those cells and keeps the
-// nsample smallest qualifying indices in a sorted list.  The result does not
+// points by cell; one warp per centre then scans those cells, collects the
+// qualifying indices in shared memory (sorted and cut to the nsample smallest
+// whenever the buffer fills, the largest kept one then bounding the rest) and
+// sorts them once at the end.  The result does not
 // depend on the grid, only the work does.  Two kernels on the caller's
 // stream: the grid build (one cooperative launch) and the query.
 
@@ -182,18 +184,44 @@ __global__ void __launch_bounds__(kThreads, 1)
 // entry is skipped once the list is full).  The list's contents do not depend
 // on the order in which the candidates arrive.
 constexpr int kQueryWarps = 4;  // warps per block of the query
+constexpr int kCollect = 512;   // qualifying points a warp collects at most before it sorts and cuts them
+
+// Ascending bitonic sort of buf[0, cnt) by one warp (cnt <= kCollect; the
+// rest of the next power of two is padded with the largest index).
+__device__ __forceinline__ void sort_prefix(int32_t* buf, int cnt, int lane) {
+    int n2 = 32;
+    while (n2 < cnt) n2 <<= 1;
+    for (int e = cnt + lane; e < n2; e += 32) buf[e] = 0x7fffffff;
+    __syncwarp();
+    for (int k2 = 2; k2 <= n2; k2 <<= 1)
+        for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+            for (int i = lane; i < n2; i += 32) {
+                const int ixj = i ^ j2;
+                if (ixj > i) {
+                    const int32_t u = buf[i], w = buf[ixj];
+                    if ((u > w) == ((i & k2) == 0)) {
+                        buf[i] = w;
+                        buf[ixj] = u;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+}
 
 __global__ void __launch_bounds__(32 * kQueryWarps)
     grp_query(const float* pts, long long n, const int32_t* centres, long long m, float radius, int nsample,
               const GroupGrid* g, const uint32_t* end, const int32_t* list, int32_t* out_idx, float* out_xyz,
               int32_t* status, const GlobalHdr* gh) {
-    __shared__ int32_t sbest[kQueryWarps][kGrpMaxSample];
+    __shared__ int32_t sbuf[kQueryWarps][kCollect];
     if (ld_volatile(&gh->abort)) return;  // the build gave up (its status says so)
     const GroupGrid G = *g;
     const float r2 = __fmul_rn(radius, radius);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    int32_t* best = sbest[wib];
+    int32_t* buf = sbuf[wib];
+    int cap = 64;
+    while (cap < 2 * nsample && cap < kCollect) cap <<= 1;
     const long long warps = static_cast<long long>(gridDim.x) * kQueryWarps;
     for (long long j = blockIdx.x * static_cast<long long>(kQueryWarps) + wib; j < m; j += warps) {
         const int32_t ci = centres[j];
@@ -209,75 +237,72 @@ __global__ void __launch_bounds__(32 * kQueryWarps)
         int c[3];
         const float cp[3] = {cx, cy, cz};
         cell_of(cp, G, c);
-        int cnt = 0;           // entries in best (warp-uniform)
-        int32_t top = 0x7fffffff;  // best[nsample - 1] once the list is full
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int z = c[2] + dz;
-            if (z < 0 || z >= G.dims[2]) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int y = c[1] + dy;
-                if (y < 0 || y >= G.dims[1]) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int x = c[0] + dx;
-                    if (x < 0 || x >= G.dims[0]) continue;
-                    const long long cell = (static_cast<long long>(z) * G.dims[1] + y) * G.dims[0] + x;
-                    const uint32_t a = (cell > 0) ? end[cell - 1] : 0u;
-                    uint32_t b = end[cell];
-                    if (b > static_cast<uint32_t>(n)) b = static_cast<uint32_t>(n);
-                    for (uint32_t q0 = a; q0 < b; q0 += 32) {  // warp-uniform
-                        const uint32_t q = q0 + lane;
-                        int32_t k = 0;
-                        bool ok = false;
-                        if (q < b) {
-                            k = list[q];
-                            if (k >= 0 && k < n && k < top) {
-                                const float ex = __fsub_rn(pts[3ll * k], cx), ey = __fsub_rn(pts[3ll * k + 1], cy),
-                                            ez = __fsub_rn(pts[3ll * k + 2], cz);
-                                const float d2 =
-                                    __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-                                ok = d2 < r2;
+        // the 3 x 3 x 3 cells around the centre's, every point within the radius
+        // visited once; visit(k, ok) is called by the whole warp per 32 points
+        auto scan = [&](auto&& visit, const int32_t& top) {
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int z = c[2] + dz;
+                if (z < 0 || z >= G.dims[2]) continue;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int y = c[1] + dy;
+                    if (y < 0 || y >= G.dims[1]) continue;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int x = c[0] + dx;
+                        if (x < 0 || x >= G.dims[0]) continue;
+                        const long long cell = (static_cast<long long>(z) * G.dims[1] + y) * G.dims[0] + x;
+                        const uint32_t a = (cell > 0) ? end[cell - 1] : 0u;
+                        uint32_t b = end[cell];
+                        if (b > static_cast<uint32_t>(n)) b = static_cast<uint32_t>(n);
+                        for (uint32_t q0 = a; q0 < b; q0 += 32) {  // warp-uniform
+                            const uint32_t q = q0 + lane;
+                            int32_t k = 0;
+                            bool ok = false;
+                            if (q < b) {
+                                k = list[q];
+                                if (k >= 0 && k < n && k < top) {
+                                    const float ex = __fsub_rn(pts[3ll * k], cx), ey = __fsub_rn(pts[3ll * k + 1], cy),
+                                                ez = __fsub_rn(pts[3ll * k + 2], cz);
+                                    const float d2 =
+                                        __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+                                    ok = d2 < r2;
+                                }
                             }
-                        }
-                        unsigned mask = __ballot_sync(0xffffffffu, ok);
-                        while (mask) {  // insert the qualifying candidates one by one
-                            const int src = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            const int32_t kk = __shfl_sync(0xffffffffu, k, src);
-                            if (kk >= top) continue;  // (top only falls)
-                            // its position: the entries below it
-                            int below = 0;
-                            for (int e = lane; e < cnt; e += 32) below += (best[e] < kk) ? 1 : 0;
-                            const int pos = __reduce_add_sync(0xffffffffu, below);
-                            // entries [pos, last) move up one place; the last one drops out when full
-                            const int last = (cnt < nsample) ? cnt : nsample - 1;
-                            int32_t v[kGrpMaxSample / 32];
-#pragma unroll
-                            for (int r = 0; r < kGrpMaxSample / 32; ++r) {
-                                const int e = pos + lane + 32 * r;
-                                v[r] = (e < last) ? best[e] : 0;
-                            }
-                            __syncwarp();
-#pragma unroll
-                            for (int r = 0; r < kGrpMaxSample / 32; ++r) {
-                                const int e = pos + lane + 32 * r;
-                                if (e < last) best[e + 1] = v[r];
-                            }
-                            if (lane == 0) best[pos] = kk;
-                            __syncwarp();
-                            if (cnt < nsample) ++cnt;
-                            if (cnt == nsample) top = best[nsample - 1];
+                            visit(k, ok);
                         }
                     }
                 }
             }
-        }
+        };
+        // the qualifying indices, unsorted, into the warp's buffer; when it is
+        // full it is sorted and cut to the nsample smallest, whose largest then
+        // bounds every later index (indices are distinct); one sort at the end.
+        // The buffer holds 2 nsample rounded up to a power of two, 64 to
+        // kCollect: a small one bounds the scan early where many points qualify
+        int cnt = 0;
+        int32_t top = 0x7fffffff;
+        scan([&](int32_t k, bool ok) {
+            unsigned mask = __ballot_sync(0xffffffffu, ok);
+            if (cnt + __popc(mask) > cap) {  // (warp-uniform)
+                sort_prefix(buf, cnt, lane);
+                if (cnt > nsample) cnt = nsample;
+                if (cnt == nsample) top = buf[nsample - 1];
+                ok = ok && k < top;
+                mask = __ballot_sync(0xffffffffu, ok);
+            }
+            if (ok) buf[cnt + __popc(mask & ((1u << lane) - 1u))] = k;
+            cnt += __popc(mask);
+        }, top);
+        __syncwarp();
+        sort_prefix(buf, cnt, lane);
+        const int32_t* res = buf;
+        if (cnt > nsample) cnt = nsample;
         if (cnt == 0) {  // unreachable: the centre is at distance 0
-            if (lane == 0) best[0] = ci;
+            if (lane == 0) buf[0] = ci;
             __syncwarp();
             cnt = 1;
         }
         for (int s = lane; s < nsample; s += 32) {
-            const int32_t k = (s < cnt) ? best[s] : best[0];
+            const int32_t k = (s < cnt) ? res[s] : res[0];
             row[s] = k;
             if (out_xyz) {
                 float* o = out_xyz + (j * nsample + s) * 3;

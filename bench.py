@@ -145,13 +145,19 @@ def _code_only(text: str) -> str:
     return " ".join("".join(out).split())
 
 
+# the files the sampler's kernels (hav_chain_kernel, hav_small_kernel) and
+# their launch are built from; the other kernels (grouping, spacing, FPS,
+# representatives, the allocation-free entry) do not change the profiled call
+SAMPLER_SOURCES = ("hav_api.cu", "hav_device.cuh", "hav_internal.h", "hav_sampler.cu", "hav_small.cu")
+
+
 def source_hash() -> str:
-    """Hash of the kernel sources' code (comments and layout ignored)."""
+    """Hash of the sampler kernels' source code (comments and layout ignored)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_14306_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode() + b"\0" + _code_only(open(os.path.join(csrc, f)).read()).encode() + b"\0")
+    for f in SAMPLER_SOURCES + ("../../include/hav.h",):
+        h.update(os.path.basename(f).encode() + b"\0" +
+                 _code_only(open(os.path.join(csrc, f)).read()).encode() + b"\0")
     return h.hexdigest()[:16]
 
 

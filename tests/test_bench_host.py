@@ -20,21 +20,31 @@ def test_code_only_drops_comments_and_layout_but_keeps_literals():
 
 
 def test_captured_traffic_follows_the_code_hash(tmp_path, monkeypatch):
+    # the hash covers the code of the sampler kernels' sources and the ABI
+    # header: comments do not count, and neither do the other kernels' files
     csrc = tmp_path / "paper_2305_14306_gb300" / "csrc"
     csrc.mkdir(parents=True)
+    (tmp_path / "include").mkdir()
     (tmp_path / "profiles").mkdir()
-    k = csrc / "k.cu"
-    k.write_text("__global__ void f() {}  // first\n")
+    for f in bench.SAMPLER_SOURCES:
+        (csrc / f).write_text(f"// {f}\nint x_{len(f)} = 1;\n")
+    (tmp_path / "include" / "hav.h").write_text("int abi = 1;\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h = bench.source_hash()
     prof = tmp_path / "profiles" / "hav_chain_kernel_w.md"
     prof.write_text(f"x\n\nsource_hash: {h}\ndram_bytes_per_call: 12345\n")
     assert bench.profiled_traffic("w") == 12345
     assert bench.profiled_traffic("other") is None
-    k.write_text("__global__ void f() {}\n/* reworded comment */\n")
+    k = csrc / "hav_sampler.cu"
+    k.write_text(k.read_text() + "/* reworded comment */\n")
+    (csrc / "hav_group.cu").write_text("__global__ void g() {}\n")  # another kernel's file
     assert bench.source_hash() == h and bench.profiled_traffic("w") == 12345
-    (csrc / "d.cuh").write_text("#define X 1\n")  # device headers count too
+    (csrc / "hav_device.cuh").write_text("#define X 1\n")  # a device header of the sampler
     assert bench.source_hash() != h and bench.profiled_traffic("w") is None
+    (csrc / "hav_device.cuh").write_text("// hav_device.cuh\nint x_14 = 1;\n")
+    assert bench.source_hash() == h
+    (tmp_path / "include" / "hav.h").write_text("int abi = 2;\n")  # the ABI header
+    assert bench.source_hash() != h
 
 
 def test_algorithmic_bytes_by_hand():

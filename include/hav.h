@@ -358,8 +358,12 @@ hav_status hav_fps(hav_ctx* ctx, const float* points, int64_t n, int64_t m, int3
  * n*3 floats; idx: device, m int32 indices into points (any order, repeats
  * allowed: a repeated point has spacing 0); out_d2: device, m floats.  An
  * index outside [0, n) is skipped and reported as HAV_ERR_INVALID by
- * hav_status_get.  Exact all-pairs search (O(m^2) work, about 31 ms for
- * m = 262,144 on GB300); a measurement, not part of the sampler. */
+ * hav_status_get.  Exact nearest-neighbour search: all pairs below 32,768
+ * subset points (two launches); from there, when the subset fits the
+ * context's max_points, on a grid built over the subset (three launches;
+ * cells of 1/256 of the largest extent searched shell by shell with an exact
+ * stopping bound: 0.2 ms for m = 262,144 on GB300, against 31 ms for all
+ * pairs).  A measurement, not part of the sampler. */
 hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32_t* idx, int64_t m,
                        float* out_d2, hav_stream stream);
 

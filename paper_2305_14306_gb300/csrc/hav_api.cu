@@ -423,6 +423,13 @@ hav_status hav_spacing(hav_ctx* ctx, const float* points, int64_t n, const int32
     ctx->last_S = 1;
     if (m == 0) return HAV_OK;
     havk::GlobalHdr* gh = reinterpret_cast<havk::GlobalHdr*>(ctx->ws + ctx->lay.ghdr);
+    // large subsets that fit the workspace: the exact grid search; else all pairs
+    if (m >= havk::kSpacingGridMin && m <= ctx->lay.max_points) {
+        if (!counted(ctx, havk::launch_spacing_grid(points, n, idx, m, out_d2, ctx->ws, ctx->lay, &gh->status,
+                                                    ctx->max_blocks, strm)))
+            return HAV_ERR_CUDA;
+        return HAV_OK;
+    }
     if (!counted(ctx, havk::launch_spacing(points, n, idx, m, out_d2, &gh->status, ctx->max_blocks, strm)))
         return HAV_ERR_CUDA;
     return HAV_OK;

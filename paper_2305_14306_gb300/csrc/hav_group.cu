@@ -179,10 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // One warp per centre: the lanes test 32 candidates of the 27 cells at a
-// time, and the warp keeps the nsample smallest qualifying indices so far in
-// an ascending list in shared memory (a candidate at or above the list's last
-// entry is skipped once the list is full).  The list's contents do not depend
-// on the order in which the candidates arrive.
+// time, and the warp collects the qualifying indices in shared memory; the
+// nsample smallest do not depend on the order in which the candidates arrive.
 constexpr int kQueryWarps = 4;  // warps per block of the query
 constexpr int kCollect = 512;   // qualifying points a warp collects at most before it sorts and cuts them
 
@@ -315,6 +313,106 @@ __global__ void __launch_bounds__(32 * kQueryWarps)
     }
 }
 
+// ------------------------------------------------------ spacing on the grid
+// The Fig. 3 spacing of a large subset (hav_spacing): the subset's points are
+// gathered (an invalid index or a non-finite coordinate as NaN: no distance
+// involving such a point is ever below another, exactly as in the all-pairs
+// search), the grid above is built over them (cells of 1/256 of the largest
+// extent, grown within the budget), and one thread per point, in cell order,
+// visits the shells of cells at Chebyshev distance r = 0, 1, ... around its
+// own until no cell farther out can hold a nearer point.  A point of a cell r
+// + 1 or more shells away lies at least (r - 0.01) h away (the cell map is
+// exact to far less than 0.01 cells), and a computed squared distance is
+// within a relative 2^-20 of the exact one, so the search stops once best <
+// ((r - 0.01) h)^2 (1 - 2^-20), every bound rounded down.  A point still
+// searching after kShellMax shells scans the whole subset instead.
+constexpr int kShellMax = 32;
+
+__global__ void spacing_gather(const float* pts, long long n, const int32_t* idx, long long m, float* sub,
+                               int32_t* status) {
+    for (long long q = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; q < m;
+         q += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int32_t i = idx[q];
+        float x = NAN, y = NAN, z = NAN;
+        if (i < 0 || i >= n) {
+            atomicCAS(status, 0, static_cast<int>(HAV_ERR_INVALID));
+        } else {
+            x = pts[3ll * i];
+            y = pts[3ll * i + 1];
+            z = pts[3ll * i + 2];
+            if (!(isfinite(x) && isfinite(y) && isfinite(z))) x = y = z = NAN;
+        }
+        sub[3 * q] = x;
+        sub[3 * q + 1] = y;
+        sub[3 * q + 2] = z;
+    }
+}
+
+__device__ __forceinline__ float sq_dist(const float* p, float x, float y, float z) {
+    const float ex = __fsub_rn(p[0], x), ey = __fsub_rn(p[1], y), ez = __fsub_rn(p[2], z);
+    return __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+}
+
+__global__ void spacing_grid_query(const float* sub, long long m, const GroupGrid* g, const uint32_t* end,
+                                   const int32_t* list, float* out_d2, const GlobalHdr* gh) {
+    if (ld_volatile(&gh->abort)) return;  // the build gave up (its status says so)
+    const GroupGrid G = *g;
+    // the cell width, rounded down and shrunk by 2^-20
+    const float h = __fmul_rd(__fdiv_rd(1.0f, G.inv_h), 0.99999904632568359375f);
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < m;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = list[t];
+        const float x = sub[3ll * i], y = sub[3ll * i + 1], z = sub[3ll * i + 2];
+        float best = INFINITY;
+        if (x == x) {  // (a gathered point is NaN on every axis or on none)
+            int c[3];
+            const float p3[3] = {x, y, z};
+            cell_of(p3, G, c);
+            bool done = false;
+            int r = 0;
+            for (; r <= kShellMax && !done; ++r) {
+                for (int dz = -r; dz <= r; ++dz) {
+                    const int zc = c[2] + dz;
+                    if (zc < 0 || zc >= G.dims[2]) continue;
+                    for (int dy = -r; dy <= r; ++dy) {
+                        const int yc = c[1] + dy;
+                        if (yc < 0 || yc >= G.dims[1]) continue;
+                        const bool face = (dz == -r || dz == r || dy == -r || dy == r);
+                        for (int dx = -r; dx <= r; dx += (face || r == 0) ? 1 : 2 * r) {
+                            const int xc = c[0] + dx;
+                            if (xc < 0 || xc >= G.dims[0]) continue;
+                            const long long cell = (static_cast<long long>(zc) * G.dims[1] + yc) * G.dims[0] + xc;
+                            const uint32_t a = (cell > 0) ? end[cell - 1] : 0u;
+                            const uint32_t b = end[cell];
+                            for (uint32_t q = a; q < b && q < static_cast<uint32_t>(m); ++q) {
+                                const int j = list[q];
+                                if (j == i) continue;
+                                best = fminf(best, sq_dist(sub + 3ll * j, x, y, z));
+                            }
+                        }
+                    }
+                }
+                // every cell visited, or none farther out can hold a nearer point
+                bool all = true;
+                for (int a3 = 0; a3 < 3; ++a3) all = all && c[a3] - r <= 0 && c[a3] + r >= G.dims[a3] - 1;
+                if (all) {
+                    done = true;
+                } else if (r >= 1) {
+                    const float bd = __fmul_rd(__fsub_rd(static_cast<float>(r), 0.01f), h);
+                    const float bd2 = __fmul_rd(__fmul_rd(bd, bd), 0.99999904632568359375f);
+                    if (best < bd2) done = true;
+                }
+            }
+            if (!done) {  // an isolated point: the whole subset
+                best = INFINITY;
+                for (long long j = 0; j < m; ++j)
+                    if (j != i) best = fminf(best, sq_dist(sub + 3 * j, x, y, z));
+            }
+        }
+        out_d2[i] = best;
+    }
+}
+
 }  // namespace
 
 int group_coresident_blocks(int device) {
@@ -359,6 +457,40 @@ int launch_ball_query(const float* points, long long n, const int32_t* centres, 
     grp_query<<<static_cast<unsigned>(qb < 1 ? 1 : qb), 32 * kQueryWarps, 0, stream>>>(
         points, n, centres, m, radius, nsample, g, counts, list, out_idx, out_xyz, status, gh);
     return cudaGetLastError() == cudaSuccess ? 2 : -1;
+}
+
+int launch_spacing_grid(const float* points, long long n, const int32_t* idx, long long m, float* out_d2,
+                        unsigned char* ws, const Layout& lay, int32_t* status, int nblocks, cudaStream_t stream) {
+    if (m < 2 || m > lay.max_points) return -1;
+    // scratch as the ball query's, and the gathered subset in the second staged-point array
+    GroupGrid* g = reinterpret_cast<GroupGrid*>(ws + lay.ptimes);
+    uint32_t* block_sums = reinterpret_cast<uint32_t*>(ws + lay.ptimes + 256);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(ws + lay.cand);
+    int32_t* list = reinterpret_cast<int32_t*>(ws + lay.ord[0]);
+    float* sub = reinterpret_cast<float*>(ws + lay.ord[1]);
+    long long budget = static_cast<long long>(sizeof(Cand)) * lay.cand_slots / 4;
+    if (budget > kMaxCells) budget = kMaxCells;
+    if (cudaMemsetAsync(g, 0, sizeof(GroupGrid), stream) != cudaSuccess) return -1;
+    long long gb = (m + 255) / 256;
+    if (gb > 65536) gb = 65536;
+    spacing_gather<<<static_cast<unsigned>(gb), 256, 0, stream>>>(points, n, idx, m, sub, status);
+    Barrier* bar = reinterpret_cast<Barrier*>(ws + lay.barrier);  // zeroed by the caller
+    GlobalHdr* gh = reinterpret_cast<GlobalHdr*>(ws + lay.ghdr);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(nblocks));
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // (the smallest normal radius: the cells follow the extent alone)
+    if (cudaLaunchKernelEx(&cfg, grp_build, static_cast<const float*>(sub), m, 1.17549435e-38f, budget, g, counts,
+                           block_sums, list, bar, gh) != cudaSuccess)
+        return -1;
+    spacing_grid_query<<<static_cast<unsigned>(gb), 256, 0, stream>>>(sub, m, g, counts, list, out_d2, gh);
+    return cudaGetLastError() == cudaSuccess ? 3 : -1;
 }
 
 }  // namespace havk

@@ -121,6 +121,7 @@ constexpr int kMaxItems = kMaxBlocks + kMaxSegments;  // work items of one level
 
 // Largest table load factor setting: capacity nextpow2(2^3 n), at most 1/8 full.
 constexpr int kMaxTableLog2 = 3;
+constexpr long long kSpacingGridMin = 32768;  // subsets from this size search their spacing on a grid
 
 inline Layout make_layout(int64_t N, int32_t S, bool spec_room = true, int table_log2 = 1) {
     Layout L{};
@@ -235,6 +236,9 @@ int launch_ball_query(const float* points, long long n, const int32_t* centres, 
                       int nsample, int32_t* out_idx, float* out_xyz, unsigned char* ws, const Layout& lay,
                       int32_t* status, int nblocks, cudaStream_t stream);
 // Subset point spacing (hav_spacing.cu), and its histogram over bin edges.
+// the spacing of a subset of 2 to max_points points on a grid (3 launches)
+int launch_spacing_grid(const float* points, long long n, const int32_t* idx, long long m, float* out_d2,
+                        unsigned char* ws, const Layout& lay, int32_t* status, int nblocks, cudaStream_t stream);
 int launch_spacing(const float* points, long long n, const int32_t* idx, long long m, float* out_d2,
                    int32_t* status, int sms, cudaStream_t stream);
 constexpr int kHistEdgesMax = HAV_SPACING_MAX_BINS + 1;

@@ -140,3 +140,27 @@ def test_spacing_histogram_edge_cases(hv, ctx, oracle_mod):
     for bad in ([1.0, 1.0], [2.0, 1.0], [0.0, np.inf]):
         with pytest.raises(hv.HavError):
             hv.hav_spacing_histogram(ctx, dev(pts), torch.from_numpy(idx).cuda(), np.array(bad, np.float32))
+
+
+def test_spacing_on_the_grid(hv, ctx, oracle_mod):
+    # subsets of 32,768 points and more are searched on a grid, shell by shell
+    # around each point's cell, with an exact stopping bound: bit-identical to
+    # the oracle's all-pairs minimum on a room, a LiDAR scan (cells near the
+    # sensor hold thousands of returns), repeated indices, a NaN point, and a
+    # far isolated point that scans the whole subset
+    room = scenes.room_scene(120000, 4)
+    rng = np.random.default_rng(2)
+    check(hv, ctx, oracle_mod, room, rng.choice(120000, 40000, replace=False))
+    lidar = scenes.lidar_exact(40000, 2)
+    check(hv, ctx, oracle_mod, lidar, np.arange(lidar.shape[0]))
+    box = scenes.uniform_box(60000, seed=6)
+    idx = rng.choice(60000, 40000, replace=False)
+    idx[100:200] = idx[:100]  # repeated indices: spacing 0
+    got = check(hv, ctx, oracle_mod, box, idx)
+    assert (got[:100] == 0).all()
+    nan = box.copy()
+    nan[idx[5], 2] = np.nan
+    got = check(hv, ctx, oracle_mod, nan, idx[:32768])
+    assert np.isinf(got[5])
+    far = np.concatenate([scenes.uniform_box(32768, seed=7), np.array([[1e6, 1e6, 1e6]], np.float32)])
+    check(hv, ctx, oracle_mod, far, np.arange(far.shape[0]))

@@ -248,7 +248,8 @@ hav_status hav_context_set_tuning(hav_ctx* ctx, const hav_tuning* t);
 /* Number of device kernels the context's calls have launched since it was
  * created (memsets and copies excluded), in *out (HOST).  A level chain
  * launches one to three kernels (hav_tuning), hav_sample_xyz one more, the
- * spacing and farthest-point calls one each, the ball query two.
+ * spacing call two (three for a subset searched on a grid), its histogram
+ * one more, the farthest-point call one, the ball query two.
  * HAV_ERR_INVALID on a NULL argument. */
 hav_status hav_context_launches(const hav_ctx* ctx, uint64_t* out);
 

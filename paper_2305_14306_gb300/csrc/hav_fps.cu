@@ -16,6 +16,7 @@ namespace havk {
 namespace {
 
 constexpr int kFpsThreads = 1024;
+constexpr size_t kFpsResidentBytes = 200 * 1024;  // shared memory for a block's resident points
 
 // packed (distance bits, inverted index): the maximum is the farthest point,
 // ties to the lowest index; picked points pack to 0 and never win
@@ -24,9 +25,14 @@ __device__ __forceinline__ unsigned long long fps_pack(float d2, int i) {
            static_cast<unsigned long long>(0xffffffffu - static_cast<unsigned>(i));
 }
 
+// kResident: the block's points and distances stay in shared memory (x, y,
+// z, distance per point) for the whole run instead of being read from L2 in
+// every round; the arithmetic and the picks are the same.
+template <bool kResident>
 __global__ void __launch_bounds__(kFpsThreads, 1)
-    fps_kernel(const float* pts, int n, int m, int32_t* out, float* dist, unsigned long long* bmax, Barrier* bar,
+    fps_kernel(const float* pts, int n, int m, int32_t* out, float* dist_g, unsigned long long* bmax, Barrier* bar,
                GlobalHdr* gh, int nblocks) {
+    extern __shared__ float4 res[];
     __shared__ unsigned long long red[32];
     __shared__ int s_flag;
     __shared__ unsigned epoch;
@@ -36,7 +42,10 @@ __global__ void __launch_bounds__(kFpsThreads, 1)
     const int chunk = (n + nblocks - 1) / nblocks;
     const int a = blockIdx.x * chunk;
     const int b = min(n, a + chunk);
-    for (int i = a + tid; i < b; i += kFpsThreads) dist[i] = INFINITY;
+    for (int i = a + tid; i < b; i += kFpsThreads) {
+        if constexpr (kResident) res[i - a] = make_float4(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], INFINITY);
+        else dist_g[i] = INFINITY;
+    }
     int last = 0;
     if (blockIdx.x == 0 && tid == 0) out[0] = 0;
     __syncthreads();
@@ -44,19 +53,35 @@ __global__ void __launch_bounds__(kFpsThreads, 1)
         const float qx = pts[3 * last], qy = pts[3 * last + 1], qz = pts[3 * last + 2];
         unsigned long long best = 0ull;
         for (int i = a + tid; i < b; i += kFpsThreads) {
-            float di = dist[i];
+            float px, py, pz, di;
+            if constexpr (kResident) {
+                const float4 r4 = res[i - a];
+                px = r4.x;
+                py = r4.y;
+                pz = r4.z;
+                di = r4.w;
+            } else {
+                di = dist_g[i];
+            }
             if (i == last) {
                 di = -1.0f;  // picked: never again
-                dist[i] = di;
+                if constexpr (kResident) res[i - a].w = di;
+                else dist_g[i] = di;
             }
             if (di < 0.0f) continue;
-            const float dx = __fsub_rn(pts[3 * i], qx);
-            const float dy = __fsub_rn(pts[3 * i + 1], qy);
-            const float dz = __fsub_rn(pts[3 * i + 2], qz);
+            if constexpr (!kResident) {
+                px = pts[3 * i];
+                py = pts[3 * i + 1];
+                pz = pts[3 * i + 2];
+            }
+            const float dx = __fsub_rn(px, qx);
+            const float dy = __fsub_rn(py, qy);
+            const float dz = __fsub_rn(pz, qz);
             const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
             if (d2 < di) {
                 di = d2;
-                dist[i] = di;
+                if constexpr (kResident) res[i - a].w = di;
+                else dist_g[i] = di;
             }
             const unsigned long long k = fps_pack(di, i);
             best = k > best ? k : best;
@@ -102,7 +127,8 @@ __global__ void __launch_bounds__(kFpsThreads, 1)
 int fps_coresident_blocks(int device) {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fps_kernel, kFpsThreads, 0) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fps_kernel<false>, kFpsThreads, 0) != cudaSuccess)
+        return -1;
     long long nb = static_cast<long long>(sms) * per_sm;
     if (nb > kMaxBlocks) nb = kMaxBlocks;
     return static_cast<int>(nb);
@@ -128,7 +154,30 @@ int launch_fps(const float* points, int n, int m, int32_t* out, unsigned char* w
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, fps_kernel, points, n, m, out, dist, bmax, bar, gh, nb) == cudaSuccess ? 1 : -1;
+    // the block's share resident in shared memory where it fits and the grid
+    // stays co-resident with that much shared memory per block
+    const long long chunk = (static_cast<long long>(n) + nb - 1) / nb;
+    const size_t bytes = static_cast<size_t>(chunk) * sizeof(float4);
+    bool resident = bytes <= kFpsResidentBytes &&
+                    cudaFuncSetAttribute(fps_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kFpsResidentBytes)) == cudaSuccess;
+    if (resident) {
+        int dev = 0, sms = 0, per_sm = 0;
+        resident = cudaGetDevice(&dev) == cudaSuccess &&
+                   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fps_kernel<true>, kFpsThreads, bytes) ==
+                       cudaSuccess &&
+                   static_cast<long long>(sms) * per_sm >= nb;
+    }
+    if (resident) {
+        cfg.dynamicSmemBytes = bytes;
+        return cudaLaunchKernelEx(&cfg, fps_kernel<true>, points, n, m, out, dist, bmax, bar, gh, nb) == cudaSuccess
+                   ? 1
+                   : -1;
+    }
+    return cudaLaunchKernelEx(&cfg, fps_kernel<false>, points, n, m, out, dist, bmax, bar, gh, nb) == cudaSuccess
+               ? 1
+               : -1;
 }
 
 }  // namespace havk

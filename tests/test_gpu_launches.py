@@ -76,6 +76,9 @@ def test_other_calls_count_their_kernels(hv):
         torch.cuda.synchronize()
         assert launched(ctx, lambda: hv.hav_fps(ctx, big, 500)) == 1
         assert launched(ctx, lambda: hv.hav_spacing(ctx, big, idx)) == 2
+        # a subset from 32,768 points: gathered, a grid built over it, searched
+        assert launched(ctx, lambda: hv.hav_spacing(ctx, big, torch.arange(40_000, dtype=torch.int32,
+                                                                          device="cuda"))) == 3
         assert launched(ctx, lambda: hv.hav_ball_query(ctx, big, idx[:100], 0.05, 16)) == 2
         st, _ = hv.hav_status_get(ctx, 1)
         assert st == hv.HAV_OK

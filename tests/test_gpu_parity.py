@@ -416,6 +416,20 @@ def test_fps_matches_oracle(hv, ctx, oracle_mod, n, m, seed):
     assert np.array_equal(got, oracle_mod.fps(pts, m))
 
 
+@pytest.mark.parametrize("n,m", [(1_000_003, 64), (2_000_003, 48)])
+def test_fps_large_clouds(hv, oracle_mod, n, m):
+    # a million points: each block's share held in shared memory; two
+    # million: too many for that, read from global memory in every round
+    pts = scenes.uniform_box(n, 6)
+    ctx = hv.Context(n, 1)
+    try:
+        got = hv.hav_fps(ctx, dev(pts), m).cpu().numpy()
+        assert hv.hav_status_get(ctx)[0] == 0
+    finally:
+        ctx.close()
+    assert np.array_equal(got, oracle_mod.fps(pts, m))
+
+
 def test_fps_hand_case_and_duplicates(hv, ctx, oracle_mod):
     line = np.array([[x, 0, 0] for x in range(11)], dtype=np.float32)
     assert list(hv.hav_fps(ctx, dev(line), 4).cpu().numpy()) == [0, 10, 5, 2]

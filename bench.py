@@ -870,8 +870,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-slots", type=int, default=2,
-                    help="co-resident serving slots (GB300 sweep at 800 requests: 2 slots of 4x the largest "
-                         "scene 3.08x the plain path, 3 of 2x 3.02x, larger slots slower)")
+                    help="co-resident serving slots (GB300 at 800 requests: 2 slots of 4x the largest "
+                         "scene 4.79x the plain path, 3 of 2x 4.8x)")
     ap.add_argument("--no-search-compare", action="store_true",
                     help="skip timing the guided search start beside the default one")
     ap.add_argument("--search", choices=["bisect", "guided"], default="bisect",
@@ -885,7 +885,7 @@ def main():
                     help="served path: clouds of at least this many points get a call of their own "
                          "(lower p99, lower throughput: GB300 at 2^17, p99 at 0.95 load 2.6 -> 1.5 ms, "
                          "3.08x -> 2.2-2.8x the plain path); 0: batch every cloud")
-    ap.add_argument("--serve-requests", type=int, default=800,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving object in the default line")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON cache of autotuned knobs (default: always sweep, write nothing)")

@@ -494,3 +494,48 @@ def test_small_level_engines_match_the_grid_kernel(hv, spec):
                 c.set_tuning(cluster_ctas=q)
     finally:
         c.close()
+
+
+# ------------------------------------------------------ limits of the boundary
+def test_maximum_segment_count(hv, ctx):
+    # 256 segments, the most a call takes: two large clouds that are sorted by
+    # Morton cell (one at exactly 2^17 points, where that starts), the others
+    # small, empty or single points
+    rng = np.random.default_rng(77)
+    sizes = [int(x) for x in rng.integers(0, 2500, size=256)]
+    sizes[3], sizes[200], sizes[17], sizes[90] = 131072, 140000, 0, 1
+    clouds = [scenes.room_scene(n, 40 + i) if n >= 131072 else scenes.uniform_box(n, 40 + i)
+              for i, n in enumerate(sizes)]
+    check_batched(hv, ctx, clouds, [[n // 4 for n in sizes], [n // 16 for n in sizes]])
+    with pytest.raises(hv.HavError):
+        hv.Context(1000, 257)
+
+
+@pytest.mark.parametrize("pkw,ml", [
+    ({"layers": 8, "layer_ratio": 2}, [16384]),  # the most layers
+    ({"layers": 8}, [16384, 4096]),  # ratio 4: the first layers get no budget and are skipped
+    ({}, [32768, 16384, 8192, 4096, 2048, 1024, 512, 256]),  # the most levels
+])
+def test_maximum_layers_and_levels(hv, ctx, pkw, ml):
+    pts = scenes.room_scene(65536, 12)
+    res, st, tr, K = run_levels(hv, ctx, pts, ml, pkw)
+    assert st == 0
+    (ora, tr_o), = G.oracle_many([pts], [ml], pkw)
+    assert_parity(res, tr, K, ora, tr_o)
+    with pytest.raises(hv.HavError):
+        hv.hav_sample_levels(ctx, dev(pts[:4096]), [256] * 9)
+
+
+@pytest.mark.slow
+def test_eight_million_points(hv, oracle_mod):
+    # a room of 2^23 points to 2^21 in one call (one level, two layers)
+    n, m = 1 << 23, 1 << 21
+    pts = scenes.room_scene(n, 9)
+    c = hv.Context(n, 1)
+    try:
+        got = hv.hav_sample(c, dev(pts), m).cpu().numpy()
+        assert hv.hav_status_get(c)[0] == 0
+    finally:
+        c.close()
+    ref = oracle_mod.sample(pts, m)
+    assert np.array_equal(got, ref)

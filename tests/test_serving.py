@@ -10,7 +10,9 @@ pytestmark = pytest.mark.gpu
 from paper_2305_14306_gb300 import scenes  # noqa: E402
 
 
-def test_served_results_equal_standalone_calls():
+@pytest.mark.parametrize("solo", [None, 100_000])
+def test_served_results_equal_standalone_calls(solo):
+    # solo: clouds of at least that many points get a call of their own
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2305_14306_gb300 import build, hav, serving
@@ -23,13 +25,15 @@ def test_served_results_equal_standalone_calls():
         pts = scenes.lidar_exact(n, 100 + i) if n > 20000 else scenes.uniform_box(n, i)
         m = [n // 4, n // 16, min(4096, n)][i % 3]
         reqs.append(serving.Request(i, arrival=0.002 * (i // 6), points=torch.from_numpy(pts).pin_memory(), m=m))
-    srv = serving.Server(slots=3, slot_points=400_000, max_segments=16)
+    srv = serving.Server(slots=3, slot_points=400_000, max_segments=16, solo_points=solo)
     try:
         res = srv.serve(reqs)
     finally:
         srv.close()
     assert sorted(res) == list(range(len(reqs)))
     assert max(r.batch for r in res.values()) > 1  # requests really shared launches
+    if solo:
+        assert all(res[r.rid].batch == 1 for r in reqs if r.points.shape[0] >= solo)
     ctx = hav.Context(150000, 1)
     try:
         for r in reqs:

@@ -346,11 +346,12 @@ hav_status hav_count(hav_ctx* ctx, const float* points, int64_t n, float s,
  * index 0, repeatedly take the point farthest (squared binary32 distance,
  * ties to the lowest index) from the points taken so far.  points: device,
  * n*3 floats; out_idx: device, m int32 in selection order.  0 <= m <= n <=
- * the context's max_points.  One cooperative launch with one grid barrier
- * per selected point (each block's share of the points and their distances
- * held in its shared memory where 16 bytes a point fit, about 1.9 M points on
- * 152 SMs); asynchronous on `stream`; a barrier timeout is read with
- * hav_status_get. */
+ * the context's max_points.  One launch: up to 32,768 points one cluster of
+ * 8 CTAs with one cluster barrier per selected point, above that a
+ * cooperative grid with one grid barrier per selected point (each block's
+ * share of the points and their distances held in its shared memory where 16
+ * bytes a point fit, about 1.9 M points on 152 SMs); asynchronous on
+ * `stream`; a grid barrier timeout is read with hav_status_get. */
 hav_status hav_fps(hav_ctx* ctx, const float* points, int64_t n, int64_t m, int32_t* out_idx,
                    hav_stream stream);
 

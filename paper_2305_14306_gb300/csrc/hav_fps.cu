@@ -1,16 +1,20 @@
 // Farthest point sampling (Eq. 1 of Section 3.1), the comparator the paper
 // measures HAVSampler against: one cooperative launch, one bounded grid
-// barrier per selected point.
+// barrier per selected point; clouds of up to 32,768 points on one cluster
+// of 8 CTAs instead, one cluster barrier per selected point.
 //
 // Start at index 0; every point keeps its squared distance to the selected
 // set (binary32, (dx*dx + dy*dy) + dz*dz without contraction); the next pick
 // is the largest distance, ties to the lowest index; picked points are never
 // picked again.
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "hav_device.cuh"
 #include "hav_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace havk {
 namespace {
@@ -122,6 +126,116 @@ __global__ void __launch_bounds__(kFpsThreads, 1)
     }
 }
 
+constexpr int kFpsQ = 8;                  // CTAs of the small-cloud cluster (portable size)
+constexpr int kFpsQPoints = 4096;         // points one CTA of it holds
+constexpr int kFpsClusterMax = kFpsQ * kFpsQPoints;
+
+// a CTA's best candidate of a round with the point's coordinates
+struct FpsCand {
+    unsigned long long key;  // fps_pack of the CTA's farthest unpicked point
+    float x, y, z, pad;
+};
+
+// Clouds of at most kFpsClusterMax points: CTA r of one cluster holds points
+// [r c, (r + 1) c), c = ceil(n / kFpsQ), with their distances in its shared
+// memory.  Each round every CTA writes its best candidate into its own slot
+// (two slots alternate), the cluster barrier publishes them, and every CTA
+// takes the same maximum over the kFpsQ slots read through distributed shared
+// memory; round j + 2 rewrites a slot only after every CTA has passed round
+// j + 1's barrier, so no read of round j can see it.  The same arithmetic,
+// ties and picks as fps_kernel.
+__global__ void __cluster_dims__(kFpsQ, 1, 1) __launch_bounds__(kFpsThreads, 1)
+    fps_cluster_kernel(const float* pts, int n, int m, int32_t* out) {
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ float4 res[];
+    __shared__ unsigned long long red[32];
+    __shared__ FpsCand cand[2];
+    __shared__ float4 s_q;  // the last pick: x, y, z and its index bits
+    const int tid = threadIdx.x;
+    const int r = static_cast<int>(cl.block_rank());
+    const int chunk = (n + kFpsQ - 1) / kFpsQ;
+    const int a = r * chunk;
+    const int b = min(n, a + chunk);
+    for (int i = a + tid; i < b; i += kFpsThreads)
+        res[i - a] = make_float4(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], INFINITY);
+    if (r == 0 && tid == 0 && m > 0) out[0] = 0;
+    float qx = 0.0f, qy = 0.0f, qz = 0.0f;
+    if (n > 0) {
+        qx = pts[0];
+        qy = pts[1];
+        qz = pts[2];
+    }
+    int last = 0;
+    __syncthreads();
+    for (int j = 1; j < m; ++j) {
+        unsigned long long best = 0ull;
+        for (int i = a + tid; i < b; i += kFpsThreads) {
+            const float4 p4 = res[i - a];
+            float di = p4.w;
+            if (i == last) {
+                di = -1.0f;  // picked: never again
+                res[i - a].w = di;
+            }
+            if (di < 0.0f) continue;
+            const float dx = __fsub_rn(p4.x, qx);
+            const float dy = __fsub_rn(p4.y, qy);
+            const float dz = __fsub_rn(p4.z, qz);
+            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            if (d2 < di) {
+                di = d2;
+                res[i - a].w = di;
+            }
+            const unsigned long long k = fps_pack(di, i);
+            best = k > best ? k : best;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+            best = v > best ? v : best;
+        }
+        if ((tid & 31) == 0) red[tid >> 5] = best;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long bb = red[0];
+            for (int w = 1; w < kFpsThreads / 32; ++w) bb = red[w] > bb ? red[w] : bb;
+            FpsCand& c = cand[j & 1];
+            c.key = bb;
+            if (bb != 0ull) {  // this CTA's point: its coordinates travel with it
+                const int g = static_cast<int>(0xffffffffu - static_cast<unsigned>(bb & 0xffffffffull));
+                const float4 p4 = res[g - a];
+                c.x = p4.x;
+                c.y = p4.y;
+                c.z = p4.z;
+            }
+        }
+        cl.sync();
+        if (tid == 0) {
+            unsigned long long bk = 0ull;
+            float bx = qx, by = qy, bz = qz;
+            for (int q = 0; q < kFpsQ; ++q) {
+                const FpsCand* c = cl.map_shared_rank(&cand[j & 1], q);
+                const unsigned long long k = c->key;
+                if (k > bk) {
+                    bk = k;
+                    bx = c->x;
+                    by = c->y;
+                    bz = c->z;
+                }
+            }
+            const int pick = static_cast<int>(0xffffffffu - static_cast<unsigned>(bk & 0xffffffffull));
+            const int s_last = (bk != 0ull && pick >= 0 && pick < n) ? pick : 0;  // m <= n: an unpicked point exists
+            s_q = make_float4(bx, by, bz, __int_as_float(s_last));
+            if (r == 0) out[j] = s_last;
+        }
+        __syncthreads();
+        const float4 q4 = s_q;
+        qx = q4.x;
+        qy = q4.y;
+        qz = q4.z;
+        last = __float_as_int(q4.w);
+    }
+    cl.sync();  // no CTA leaves while another may still read its slots
+}
+
 }  // namespace
 
 int fps_coresident_blocks(int device) {
@@ -141,6 +255,20 @@ int launch_fps(const float* points, int n, int m, int32_t* out, unsigned char* w
     unsigned long long* bmax = reinterpret_cast<unsigned long long*>(ws + lay.ptimes);
     Barrier* bar = reinterpret_cast<Barrier*>(ws + lay.barrier);
     GlobalHdr* gh = reinterpret_cast<GlobalHdr*>(ws + lay.ghdr);
+    // up to 32,768 points: one cluster of 8 CTAs, a cluster barrier per pick
+    if (n <= kFpsClusterMax) {
+        const int chunk = (n + kFpsQ - 1) / kFpsQ;
+        const size_t bytes = static_cast<size_t>(chunk < 1 ? 1 : chunk) * sizeof(float4);
+        if (cudaFuncSetAttribute(fps_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kFpsQPoints * sizeof(float4))) == cudaSuccess) {
+            cudaLaunchConfig_t cc = {};
+            cc.gridDim = dim3(kFpsQ);
+            cc.blockDim = dim3(kFpsThreads);
+            cc.dynamicSmemBytes = bytes;
+            cc.stream = stream;
+            return cudaLaunchKernelEx(&cc, fps_cluster_kernel, points, n, m, out) == cudaSuccess ? 1 : -1;
+        }
+    }
     // fewer blocks than points per block of work would only add barrier arrivals
     int nb = nblocks;
     const int want = (n + kFpsThreads - 1) / kFpsThreads;

@@ -408,7 +408,10 @@ def test_c4_batch_64_lidar_clouds(hv):
 
 
 # ------------------------------------------------------ FPS comparator
-@pytest.mark.parametrize("n,m,seed", [(16384, 512, 0), (16384, 4096, 1), (1000, 100, 2), (5, 5, 3), (3000, 1, 4)])
+# up to 32,768 points on one 8-CTA cluster (some CTAs empty for tiny clouds),
+# above it on the cooperative grid
+@pytest.mark.parametrize("n,m,seed", [(16384, 512, 0), (16384, 4096, 1), (1000, 100, 2), (5, 5, 3), (3000, 1, 4),
+                                      (7, 7, 7), (32768, 700, 8), (32769, 700, 9)])
 def test_fps_matches_oracle(hv, ctx, oracle_mod, n, m, seed):
     pts = scenes.uniform_box(n, seed)
     got = hv.hav_fps(ctx, dev(pts), m).cpu().numpy()

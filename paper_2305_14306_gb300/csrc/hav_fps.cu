@@ -256,6 +256,7 @@ int launch_fps(const float* points, int n, int m, int32_t* out, unsigned char* w
     Barrier* bar = reinterpret_cast<Barrier*>(ws + lay.barrier);
     GlobalHdr* gh = reinterpret_cast<GlobalHdr*>(ws + lay.ghdr);
     // up to 32,768 points: one cluster of 8 CTAs, a cluster barrier per pick
+    // (where the device refuses the cluster, the grid form below)
     if (n <= kFpsClusterMax) {
         const int chunk = (n + kFpsQ - 1) / kFpsQ;
         const size_t bytes = static_cast<size_t>(chunk < 1 ? 1 : chunk) * sizeof(float4);
@@ -266,7 +267,8 @@ int launch_fps(const float* points, int n, int m, int32_t* out, unsigned char* w
             cc.blockDim = dim3(kFpsThreads);
             cc.dynamicSmemBytes = bytes;
             cc.stream = stream;
-            return cudaLaunchKernelEx(&cc, fps_cluster_kernel, points, n, m, out) == cudaSuccess ? 1 : -1;
+            if (cudaLaunchKernelEx(&cc, fps_cluster_kernel, points, n, m, out) == cudaSuccess) return 1;
+            (void)cudaGetLastError();  // a refused launch configuration leaves no sticky error
         }
     }
     // fewer blocks than points per block of work would only add barrier arrivals
